@@ -1,0 +1,9 @@
+"""CPU FP64 oracle for the BLDTT compute phase.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, __graft_entry__.smoke() and the
+CPU-baseline leg of bench.py, never by the library.  See bldtt_oracle.py for
+the passages of the paper each function follows and the readings taken.
+"""
+from .bldtt_oracle import *  # noqa: F401,F403
+from .bldtt_oracle import (COULOMB, YUKAWA, TEST_POLY, PP, PC, CP, CC, Result,  # noqa: F401
+                           SampledBLDTT, Tree)
