@@ -1,0 +1,227 @@
+/*
+ * bldtt.h - C ABI of the GB300 BLDTT library (libbldtt.so).
+ *
+ * The library computes the compute phase of the barycentric Lagrange dual
+ * tree traversal (BLDTT) of Wilson, Vaughn & Krasny: the potentials
+ *
+ *     phi(x_i) = sum_j G(x_i, y_j) q_j,   i = 1..M          (Eq. (1))
+ *
+ * of M target particles due to N charged source particles, approximated with
+ * particle-particle (PP), particle-cluster (PC), cluster-particle (CP) and
+ * cluster-cluster (CC) interactions between the clusters of a target tree and
+ * a source tree (Algorithm 1).  Every step runs in CUDA kernels on the device
+ * that is current when bldtt_setup is called; there is no CPU fallback.
+ *
+ * Conventions shared by all entry points
+ *  - Particle coordinates are float64 structure-of-arrays: a buffer of 3*M
+ *    doubles holding x[0..M), then y[0..M), then z[0..M).
+ *  - "device" pointers are CUDA device (or managed) memory of the current
+ *    device; "host" pointers are ordinary host memory.
+ *  - cuda_stream is a cudaStream_t passed as void*; NULL means the legacy
+ *    default stream.  All work of a call is ordered on that stream.
+ *  - Every int-returning function returns a bldtt_status; nothing throws and
+ *    nothing aborts.  After an error the plan can still be destroyed.
+ *  - Readings of the paper the library applies where the paper is silent:
+ *    leaf iff |C| <= M0 (or all box extents are zero); up to 1, 2 or 3
+ *    split dimensions for M0<|C|<=2M0, 2M0<|C|<=4M0, larger; a dimension is
+ *    split only if L_d*L_d*2 >= L_max*L_max; split at the midpoint of the
+ *    shrunk box, upper half iff coord >= midpoint; children ordered by
+ *    (x,y,z) bits; cluster radius = half the box diagonal; MAC evaluated as
+ *    r_t + r_s < theta*R; proxy points c + h*cos(pi k/n) per dimension;
+ *    a pair at distance 0 contributes nothing.
+ */
+#ifndef BLDTT_H
+#define BLDTT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum bldtt_status {
+    BLDTT_OK = 0,
+    BLDTT_EINVAL = 1,     /* invalid argument (size, degree, theta, kernel, NaN input ...) */
+    BLDTT_ENOMEM = 2,     /* a device allocation failed */
+    BLDTT_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed */
+    BLDTT_ETIMEOUT = 4,   /* a bounded wait inside a kernel gave up (error flag set) */
+    BLDTT_EINTERNAL = 5   /* an internal consistency check failed */
+};
+
+/* Interaction kernels G(x, y), with r = |x - y| (Sec. 4.6). */
+enum bldtt_kernel {
+    BLDTT_COULOMB = 0,    /* G = 1/r */
+    BLDTT_YUKAWA = 1,     /* G = exp(-kappa r)/r, kappa >= 0 */
+    BLDTT_TEST_POLY = 99  /* test kernel of degree 2 in each coordinate, d = x - y:
+                             G = 1 + d1 - 2 d2 + 3 d3 + d1 d2 - d2 d3 + d1^2 d3^2 - d2^2/2.
+                             Interpolation of degree n >= 2 reproduces it exactly. */
+};
+
+/* Arithmetic of the kernel evaluations. */
+enum bldtt_precision {
+    BLDTT_FP64 = 0,       /* plain FP64 everywhere */
+    BLDTT_FP32_BULK = 1   /* kernel evaluations and Lagrange contractions in FP32, in
+                             coordinate frames local to each source cluster, summed in
+                             FP64 every 64 sources; barycentric weights, the
+                             coincident-point guard, proxy points, proxy charges,
+                             proxy potentials and the final phi stay FP64 */
+};
+
+/* Interaction types (Sec. 2.4), used to index the list arrays below. */
+enum bldtt_interaction { BLDTT_PP = 0, BLDTT_PC = 1, BLDTT_CP = 2, BLDTT_CC = 3 };
+
+typedef struct bldtt_plan bldtt_plan;   /* opaque; owned by the library */
+
+typedef struct bldtt_stats {
+    int64_t num_targets, num_sources;
+    int32_t num_target_clusters, num_source_clusters;
+    int32_t num_target_leaves, num_source_leaves;
+    int32_t target_levels, source_levels;
+    int64_t list_entries[4];            /* entries per type PP, PC, CP, CC */
+    double interactions[4];             /* kernel evaluations per type, as defined by
+                                           Eqs. (6), (8), (12), (15): |C_t||C_s|,
+                                           |C_t| n_p, n_p |C_s|, n_p^2 per entry */
+    double executed_evaluations;        /* evaluations the interaction kernel performs,
+                                           padding of tiles and chunks included */
+    int64_t work_items;                 /* target tiles drained by the interaction kernel */
+    int32_t interact_grid;              /* CTAs of the persistent interaction kernel */
+    int32_t interact_threads;           /* threads per CTA of that kernel */
+    float ms_tree, ms_lists;            /* last bldtt_setup: trees; traversal + work lists */
+    float ms_upward, ms_interact, ms_downward, ms_compute;   /* last bldtt_compute */
+    int64_t launches_setup, launches_compute;                /* kernels launched */
+} bldtt_stats_t;
+
+/*
+ * bldtt_setup - build both trees (Sec. 2.3), run the dual tree traversal
+ * (Algorithm 2) and lay out the work of the compute phase.
+ *
+ *  plan      out: receives a new plan; *plan is NULL on error.
+ *  targets   device, 3*M float64, SoA (x block, y block, z block).
+ *  M         number of targets, 1 <= M < 2^31.
+ *  sources   device, 3*N float64, SoA.
+ *  N         number of sources, 1 <= N < 2^31.
+ *  charges   device, N float64 (input order of the sources).
+ *  kernel    enum bldtt_kernel; kappa >= 0 is used by BLDTT_YUKAWA only.
+ *  n         interpolation degree, 1 <= n <= 16; proxies per cluster n_p=(n+1)^3.
+ *  theta     MAC parameter, theta >= 0 (theta = 0 gives only PP, i.e. the direct sum).
+ *  N0, M0    maximum particles per source / target leaf, >= 1.
+ *  precision enum bldtt_precision.
+ *
+ * The caller keeps ownership of targets/sources/charges; they are copied into
+ * tree order before the call returns (the call synchronises the stream), so
+ * they may be freed afterwards.  The plan owns all device memory it
+ * allocates (stream-ordered allocations on cuda_stream).
+ * Errors: EINVAL for out-of-range sizes or parameters, a non-finite
+ * coordinate or charge, an unknown kernel or precision; ENOMEM; ECUDA.
+ */
+int bldtt_setup(bldtt_plan** plan,
+                const double* targets, int64_t M,
+                const double* sources, int64_t N,
+                const double* charges,
+                int kernel, double kappa, int n, double theta, int N0, int M0,
+                int precision, void* cuda_stream);
+
+/*
+ * bldtt_set_charges - replace the source charges of a plan (device, N
+ * float64, input order).  Trees and interaction lists depend only on the
+ * positions and parameters and are reused.  Errors: EINVAL (NULL arguments,
+ * non-finite charge), ECUDA.
+ */
+int bldtt_set_charges(bldtt_plan* plan, const double* charges, void* cuda_stream);
+
+/*
+ * bldtt_compute - upward pass (Sec. 2.5), PP/PC/CP/CC interactions over the
+ * lists (Sec. 2.4), downward pass (Sec. 2.7); writes phi.
+ *
+ *  phi  device, M float64, input order of the targets; overwritten.
+ *
+ * Asynchronous on cuda_stream (no host synchronisation; phase timings are
+ * read later by bldtt_stats).  Errors: EINVAL, ECUDA, ETIMEOUT (reported by
+ * the next call that synchronises, e.g. bldtt_stats or bldtt_check_error).
+ */
+int bldtt_compute(bldtt_plan* plan, double* phi, void* cuda_stream);
+
+/* Synchronise the plan's last stream and report a device-side error flag
+ * (ETIMEOUT from a bounded wait, EINTERNAL from a bounds check). */
+int bldtt_check_error(bldtt_plan* plan);
+
+/* Fill *out with the counts above and the phase times of the last setup and
+ * compute (synchronises the plan's stream).  Errors: EINVAL, ECUDA. */
+int bldtt_stats(bldtt_plan* plan, bldtt_stats_t* out);
+
+/* Release the plan and all its device memory.  NULL is ignored. */
+void bldtt_destroy(bldtt_plan* plan);
+
+/* Static, NUL-terminated name of a status code. */
+const char* bldtt_status_string(int status);
+
+/* Text of the last error raised by the calling host thread ("" if none). */
+const char* bldtt_last_error(void);
+
+/* ---- Introspection (host copies; each synchronises the plan's stream) ---- */
+
+/*
+ * bldtt_tree_size - number of clusters and levels of the target (which = 0)
+ * or source (which = 1) tree.
+ */
+int bldtt_tree_size(bldtt_plan* plan, int which, int32_t* num_clusters, int32_t* num_levels);
+
+/*
+ * bldtt_export_tree - copy one tree to host buffers.  Clusters are numbered
+ * level by level (parents before children).  perm[p] (num particles) is the
+ * input index of the particle at tree position p; cluster c holds tree
+ * positions [begin[c], end[c]); lo/hi are 3*C float64 SoA (x block, y block,
+ * z block) of the shrunk box; parent[c] is -1 for the root; level[c] is the
+ * depth.  Any pointer may be NULL to skip that array.
+ */
+int bldtt_export_tree(bldtt_plan* plan, int which, int32_t* perm, int32_t* begin, int32_t* end,
+                      double* lo, double* hi, int32_t* parent, int32_t* level);
+
+/*
+ * bldtt_export_lists - copy the entries of one interaction list type
+ * (enum bldtt_interaction) as (target cluster, source cluster) pairs, sorted
+ * by target cluster.  count is in/out: capacity on entry, entries on return
+ * (EINVAL, with the needed count, if the capacity is too small).
+ */
+int bldtt_export_lists(bldtt_plan* plan, int type, int32_t* target, int32_t* source,
+                       int64_t* count);
+
+/* Copy the proxy charges q-hat (Eq. (9)) of every source cluster after the
+ * last compute: num_source_clusters * n_p float64, cluster-major, proxy index
+ * k = (k1*(n+1) + k2)*(n+1) + k3. */
+int bldtt_export_proxy_charges(bldtt_plan* plan, double* qhat);
+
+/* Copy the proxy potentials phi(t) of every target cluster after the
+ * downward pass of the last compute (CP + CC of the cluster plus everything
+ * interpolated down from its ancestors, Eq. (20)); same layout as q-hat. */
+int bldtt_export_proxy_potentials(bldtt_plan* plan, double* phit);
+
+/* ---- Helpers ---- */
+
+/*
+ * bldtt_direct_sum - FP64 direct summation, Eq. (1), on the device: for
+ * every target i, phi[i] = sum_j G(x_i, y_j) q_j with pairs at distance 0
+ * skipped.  Pointers are device memory in the layouts above.  Used to measure
+ * the error of the fast method on sampled targets.  Asynchronous on
+ * cuda_stream.  Errors: EINVAL, ECUDA.
+ */
+int bldtt_direct_sum(const double* targets, int64_t M, const double* sources, int64_t N,
+                     const double* charges, int kernel, double kappa, double* phi,
+                     void* cuda_stream);
+
+/*
+ * bldtt_solve_host - one-shot solve from host memory: copies the inputs to
+ * the device, runs bldtt_setup and bldtt_compute, copies phi back and frees
+ * everything.  targets (3*M), sources (3*N), charges (N) and phi (M) are
+ * host float64 buffers; stats may be NULL.  Synchronous.
+ */
+int bldtt_solve_host(const double* targets, int64_t M, const double* sources, int64_t N,
+                     const double* charges, int kernel, double kappa, int n, double theta,
+                     int N0, int M0, int precision, double* phi, bldtt_stats_t* stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BLDTT_H */

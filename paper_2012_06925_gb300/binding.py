@@ -1,0 +1,289 @@
+"""Thin ctypes binding of libbldtt.so (C ABI in include/bldtt.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Device arrays are torch CUDA float64 tensors (PyTorch provides
+device memory and streams); host arrays are numpy float64 arrays.  If the
+library is missing or cannot be loaded this module raises; there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbldtt.so")
+
+COULOMB, YUKAWA, TEST_POLY = 0, 1, 99
+FP64, FP32_BULK = 0, 1
+PP, PC, CP, CC = 0, 1, 2, 3
+
+EXPORTED = (
+    "bldtt_setup", "bldtt_set_charges", "bldtt_compute", "bldtt_check_error", "bldtt_stats",
+    "bldtt_destroy", "bldtt_status_string", "bldtt_last_error", "bldtt_tree_size",
+    "bldtt_export_tree", "bldtt_export_lists", "bldtt_export_proxy_charges",
+    "bldtt_export_proxy_potentials", "bldtt_direct_sum", "bldtt_solve_host",
+)
+
+
+class BLDTTError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(what)
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("num_targets", ctypes.c_int64), ("num_sources", ctypes.c_int64),
+        ("num_target_clusters", ctypes.c_int32), ("num_source_clusters", ctypes.c_int32),
+        ("num_target_leaves", ctypes.c_int32), ("num_source_leaves", ctypes.c_int32),
+        ("target_levels", ctypes.c_int32), ("source_levels", ctypes.c_int32),
+        ("list_entries", ctypes.c_int64 * 4), ("interactions", ctypes.c_double * 4),
+        ("executed_evaluations", ctypes.c_double), ("work_items", ctypes.c_int64),
+        ("interact_grid", ctypes.c_int32), ("interact_threads", ctypes.c_int32),
+        ("ms_tree", ctypes.c_float), ("ms_lists", ctypes.c_float),
+        ("ms_upward", ctypes.c_float), ("ms_interact", ctypes.c_float),
+        ("ms_downward", ctypes.c_float), ("ms_compute", ctypes.c_float),
+        ("launches_setup", ctypes.c_int64), ("launches_compute", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if hasattr(v, "__len__") else v
+        return out
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libbldtt.so (raises if it is missing: build it with build.py)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: the CUDA library must be built "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    P_i32 = ctypes.POINTER(ctypes.c_int32)
+    P_i64 = ctypes.POINTER(ctypes.c_int64)
+    P_dbl = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "bldtt_setup": (i32, [ctypes.POINTER(vp), vp, i64, vp, i64, vp, i32, dbl, i32, dbl, i32,
+                               i32, i32, vp]),
+        "bldtt_set_charges": (i32, [vp, vp, vp]),
+        "bldtt_compute": (i32, [vp, vp, vp]),
+        "bldtt_check_error": (i32, [vp]),
+        "bldtt_stats": (i32, [vp, ctypes.POINTER(Stats)]),
+        "bldtt_destroy": (None, [vp]),
+        "bldtt_status_string": (ctypes.c_char_p, [i32]),
+        "bldtt_last_error": (ctypes.c_char_p, []),
+        "bldtt_tree_size": (i32, [vp, i32, P_i32, P_i32]),
+        "bldtt_export_tree": (i32, [vp, i32, P_i32, P_i32, P_i32, P_dbl, P_dbl, P_i32, P_i32]),
+        "bldtt_export_lists": (i32, [vp, i32, P_i32, P_i32, P_i64]),
+        "bldtt_export_proxy_charges": (i32, [vp, P_dbl]),
+        "bldtt_export_proxy_potentials": (i32, [vp, P_dbl]),
+        "bldtt_direct_sum": (i32, [vp, i64, vp, i64, vp, i32, dbl, vp, vp]),
+        "bldtt_solve_host": (i32, [P_dbl, i64, P_dbl, i64, P_dbl, i32, dbl, i32, dbl, i32, i32,
+                                   i32, P_dbl, ctypes.POINTER(Stats)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        lib = load_library()
+        name = lib.bldtt_status_string(status).decode()
+        detail = lib.bldtt_last_error().decode()
+        raise BLDTTError(status, f"{name}: {detail}")
+
+
+def _dptr(t, n_expected=None):
+    """Device pointer of a contiguous CUDA float64 tensor."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64):
+        raise TypeError("expected a CUDA float64 tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if n_expected is not None and t.numel() != n_expected:
+        raise ValueError(f"expected {n_expected} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _np_ptr(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+class Plan:
+    """A set-up BLDTT problem (bldtt_setup); compute() runs the compute phase."""
+
+    def __init__(self, targets, sources, charges, kernel=COULOMB, kappa=0.0, n=8, theta=0.7,
+                 N0=2000, M0=2000, precision=FP32_BULK, stream=None):
+        lib = load_library()
+        if targets.dim() != 2 or targets.shape[0] != 3 or sources.dim() != 2 or sources.shape[0] != 3:
+            raise ValueError("targets and sources must have shape (3, count)")
+        self.M = int(targets.shape[1])
+        self.N = int(sources.shape[1])
+        self.n = int(n)
+        self.P = self.n + 1
+        self.np = self.P ** 3
+        self._h = ctypes.c_void_p()
+        _check(lib.bldtt_setup(ctypes.byref(self._h), _dptr(targets), self.M, _dptr(sources),
+                               self.N, _dptr(charges, self.N), int(kernel), float(kappa),
+                               self.n, float(theta), int(N0), int(M0), int(precision),
+                               _stream_ptr(stream)))
+
+    def _handle(self):
+        if not self._h:
+            raise RuntimeError("plan already destroyed")
+        return self._h
+
+    def compute(self, phi=None, stream=None):
+        import torch
+        if phi is None:
+            phi = torch.empty(self.M, dtype=torch.float64, device="cuda")
+        _check(load_library().bldtt_compute(self._handle(), _dptr(phi, self.M), _stream_ptr(stream)))
+        return phi
+
+    def set_charges(self, charges, stream=None):
+        _check(load_library().bldtt_set_charges(self._handle(), _dptr(charges, self.N),
+                                                 _stream_ptr(stream)))
+
+    def check_error(self):
+        _check(load_library().bldtt_check_error(self._handle()))
+
+    def stats(self) -> dict:
+        st = Stats()
+        _check(load_library().bldtt_stats(self._handle(), ctypes.byref(st)))
+        return st.as_dict()
+
+    def export_tree(self, which: int) -> dict:
+        lib = load_library()
+        nc, nl = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib.bldtt_tree_size(self._handle(), which, ctypes.byref(nc), ctypes.byref(nl)))
+        C = nc.value
+        npart = self.M if which == 0 else self.N
+        perm = np.empty(npart, dtype=np.int32)
+        begin = np.empty(C, dtype=np.int32)
+        end = np.empty(C, dtype=np.int32)
+        parent = np.empty(C, dtype=np.int32)
+        level = np.empty(C, dtype=np.int32)
+        lo = np.empty(3 * C, dtype=np.float64)
+        hi = np.empty(3 * C, dtype=np.float64)
+        _check(lib.bldtt_export_tree(self._handle(), which, _np_ptr(perm, ctypes.c_int32),
+                                     _np_ptr(begin, ctypes.c_int32), _np_ptr(end, ctypes.c_int32),
+                                     _np_ptr(lo, ctypes.c_double), _np_ptr(hi, ctypes.c_double),
+                                     _np_ptr(parent, ctypes.c_int32), _np_ptr(level, ctypes.c_int32)))
+        return dict(perm=perm, begin=begin, end=end, lo=lo.reshape(3, C), hi=hi.reshape(3, C),
+                    parent=parent, level=level, levels=nl.value)
+
+    def export_lists(self):
+        """Four (target, source) int32 array pairs: PP, PC, CP, CC."""
+        lib = load_library()
+        out = []
+        for typ in range(4):
+            cnt = ctypes.c_int64(0)
+            st = lib.bldtt_export_lists(self._handle(), typ, None, None, ctypes.byref(cnt))
+            if st != 0 and cnt.value == 0:
+                _check(st)
+            t = np.empty(cnt.value, dtype=np.int32)
+            s = np.empty(cnt.value, dtype=np.int32)
+            _check(lib.bldtt_export_lists(self._handle(), typ, _np_ptr(t, ctypes.c_int32),
+                                          _np_ptr(s, ctypes.c_int32), ctypes.byref(cnt)))
+            out.append((t, s))
+        return out
+
+    def proxy_charges(self):
+        lib = load_library()
+        nc = ctypes.c_int32()
+        _check(lib.bldtt_tree_size(self._handle(), 1, ctypes.byref(nc), None))
+        q = np.empty(nc.value * self.np, dtype=np.float64)
+        _check(lib.bldtt_export_proxy_charges(self._handle(), _np_ptr(q, ctypes.c_double)))
+        return q.reshape(nc.value, self.P, self.P, self.P)
+
+    def proxy_potentials(self):
+        lib = load_library()
+        nc = ctypes.c_int32()
+        _check(lib.bldtt_tree_size(self._handle(), 0, ctypes.byref(nc), None))
+        p = np.empty(nc.value * self.np, dtype=np.float64)
+        _check(lib.bldtt_export_proxy_potentials(self._handle(), _np_ptr(p, ctypes.c_double)))
+        return p.reshape(nc.value, self.P, self.P, self.P)
+
+    def close(self):
+        if self._h:
+            load_library().bldtt_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def direct_sum(targets, sources, charges, kernel=COULOMB, kappa=0.0, phi=None, stream=None):
+    """FP64 direct sum on the device (bldtt_direct_sum)."""
+    import torch
+    M, N = int(targets.shape[1]), int(sources.shape[1])
+    if phi is None:
+        phi = torch.empty(M, dtype=torch.float64, device="cuda")
+    _check(load_library().bldtt_direct_sum(_dptr(targets), M, _dptr(sources), N,
+                                           _dptr(charges, N), int(kernel), float(kappa),
+                                           _dptr(phi, M), _stream_ptr(stream)))
+    return phi
+
+
+def solve_host(targets, sources, charges, kernel=COULOMB, kappa=0.0, n=8, theta=0.7, N0=2000,
+               M0=2000, precision=FP32_BULK):
+    """One-shot solve from host numpy arrays (bldtt_solve_host); returns (phi, stats)."""
+    t = np.ascontiguousarray(targets, dtype=np.float64)
+    s = t if sources is targets else np.ascontiguousarray(sources, dtype=np.float64)
+    q = np.ascontiguousarray(charges, dtype=np.float64)
+    M, N = t.shape[1], s.shape[1]
+    phi = np.empty(M, dtype=np.float64)
+    st = Stats()
+    _check(load_library().bldtt_solve_host(_np_ptr(t, ctypes.c_double), M,
+                                           _np_ptr(s, ctypes.c_double), N,
+                                           _np_ptr(q, ctypes.c_double), int(kernel), float(kappa),
+                                           int(n), float(theta), int(N0), int(M0), int(precision),
+                                           _np_ptr(phi, ctypes.c_double), ctypes.byref(st)))
+    return phi, st.as_dict()
+
+
+def status_string(status: int) -> str:
+    return load_library().bldtt_status_string(status).decode()
+
+
+def setup_status(targets_ptr, M, sources_ptr, N, charges_ptr, kernel, kappa, n, theta, N0, M0,
+                 precision):
+    """Raw bldtt_setup status for the given (possibly invalid) arguments; used
+    to test argument validation, which happens before any device work."""
+    lib = load_library()
+    h = ctypes.c_void_p()
+    st = lib.bldtt_setup(ctypes.byref(h), targets_ptr, M, sources_ptr, N, charges_ptr, kernel,
+                         float(kappa), n, float(theta), N0, M0, precision, None)
+    if h:
+        lib.bldtt_destroy(h)
+    return st

@@ -1,0 +1,431 @@
+// C ABI of the library (declared, with argument conventions, in include/bldtt.h).
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace bldtt {
+const char* last_error();
+int configure_pass_kernels();
+}  // namespace bldtt
+
+using namespace bldtt;
+
+namespace {
+
+bool finite(double v) { return std::isfinite(v); }
+
+int validate(int64_t M, int64_t N, int kernel, double kappa, int n, double theta, int N0, int M0,
+             int precision) {
+  if (M < 1 || N < 1 || M >= INT32_MAX || N >= INT32_MAX) {
+    set_error("M=%lld and N=%lld must lie in [1, 2^31-1)", (long long)M, (long long)N);
+    return BLDTT_EINVAL;
+  }
+  if (kernel != BLDTT_COULOMB && kernel != BLDTT_YUKAWA && kernel != BLDTT_TEST_POLY) {
+    set_error("unknown kernel %d", kernel);
+    return BLDTT_EINVAL;
+  }
+  if (kernel == BLDTT_YUKAWA && !(finite(kappa) && kappa >= 0.0)) {
+    set_error("Yukawa kappa must be finite and >= 0 (got %g)", kappa);
+    return BLDTT_EINVAL;
+  }
+  if (n < 1 || n > kMaxDegree) {
+    set_error("interpolation degree n=%d outside [1, %d]", n, kMaxDegree);
+    return BLDTT_EINVAL;
+  }
+  if (!(finite(theta) && theta >= 0.0)) {
+    set_error("MAC parameter theta must be finite and >= 0 (got %g)", theta);
+    return BLDTT_EINVAL;
+  }
+  if (N0 < 1 || M0 < 1) {
+    set_error("leaf sizes N0=%d, M0=%d must be >= 1", N0, M0);
+    return BLDTT_EINVAL;
+  }
+  if (precision != BLDTT_FP64 && precision != BLDTT_FP32_BULK) {
+    set_error("unknown precision %d", precision);
+    return BLDTT_EINVAL;
+  }
+  return BLDTT_OK;
+}
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+    cudaGetLastError();
+    return -1.f;
+  }
+  return ms;
+}
+
+void release(bldtt_plan* p) {
+  if (!p) return;
+  cudaStream_t s = p->stream;
+  free_tree(p->tt, s);
+  free_tree(p->st, s);
+  dfree_ptr(p->q_tree, s);
+  dfree_ptr(p->list_ptr, s);
+  dfree_ptr(p->list_src, s);
+  dfree_ptr(p->list_tgt, s);
+  dfree_ptr(p->pad_prefix, s);
+  dfree(p->pool, s);
+  p->pool = nullptr;
+  dfree_ptr(p->items, s);
+  dfree_ptr(p->item_counter, s);
+  dfree_ptr(p->qhat, s);
+  dfree_ptr(p->phit, s);
+  dfree_ptr(p->phi_near, s);
+  dfree_ptr(p->dev_err, s);
+  cudaStreamSynchronize(s);
+  for (auto& e : p->ev)
+    if (e) cudaEventDestroy(e);
+  cudaGetLastError();
+  delete p;
+}
+
+int setup_impl(bldtt_plan* p, const double* targets, const double* sources, const double* charges) {
+  cudaStream_t s = p->stream;
+  BL_CUDA(cudaGetDevice(&p->device));
+  BL_TRY(configure_pass_kernels());
+  for (auto& e : p->ev) BL_CUDA(cudaEventCreate(&e));
+  BL_TRY(dalloc_n(&p->dev_err, 1, s));
+  BL_CUDA(cudaMemsetAsync(p->dev_err, 0, sizeof(int), s));
+  int* bad = nullptr;
+  BL_TRY(dalloc_n(&bad, 1, s));
+  BL_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  BL_CUDA(cudaEventRecord(p->ev[0], s));
+  BL_TRY(build_tree(p->tt, targets, (int32_t)p->M, p->M0, p->n, bad, s, p->setup_counter));
+  BL_TRY(build_tree(p->st, sources, (int32_t)p->N, p->N0, p->n, bad, s, p->setup_counter));
+  BL_TRY(dalloc_n(&p->q_tree, p->N, s));
+  BL_TRY(permute_charges(p, charges, s));
+  BL_TRY(check_finite(p->q_tree, p->N, bad, s, p->setup_counter));
+  BL_CUDA(cudaEventRecord(p->ev[1], s));
+  int h_bad = 0;
+  BL_CUDA(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BL_CUDA(cudaStreamSynchronize(s));
+  dfree(bad, s);
+  if (h_bad) {
+    set_error("a target, source or charge value is not finite");
+    return BLDTT_EINVAL;
+  }
+  BL_TRY(build_lists(p, s));
+  BL_TRY(build_work_items(p, s));
+  const size_t esz = p->precision == BLDTT_FP32_BULK ? sizeof(float4) : sizeof(double4);
+  BL_TRY(dalloc(&p->pool, (size_t)p->pool_len * esz, s));
+  BL_TRY(dalloc_n(&p->qhat, (size_t)p->st.nclusters * p->np, s));
+  BL_TRY(dalloc_n(&p->phit, (size_t)p->tt.nclusters * p->np, s));
+  BL_TRY(dalloc_n(&p->phi_near, (size_t)p->M, s));
+  BL_TRY(dalloc_n(&p->item_counter, 1, s));
+  BL_TRY(interaction_grid(p, &p->interact_grid));
+  BL_CUDA(cudaEventRecord(p->ev[2], s));
+  BL_CUDA(cudaStreamSynchronize(s));
+  p->ms_tree = elapsed(p->ev[0], p->ev[1]);
+  p->ms_lists = elapsed(p->ev[1], p->ev[2]);
+  return BLDTT_OK;
+}
+
+int sync_plan(bldtt_plan* p) {
+  BL_CUDA(cudaStreamSynchronize(p->stream));
+  return BLDTT_OK;
+}
+
+int device_error(bldtt_plan* p) {
+  int h = 0;
+  BL_CUDA(cudaMemcpy(&h, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h == kDevErrTimeout) {
+    set_error("a bounded wait in the interaction kernel timed out");
+    return BLDTT_ETIMEOUT;
+  }
+  if (h != kDevErrNone) {
+    set_error("device error flag %d", h);
+    return BLDTT_EINTERNAL;
+  }
+  return BLDTT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bldtt_status_string(int status) {
+  switch (status) {
+    case BLDTT_OK: return "BLDTT_OK";
+    case BLDTT_EINVAL: return "BLDTT_EINVAL";
+    case BLDTT_ENOMEM: return "BLDTT_ENOMEM";
+    case BLDTT_ECUDA: return "BLDTT_ECUDA";
+    case BLDTT_ETIMEOUT: return "BLDTT_ETIMEOUT";
+    case BLDTT_EINTERNAL: return "BLDTT_EINTERNAL";
+    default: return "BLDTT_UNKNOWN_STATUS";
+  }
+}
+
+const char* bldtt_last_error(void) { return bldtt::last_error(); }
+
+int bldtt_setup(bldtt_plan** plan, const double* targets, int64_t M, const double* sources,
+                int64_t N, const double* charges, int kernel, double kappa, int n, double theta,
+                int N0, int M0, int precision, void* cuda_stream) {
+  if (!plan) {
+    set_error("plan out-pointer is NULL");
+    return BLDTT_EINVAL;
+  }
+  *plan = nullptr;
+  if (!targets || !sources || !charges) {
+    set_error("targets, sources and charges must be non-NULL device pointers");
+    return BLDTT_EINVAL;
+  }
+  BL_TRY(validate(M, N, kernel, kappa, n, theta, N0, M0, precision));
+  bldtt_plan* p = new (std::nothrow) bldtt_plan;
+  if (!p) {
+    set_error("host allocation of the plan failed");
+    return BLDTT_ENOMEM;
+  }
+  p->M = M;
+  p->N = N;
+  p->kernel = kernel;
+  p->kappa = kernel == BLDTT_YUKAWA ? kappa : 0.0;
+  p->n = n;
+  p->P = n + 1;
+  p->np = p->P * p->P * p->P;
+  p->theta = theta;
+  p->N0 = N0;
+  p->M0 = M0;
+  p->precision = precision;
+  p->stream = static_cast<cudaStream_t>(cuda_stream);
+  int st = setup_impl(p, targets, sources, charges);
+  if (st != BLDTT_OK) {
+    release(p);
+    return st;
+  }
+  *plan = p;
+  return BLDTT_OK;
+}
+
+int bldtt_set_charges(bldtt_plan* p, const double* charges, void* cuda_stream) {
+  if (!p || !charges) {
+    set_error("plan and charges must be non-NULL");
+    return BLDTT_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  p->stream = s;
+  int* bad = nullptr;
+  BL_TRY(dalloc_n(&bad, 1, s));
+  BL_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  BL_TRY(permute_charges(p, charges, s));
+  BL_TRY(check_finite(p->q_tree, p->N, bad, s, p->setup_counter));
+  int h_bad = 0;
+  BL_CUDA(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BL_CUDA(cudaStreamSynchronize(s));
+  dfree(bad, s);
+  if (h_bad) {
+    set_error("a charge is not finite");
+    return BLDTT_EINVAL;
+  }
+  return BLDTT_OK;
+}
+
+int bldtt_compute(bldtt_plan* p, double* phi, void* cuda_stream) {
+  if (!p || !phi) {
+    set_error("plan and phi must be non-NULL");
+    return BLDTT_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  p->stream = s;
+  p->compute_counter.launches = 0;
+  BL_CUDA(cudaEventRecord(p->ev[0], s));
+  BL_CUDA(cudaMemsetAsync(p->phit, 0, (size_t)p->tt.nclusters * p->np * sizeof(double), s));
+  BL_CUDA(cudaMemsetAsync(p->phi_near, 0, (size_t)p->M * sizeof(double), s));
+  BL_TRY(upward_pass(p, s));
+  BL_TRY(build_pool(p, s));
+  BL_CUDA(cudaEventRecord(p->ev[1], s));
+  BL_TRY(run_interactions(p, s));
+  BL_CUDA(cudaEventRecord(p->ev[2], s));
+  BL_TRY(downward_pass(p, phi, s));
+  BL_CUDA(cudaEventRecord(p->ev[3], s));
+  p->have_compute_events = true;
+  return BLDTT_OK;
+}
+
+int bldtt_check_error(bldtt_plan* p) {
+  if (!p) return BLDTT_EINVAL;
+  BL_TRY(sync_plan(p));
+  return device_error(p);
+}
+
+int bldtt_stats(bldtt_plan* p, bldtt_stats_t* out) {
+  if (!p || !out) {
+    set_error("plan and out must be non-NULL");
+    return BLDTT_EINVAL;
+  }
+  BL_TRY(sync_plan(p));
+  std::memset(out, 0, sizeof(*out));
+  out->num_targets = p->M;
+  out->num_sources = p->N;
+  out->num_target_clusters = p->tt.nclusters;
+  out->num_source_clusters = p->st.nclusters;
+  out->num_target_leaves = p->tt.nleaves;
+  out->num_source_leaves = p->st.nleaves;
+  out->target_levels = p->tt.nlevels;
+  out->source_levels = p->st.nlevels;
+  for (int k = 0; k < 4; ++k) {
+    out->list_entries[k] = p->list_count[k];
+    out->interactions[k] = p->interactions[k];
+  }
+  out->executed_evaluations = p->executed_evaluations;
+  out->work_items = p->nitems;
+  out->interact_grid = p->interact_grid;
+  out->interact_threads = (kConsumerWarps + 1) * 32;
+  out->ms_tree = p->ms_tree;
+  out->ms_lists = p->ms_lists;
+  if (p->have_compute_events) {
+    out->ms_upward = elapsed(p->ev[0], p->ev[1]);
+    out->ms_interact = elapsed(p->ev[1], p->ev[2]);
+    out->ms_downward = elapsed(p->ev[2], p->ev[3]);
+    out->ms_compute = elapsed(p->ev[0], p->ev[3]);
+  }
+  out->launches_setup = p->setup_counter.launches;
+  out->launches_compute = p->compute_counter.launches;
+  return device_error(p);
+}
+
+void bldtt_destroy(bldtt_plan* p) { release(p); }
+
+int bldtt_tree_size(bldtt_plan* p, int which, int32_t* num_clusters, int32_t* num_levels) {
+  if (!p || (which != 0 && which != 1)) return BLDTT_EINVAL;
+  const Tree& T = which == 0 ? p->tt : p->st;
+  if (num_clusters) *num_clusters = T.nclusters;
+  if (num_levels) *num_levels = T.nlevels;
+  return BLDTT_OK;
+}
+
+int bldtt_export_tree(bldtt_plan* p, int which, int32_t* perm, int32_t* begin, int32_t* end,
+                      double* lo, double* hi, int32_t* parent, int32_t* level) {
+  if (!p || (which != 0 && which != 1)) {
+    set_error("bad plan or tree selector");
+    return BLDTT_EINVAL;
+  }
+  BL_TRY(sync_plan(p));
+  const Tree& T = which == 0 ? p->tt : p->st;
+  const size_t C = (size_t)T.nclusters;
+  if (perm) BL_CUDA(cudaMemcpy(perm, T.perm, (size_t)T.n * 4, cudaMemcpyDeviceToHost));
+  if (begin) BL_CUDA(cudaMemcpy(begin, T.begin, C * 4, cudaMemcpyDeviceToHost));
+  if (end) BL_CUDA(cudaMemcpy(end, T.end, C * 4, cudaMemcpyDeviceToHost));
+  if (parent) BL_CUDA(cudaMemcpy(parent, T.parent, C * 4, cudaMemcpyDeviceToHost));
+  if (level) BL_CUDA(cudaMemcpy(level, T.level, C * 4, cudaMemcpyDeviceToHost));
+  if (lo || hi) {
+    std::vector<double> box(C * 6);
+    BL_CUDA(cudaMemcpy(box.data(), T.box, C * 6 * sizeof(double), cudaMemcpyDeviceToHost));
+    for (size_t c = 0; c < C; ++c)
+      for (int d = 0; d < 3; ++d) {
+        if (lo) lo[d * C + c] = box[c * 6 + d];
+        if (hi) hi[d * C + c] = box[c * 6 + 3 + d];
+      }
+  }
+  return BLDTT_OK;
+}
+
+int bldtt_export_lists(bldtt_plan* p, int type, int32_t* target, int32_t* source, int64_t* count) {
+  if (!p || type < 0 || type > 3 || !count) {
+    set_error("bad plan, list type or count pointer");
+    return BLDTT_EINVAL;
+  }
+  int64_t need = p->list_count[type];
+  if (*count < need) {
+    *count = need;
+    set_error("list capacity %lld below the %lld entries", (long long)*count, (long long)need);
+    return BLDTT_EINVAL;
+  }
+  *count = need;
+  if (need == 0) return BLDTT_OK;
+  BL_TRY(sync_plan(p));
+  int32_t first = 0;
+  BL_CUDA(cudaMemcpy(&first, p->list_ptr + (int64_t)type * p->tt.nclusters, sizeof(int32_t),
+                     cudaMemcpyDeviceToHost));
+  if (target)
+    BL_CUDA(cudaMemcpy(target, p->list_tgt + first, need * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (source)
+    BL_CUDA(cudaMemcpy(source, p->list_src + first, need * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  return BLDTT_OK;
+}
+
+int bldtt_export_proxy_charges(bldtt_plan* p, double* qhat) {
+  if (!p || !qhat) return BLDTT_EINVAL;
+  BL_TRY(sync_plan(p));
+  BL_CUDA(cudaMemcpy(qhat, p->qhat, (size_t)p->st.nclusters * p->np * sizeof(double),
+                     cudaMemcpyDeviceToHost));
+  return BLDTT_OK;
+}
+
+int bldtt_export_proxy_potentials(bldtt_plan* p, double* phit) {
+  if (!p || !phit) return BLDTT_EINVAL;
+  BL_TRY(sync_plan(p));
+  BL_CUDA(cudaMemcpy(phit, p->phit, (size_t)p->tt.nclusters * p->np * sizeof(double),
+                     cudaMemcpyDeviceToHost));
+  return BLDTT_OK;
+}
+
+int bldtt_direct_sum(const double* targets, int64_t M, const double* sources, int64_t N,
+                     const double* charges, int kernel, double kappa, double* phi,
+                     void* cuda_stream) {
+  if (!targets || !sources || !charges || !phi || M < 0 || N < 0) {
+    set_error("direct sum: NULL pointer or negative size");
+    return BLDTT_EINVAL;
+  }
+  if (kernel != BLDTT_COULOMB && kernel != BLDTT_YUKAWA && kernel != BLDTT_TEST_POLY) {
+    set_error("unknown kernel %d", kernel);
+    return BLDTT_EINVAL;
+  }
+  if (M == 0) return BLDTT_OK;
+  return direct_sum(targets, M, sources, N, charges, kernel, kappa, phi,
+                    static_cast<cudaStream_t>(cuda_stream));
+}
+
+int bldtt_solve_host(const double* targets, int64_t M, const double* sources, int64_t N,
+                     const double* charges, int kernel, double kappa, int n, double theta, int N0,
+                     int M0, int precision, double* phi, bldtt_stats_t* stats) {
+  if (!targets || !sources || !charges || !phi) {
+    set_error("solve_host: NULL host pointer");
+    return BLDTT_EINVAL;
+  }
+  BL_TRY(validate(M, N, kernel, kappa, n, theta, N0, M0, precision));
+  cudaStream_t s = nullptr;
+  BL_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  const bool same = targets == sources && M == N;
+  double *dt = nullptr, *ds = nullptr, *dq = nullptr, *dphi = nullptr;
+  bldtt_plan* plan = nullptr;
+  int st = BLDTT_OK;
+  do {
+    if ((st = dalloc_n(&dt, (size_t)3 * M, s)) != BLDTT_OK) break;
+    if (!same && (st = dalloc_n(&ds, (size_t)3 * N, s)) != BLDTT_OK) break;
+    if ((st = dalloc_n(&dq, (size_t)N, s)) != BLDTT_OK) break;
+    if ((st = dalloc_n(&dphi, (size_t)M, s)) != BLDTT_OK) break;
+    if (same) ds = dt;
+    if (cudaMemcpyAsync(dt, targets, 3 * M * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        (!same && cudaMemcpyAsync(ds, sources, 3 * N * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess) ||
+        cudaMemcpyAsync(dq, charges, N * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      set_error("solve_host: host-to-device copy failed");
+      st = BLDTT_ECUDA;
+      break;
+    }
+    if ((st = bldtt_setup(&plan, dt, M, ds, N, dq, kernel, kappa, n, theta, N0, M0, precision, s)) != BLDTT_OK) break;
+    if ((st = bldtt_compute(plan, dphi, s)) != BLDTT_OK) break;
+    if (cudaMemcpyAsync(phi, dphi, M * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+      set_error("solve_host: device-to-host copy failed");
+      st = BLDTT_ECUDA;
+      break;
+    }
+    if (stats) st = bldtt_stats(plan, stats);
+    else st = bldtt_check_error(plan);
+  } while (0);
+  bldtt_destroy(plan);
+  dfree(dt, s);
+  if (!same) dfree(ds, s);
+  dfree(dq, s);
+  dfree(dphi, s);
+  cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+  cudaGetLastError();
+  return st;
+}
+
+}  // extern "C"

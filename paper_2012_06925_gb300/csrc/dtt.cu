@@ -1,0 +1,387 @@
+// Dual tree traversal (Sec. 2.6, Algorithm 2) as a breadth-first pair
+// frontier, the four interaction lists of every target cluster (Sec. 3.1),
+// and the work items the interaction kernel drains.
+//
+// One pass classifies every (C_t, C_s) pair of the frontier: well separated
+// pairs (r_t + r_s < theta R) become a CC, CP, PC or PP list entry according
+// to |C_t|, |C_s| versus n_p; non-separated leaf pairs become PP entries; the
+// rest are replaced by the pairs of the split side's children (Alg. 2,
+// lines 11-17).  Compaction uses prefix sums, so the entry order, and hence
+// every later summation order, is deterministic.
+#include "internal.cuh"
+
+namespace bldtt {
+
+struct TreeView {
+  const int32_t *begin, *end, *nchild, *first_child;
+  const double *center, *radius;
+};
+
+static TreeView view(const Tree& T) {
+  return TreeView{T.begin, T.end, T.nchild, T.first_child, T.center, T.radius};
+}
+
+enum PairAction : int8_t { kActPP = 0, kActPC = 1, kActCP = 2, kActCC = 3, kActSplitT = 4, kActSplitS = 5 };
+
+__global__ void k_dtt_classify(const int2* __restrict__ pairs, int32_t F, TreeView tt, TreeView st,
+                               int64_t np, double theta, int32_t* __restrict__ nkids,
+                               int32_t* __restrict__ isentry, int8_t* __restrict__ action) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= F) return;
+  int t = pairs[i].x, s = pairs[i].y;
+  const double* ct = tt.center + (int64_t)t * 3;
+  const double* cs = st.center + (int64_t)s * 3;
+  double dx = __dsub_rn(ct[0], cs[0]), dy = __dsub_rn(ct[1], cs[1]), dz = __dsub_rn(ct[2], cs[2]);
+  double R = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+  bool sep = __dadd_rn(tt.radius[t], st.radius[s]) < __dmul_rn(theta, R);
+  int64_t cnt_t = tt.end[t] - tt.begin[t], cnt_s = st.end[s] - st.begin[s];
+  int8_t a;
+  int32_t kids = 0;
+  if (sep) {
+    bool big_t = cnt_t > np, big_s = cnt_s > np;
+    a = big_t ? (big_s ? kActCC : kActCP) : (big_s ? kActPC : kActPP);
+  } else {
+    bool leaf_t = tt.nchild[t] == 0, leaf_s = st.nchild[s] == 0;
+    if (leaf_t && leaf_s) a = kActPP;
+    else if (leaf_s) a = kActSplitT;
+    else if (leaf_t) a = kActSplitS;
+    else a = cnt_s < cnt_t ? kActSplitT : kActSplitS;
+    if (a == kActSplitT) kids = tt.nchild[t];
+    if (a == kActSplitS) kids = st.nchild[s];
+  }
+  action[i] = a;
+  nkids[i] = kids;
+  isentry[i] = a < kActSplitT ? 1 : 0;
+}
+
+__global__ void k_dtt_emit(const int2* __restrict__ pairs, int32_t F, const int8_t* __restrict__ action,
+                           const int32_t* __restrict__ koff, const int32_t* __restrict__ eoff,
+                           TreeView tt, TreeView st, int2* __restrict__ next, int32_t* __restrict__ ent_t,
+                           int32_t* __restrict__ ent_s, uint32_t* __restrict__ ent_key, int64_t ebase,
+                           int32_t nct) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= F) return;
+  int t = pairs[i].x, s = pairs[i].y;
+  int8_t a = action[i];
+  if (a < kActSplitT) {
+    int64_t e = ebase + eoff[i];
+    ent_t[e] = t;
+    ent_s[e] = s;
+    ent_key[e] = (uint32_t)a * (uint32_t)nct + (uint32_t)t;
+  } else if (a == kActSplitT) {
+    int32_t fc = tt.first_child[t], k = tt.nchild[t];
+    for (int j = 0; j < k; ++j) next[koff[i] + j] = make_int2(fc + j, s);
+  } else {
+    int32_t fc = st.first_child[s], k = st.nchild[s];
+    for (int j = 0; j < k; ++j) next[koff[i] + j] = make_int2(t, fc + j);
+  }
+}
+
+__global__ void k_iota(int32_t* v, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = (int32_t)i;
+}
+
+__global__ void k_gather_i32(const int32_t* __restrict__ src, const int32_t* __restrict__ idx,
+                             int32_t* __restrict__ dst, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[idx[i]];
+}
+
+__global__ void k_key_hist(const uint32_t* __restrict__ keys, int64_t n, int32_t* __restrict__ cnt) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) atomicAdd(&cnt[keys[i]], 1);
+}
+
+// Kernel evaluations per type (Eqs. (6), (8), (12), (15)); integer sums, exact.
+__global__ void k_count_evals(const int32_t* __restrict__ et, const int32_t* __restrict__ es,
+                              const uint32_t* __restrict__ key, int64_t n, int32_t nct,
+                              TreeView tt, TreeView st, int64_t np,
+                              unsigned long long* __restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int type = (int)(key[i] / (uint32_t)nct);
+  int64_t ct = tt.end[et[i]] - tt.begin[et[i]], cs = st.end[es[i]] - st.begin[es[i]];
+  int64_t v = type == 0 ? ct * cs : type == 1 ? ct * np : type == 2 ? np * cs : np * np;
+  atomicAdd(&out[type], (unsigned long long)v);
+}
+
+static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+int build_lists(bldtt_plan* p, cudaStream_t s) {
+  bldtt::Counters& cnt = p->setup_counter;
+  const TreeView tt = view(p->tt), st = view(p->st);
+  const int32_t nct = p->tt.nclusters;
+  size_t fcap = 1024, ncap = 1024, ecap = 4096;
+  int2 *front = nullptr, *next = nullptr;
+  int32_t *ent_t = nullptr, *ent_s = nullptr;
+  uint32_t* ent_key = nullptr;
+  BL_TRY(dalloc_n(&front, fcap, s));
+  BL_TRY(dalloc_n(&next, ncap, s));
+  BL_TRY(dalloc_n(&ent_t, ecap, s));
+  BL_TRY(dalloc_n(&ent_s, ecap, s));
+  BL_TRY(dalloc_n(&ent_key, ecap, s));
+  int2 root = make_int2(0, 0);
+  BL_CUDA(cudaMemcpyAsync(front, &root, sizeof(int2), cudaMemcpyHostToDevice, s));
+  int32_t F = 1;
+  int64_t E = 0;
+  while (F > 0) {
+    int32_t *nkids = nullptr, *isentry = nullptr, *koff = nullptr, *eoff = nullptr;
+    int8_t* action = nullptr;
+    BL_TRY(dalloc_n(&nkids, F, s));
+    BL_TRY(dalloc_n(&isentry, F, s));
+    BL_TRY(dalloc_n(&koff, F, s));
+    BL_TRY(dalloc_n(&eoff, F, s));
+    BL_TRY(dalloc_n(&action, F, s));
+    k_dtt_classify<<<nblk(F, 256), 256, 0, s>>>(front, F, tt, st, p->np, p->theta, nkids, isentry,
+                                                action);
+    BL_LAUNCHED(cnt.launches);
+    int32_t K = 0, En = 0;
+    BL_TRY(scan_exclusive(nkids, koff, F, &K, s, cnt));
+    BL_TRY(scan_exclusive(isentry, eoff, F, &En, s, cnt));
+    if ((size_t)K > ncap) {
+      size_t c = ncap;
+      BL_TRY(dgrow(&next, &c, (size_t)K, 0, s));
+      ncap = c;
+    }
+    if ((size_t)(E + En) > ecap) {
+      size_t c1 = ecap, c2 = ecap, c3 = ecap;
+      BL_TRY(dgrow(&ent_t, &c1, (size_t)(E + En), (size_t)E, s));
+      BL_TRY(dgrow(&ent_s, &c2, (size_t)(E + En), (size_t)E, s));
+      int32_t* kk = reinterpret_cast<int32_t*>(ent_key);
+      BL_TRY(dgrow(&kk, &c3, (size_t)(E + En), (size_t)E, s));
+      ent_key = reinterpret_cast<uint32_t*>(kk);
+      ecap = c1;
+    }
+    k_dtt_emit<<<nblk(F, 256), 256, 0, s>>>(front, F, action, koff, eoff, tt, st, next, ent_t, ent_s,
+                                            ent_key, E, nct);
+    BL_LAUNCHED(cnt.launches);
+    dfree(nkids, s); dfree(isentry, s); dfree(koff, s); dfree(eoff, s); dfree(action, s);
+    E += En;
+    int2* tmp = front; front = next; next = tmp;
+    size_t tc = fcap; fcap = ncap; ncap = tc;
+    F = K;
+  }
+  dfree(front, s);
+  dfree(next, s);
+
+  // Sort entries by (type, target cluster); the traversal order breaks ties.
+  p->nentries = E;
+  int key_bits = 1;
+  while ((1ull << key_bits) < 4ull * (unsigned long long)nct) ++key_bits;
+  int32_t* order = nullptr;
+  BL_TRY(dalloc_n(&order, E, s));
+  if (E > 0) {
+    k_iota<<<nblk(E, 256), 256, 0, s>>>(order, E);
+    BL_LAUNCHED(cnt.launches);
+  }
+  BL_TRY(radix_sort_pairs(ent_key, order, E, key_bits, s, cnt));
+  BL_TRY(dalloc_n(&p->list_src, E, s));
+  BL_TRY(dalloc_n(&p->list_tgt, E, s));
+  if (E > 0) {
+    k_gather_i32<<<nblk(E, 256), 256, 0, s>>>(ent_s, order, p->list_src, E);
+    BL_LAUNCHED(cnt.launches);
+    k_gather_i32<<<nblk(E, 256), 256, 0, s>>>(ent_t, order, p->list_tgt, E);
+    BL_LAUNCHED(cnt.launches);
+  }
+  int64_t nkeys = 4 * (int64_t)nct;
+  int32_t* hist = nullptr;
+  BL_TRY(dalloc_n(&hist, nkeys, s));
+  BL_TRY(dalloc_n(&p->list_ptr, nkeys + 1, s));
+  BL_CUDA(cudaMemsetAsync(hist, 0, nkeys * sizeof(int32_t), s));
+  if (E > 0) {
+    k_key_hist<<<nblk(E, 256), 256, 0, s>>>(ent_key, E, hist);
+    BL_LAUNCHED(cnt.launches);
+  }
+  int32_t total = 0;
+  BL_TRY(scan_exclusive(hist, p->list_ptr, nkeys, &total, s, cnt));
+  BL_CUDA(cudaMemcpyAsync(p->list_ptr + nkeys, &total, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+
+  unsigned long long* evals = nullptr;
+  BL_TRY(dalloc_n(&evals, 4, s));
+  BL_CUDA(cudaMemsetAsync(evals, 0, 4 * sizeof(unsigned long long), s));
+  if (E > 0) {
+    k_count_evals<<<nblk(E, 256), 256, 0, s>>>(p->list_tgt, p->list_src, ent_key, E, nct, tt, st,
+                                               p->np, evals);
+    BL_LAUNCHED(cnt.launches);
+  }
+  unsigned long long h_evals[4];
+  int32_t h_ptr[5];
+  for (int k = 0; k < 5; ++k)
+    BL_CUDA(cudaMemcpyAsync(&h_ptr[k], p->list_ptr + (int64_t)k * nct, sizeof(int32_t),
+                            cudaMemcpyDeviceToHost, s));
+  BL_CUDA(cudaMemcpyAsync(h_evals, evals, sizeof(h_evals), cudaMemcpyDeviceToHost, s));
+  BL_CUDA(cudaStreamSynchronize(s));
+  for (int k = 0; k < 4; ++k) {
+    p->list_count[k] = h_ptr[k + 1] - h_ptr[k];
+    p->interactions[k] = (double)h_evals[k];
+  }
+  if (total != E) {
+    set_error("interaction list CSR holds %d entries, traversal produced %lld", total, (long long)E);
+    return BLDTT_EINTERNAL;
+  }
+  dfree(evals, s); dfree(hist, s); dfree(order, s);
+  dfree(ent_t, s); dfree(ent_s, s); dfree(ent_key, s);
+  return BLDTT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Work items
+// ---------------------------------------------------------------------------
+
+__global__ void k_leaf_padded(int32_t nleaves, const int32_t* __restrict__ leaf_ids,
+                              const int32_t* __restrict__ begin, const int32_t* __restrict__ end,
+                              int32_t* __restrict__ padded) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nleaves) return;
+  int c = leaf_ids[i];
+  int32_t m = end[c] - begin[c];
+  padded[i] = (m + kChunk - 1) / kChunk * kChunk;
+}
+
+struct ListView {
+  const int32_t *ptr, *src;
+  int32_t nct;
+  const int32_t *s_leaf_first, *s_leaf_last, *pad_prefix;
+  int32_t np_pad;
+};
+
+// Chunks a target cluster's own lists of two types contribute.
+__device__ __forceinline__ int64_t list_chunks(const ListView& L, int type_particles, int type_proxies,
+                                               int32_t c) {
+  int64_t ch = 0;
+  int64_t k0 = (int64_t)type_particles * L.nct + c;
+  for (int32_t e = L.ptr[k0]; e < L.ptr[k0 + 1]; ++e) {
+    int32_t s = L.src[e];
+    ch += (L.pad_prefix[L.s_leaf_last[s]] - L.pad_prefix[L.s_leaf_first[s]]) / kChunk;
+  }
+  int64_t k1 = (int64_t)type_proxies * L.nct + c;
+  ch += (int64_t)(L.ptr[k1 + 1] - L.ptr[k1]) * (L.np_pad / kChunk);
+  return ch;
+}
+
+__global__ void k_item_count(int32_t nct, ListView L, const int32_t* __restrict__ parent,
+                             const int32_t* __restrict__ nchild, const int32_t* __restrict__ begin,
+                             const int32_t* __restrict__ end, int32_t np,
+                             int32_t* __restrict__ nitems, int64_t* __restrict__ cost_part,
+                             int64_t* __restrict__ cost_prox) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nct) return;
+  int64_t cp = 0;
+  if (nchild[c] == 0)   // PP + PC of the leaf and of all its ancestors (Sec. 2.7 chain)
+    for (int32_t a = c; a >= 0; a = parent[a]) cp += list_chunks(L, 0, 1, a);
+  int64_t cq = list_chunks(L, 2, 3, c);   // CP + CC of the cluster itself
+  int32_t tp = cp > 0 ? (end[c] - begin[c] + kTile - 1) / kTile : 0;
+  int32_t tq = cq > 0 ? (np + kTile - 1) / kTile : 0;
+  nitems[c] = tp + tq;
+  cost_part[c] = cp;
+  cost_prox[c] = cq;
+}
+
+__global__ void k_item_fill(int32_t nct, const int32_t* __restrict__ off,
+                            const int64_t* __restrict__ cost_part, const int64_t* __restrict__ cost_prox,
+                            const int32_t* __restrict__ begin, const int32_t* __restrict__ end,
+                            int32_t np, int4* __restrict__ items, uint32_t* __restrict__ keys,
+                            int32_t* __restrict__ vals, unsigned long long* __restrict__ executed) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nct) return;
+  int32_t o = off[c];
+  const uint32_t kKeyMax = (1u << 24) - 1u;
+  unsigned long long ex = 0;
+  if (cost_part[c] > 0) {
+    uint32_t k = kKeyMax - (uint32_t)min((int64_t)kKeyMax, cost_part[c]);
+    for (int32_t r = begin[c]; r < end[c]; r += kTile) {
+      items[o] = make_int4(c, r, min(kTile, end[c] - r), kItemParticles);
+      keys[o] = k;
+      vals[o] = o;
+      ++o;
+      ex += (unsigned long long)cost_part[c];
+    }
+  }
+  if (cost_prox[c] > 0) {
+    uint32_t k = kKeyMax - (uint32_t)min((int64_t)kKeyMax, cost_prox[c]);
+    for (int32_t r = 0; r < np; r += kTile) {
+      items[o] = make_int4(c, r, min(kTile, np - r), kItemProxies);
+      keys[o] = k;
+      vals[o] = o;
+      ++o;
+      ex += (unsigned long long)cost_prox[c];
+    }
+  }
+  if (ex) atomicAdd(executed, ex * (unsigned long long)kChunk * (unsigned long long)kTile);
+}
+
+__global__ void k_gather_items(const int4* __restrict__ src, const int32_t* __restrict__ idx,
+                               int4* __restrict__ dst, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[idx[i]];
+}
+
+int build_work_items(bldtt_plan* p, cudaStream_t s) {
+  bldtt::Counters& cnt = p->setup_counter;
+  const Tree& st = p->st;
+  const Tree& tt = p->tt;
+  // Source pool layout: padded leaves (leaf order), then padded proxy blocks.
+  int32_t* padded = nullptr;
+  BL_TRY(dalloc_n(&padded, st.nleaves, s));
+  BL_TRY(dalloc_n(&p->pad_prefix, (size_t)st.nleaves + 1, s));
+  k_leaf_padded<<<nblk(st.nleaves, 256), 256, 0, s>>>(st.nleaves, st.leaf_ids, st.begin, st.end,
+                                                      padded);
+  BL_LAUNCHED(cnt.launches);
+  int64_t bound = (int64_t)st.n + (int64_t)st.nleaves * kChunk;
+  if (bound >= (int64_t)INT32_MAX) {
+    set_error("source pool of %lld entries exceeds the int32 index range", (long long)bound);
+    return BLDTT_EINVAL;
+  }
+  int32_t total = 0;
+  BL_TRY(scan_exclusive(padded, p->pad_prefix, st.nleaves, &total, s, cnt));
+  BL_CUDA(cudaMemcpyAsync(p->pad_prefix + st.nleaves, &total, sizeof(int32_t),
+                          cudaMemcpyHostToDevice, s));
+  dfree(padded, s);
+  p->np_pad = (p->np + kChunk - 1) / kChunk * kChunk;
+  p->pool_particles = total;
+  p->pool_len = (int64_t)total + (int64_t)st.nclusters * p->np_pad;
+
+  const int32_t nct = tt.nclusters;
+  ListView L{p->list_ptr, p->list_src, nct, st.leaf_first, st.leaf_last, p->pad_prefix, p->np_pad};
+  int32_t *nitems = nullptr, *off = nullptr;
+  int64_t *cost_part = nullptr, *cost_prox = nullptr;
+  BL_TRY(dalloc_n(&nitems, nct, s));
+  BL_TRY(dalloc_n(&off, nct, s));
+  BL_TRY(dalloc_n(&cost_part, nct, s));
+  BL_TRY(dalloc_n(&cost_prox, nct, s));
+  k_item_count<<<nblk(nct, 128), 128, 0, s>>>(nct, L, tt.parent, tt.nchild, tt.begin, tt.end, p->np,
+                                              nitems, cost_part, cost_prox);
+  BL_LAUNCHED(cnt.launches);
+  int32_t ni = 0;
+  BL_TRY(scan_exclusive(nitems, off, nct, &ni, s, cnt));
+  p->nitems = ni;
+  int4* items = nullptr;
+  uint32_t* keys = nullptr;
+  int32_t* vals = nullptr;
+  unsigned long long* executed = nullptr;
+  BL_TRY(dalloc_n(&items, ni, s));
+  BL_TRY(dalloc_n(&keys, ni, s));
+  BL_TRY(dalloc_n(&vals, ni, s));
+  BL_TRY(dalloc_n(&executed, 1, s));
+  BL_TRY(dalloc_n(&p->items, ni, s));
+  BL_CUDA(cudaMemsetAsync(executed, 0, sizeof(unsigned long long), s));
+  k_item_fill<<<nblk(nct, 128), 128, 0, s>>>(nct, off, cost_part, cost_prox, tt.begin, tt.end, p->np,
+                                             items, keys, vals, executed);
+  BL_LAUNCHED(cnt.launches);
+  // Longest items first (stable), so the persistent kernel's tail is short.
+  BL_TRY(radix_sort_pairs(keys, vals, ni, 24, s, cnt));
+  if (ni > 0) {
+    k_gather_items<<<nblk(ni, 256), 256, 0, s>>>(items, vals, p->items, ni);
+    BL_LAUNCHED(cnt.launches);
+  }
+  unsigned long long h_exec = 0;
+  BL_CUDA(cudaMemcpyAsync(&h_exec, executed, sizeof(h_exec), cudaMemcpyDeviceToHost, s));
+  BL_CUDA(cudaStreamSynchronize(s));
+  p->executed_evaluations = (double)h_exec;
+  dfree(items, s); dfree(keys, s); dfree(vals, s); dfree(executed, s);
+  dfree(nitems, s); dfree(off, s); dfree(cost_part, s); dfree(cost_prox, s);
+  return BLDTT_OK;
+}
+
+}  // namespace bldtt

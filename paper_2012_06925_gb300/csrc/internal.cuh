@@ -1,0 +1,200 @@
+// Internal declarations of the GB300 BLDTT library.
+//
+// Layout summary (all device memory, one plan per problem):
+//  - Each tree stores its particles permuted into tree order (FP64 x, y, z
+//    arrays and perm[] back to input order) so every cluster is a contiguous
+//    range [begin, end).  Clusters are numbered level by level; the children
+//    of a cluster are consecutive.  Boxes are 6 doubles per cluster
+//    (lo x,y,z, hi x,y,z); proxy points are kept as three 1D arrays of n+1
+//    Chebyshev points per cluster (Sec. 2.1: the 3D grid is their tensor
+//    product).
+//  - The four interaction lists (Sec. 3.1) are one CSR keyed by
+//    type * num_target_clusters + target cluster.
+//  - The "source pool" is what the interaction kernel streams: every source
+//    leaf's particles followed by every source cluster's proxy points, each
+//    segment padded to a multiple of kChunk entries (charge 0) so that every
+//    chunk is one aligned bulk copy.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bldtt.h"
+
+namespace bldtt {
+
+constexpr int kMaxDegree = 16;                 // n <= 16  ->  P = n + 1 <= 17
+constexpr int kMaxP = kMaxDegree + 1;
+constexpr int kChunk = 64;                     // sources per staged chunk
+constexpr int kConsumerWarps = 4;              // interaction kernel: consumer warps per CTA
+constexpr int kTargetsPerThread = 2;           // interaction kernel: targets per consumer thread
+constexpr int kTile = kConsumerWarps * 32 * kTargetsPerThread;   // targets per work item
+constexpr int kStages = 6;                     // depth of the shared-memory ring
+
+enum ItemKind { kItemParticles = 0, kItemProxies = 1 };
+
+// Error flag codes written by kernels into plan->dev_err.
+enum DevErr { kDevErrNone = 0, kDevErrTimeout = 1, kDevErrBounds = 2 };
+
+void set_error(const char* fmt, ...);
+
+#define BL_CUDA(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      ::bldtt::set_error("%s:%d: %s failed: %s", __FILE__, __LINE__, #call,                \
+                         cudaGetErrorString(e_));                                          \
+      return e_ == cudaErrorMemoryAllocation ? BLDTT_ENOMEM : BLDTT_ECUDA;                 \
+    }                                                                                      \
+  } while (0)
+
+#define BL_LAUNCHED(counter)                                                               \
+  do {                                                                                     \
+    cudaError_t e_ = cudaGetLastError();                                                   \
+    if (e_ != cudaSuccess) {                                                               \
+      ::bldtt::set_error("%s:%d: kernel launch failed: %s", __FILE__, __LINE__,            \
+                         cudaGetErrorString(e_));                                          \
+      return BLDTT_ECUDA;                                                                  \
+    }                                                                                      \
+    ++(counter);                                                                           \
+  } while (0)
+
+#define BL_TRY(expr)                                                                       \
+  do {                                                                                     \
+    int s_ = (expr);                                                                       \
+    if (s_ != BLDTT_OK) return s_;                                                         \
+  } while (0)
+
+// Stream-ordered device allocation helpers.
+int dalloc(void** p, size_t bytes, cudaStream_t s);
+template <class T>
+inline int dalloc_n(T** p, size_t n, cudaStream_t s) {
+  return dalloc(reinterpret_cast<void**>(p), n * sizeof(T) + (n == 0 ? sizeof(T) : 0), s);
+}
+void dfree(void* p, cudaStream_t s);
+template <class T>
+inline void dfree_ptr(T*& p, cudaStream_t s) {
+  dfree(reinterpret_cast<void*>(p), s);
+  p = nullptr;
+}
+// Grow a device array to hold at least `need` elements, keeping `keep` of them.
+template <class T>
+int dgrow(T** p, size_t* cap, size_t need, size_t keep, cudaStream_t s);
+
+struct Tree {
+  int32_t n = 0;                      // particles
+  int32_t nclusters = 0, nlevels = 0, nleaves = 0;
+  size_t cap = 0;                     // allocated cluster capacity
+  double *x = nullptr, *y = nullptr, *z = nullptr;   // tree order
+  int32_t* perm = nullptr;            // tree position -> input index
+  int32_t *begin = nullptr, *end = nullptr, *parent = nullptr;
+  int32_t *first_child = nullptr, *nchild = nullptr, *level = nullptr;
+  double* box = nullptr;              // [C][6]: lo x,y,z, hi x,y,z
+  double* center = nullptr;           // [C][3]
+  double* radius = nullptr;           // [C]
+  double* nodes = nullptr;            // [C][3][P]
+  int32_t* leaf_ids = nullptr;        // leaf order (by begin) -> cluster
+  int32_t *leaf_first = nullptr, *leaf_last = nullptr;   // per cluster: leaf-order range
+  std::vector<int32_t> level_start;   // host: level l holds clusters [ls[l], ls[l+1])
+  std::vector<int32_t> h_nchild;      // host copy (used to pick upward/downward clusters)
+};
+
+struct Counters {
+  int64_t launches = 0;
+};
+
+}  // namespace bldtt
+
+struct bldtt_plan {
+  int64_t M = 0, N = 0;
+  int kernel = 0;
+  double kappa = 0.0;
+  int n = 0, P = 0, np = 0;
+  double theta = 0.0;
+  int N0 = 0, M0 = 0;
+  int precision = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;      // stream of the last call (for synchronisation)
+
+  bldtt::Tree tt, st;                 // target and source trees
+  double* q_tree = nullptr;           // [N] charges, source tree order
+
+  // Interaction lists: CSR over key = type * nct + t.
+  int32_t* list_ptr = nullptr;        // [4*nct + 1]
+  int32_t* list_src = nullptr;        // [E]
+  int32_t* list_tgt = nullptr;        // [E]
+  int64_t nentries = 0;
+  int64_t list_count[4] = {0, 0, 0, 0};
+  double interactions[4] = {0, 0, 0, 0};
+
+  // Source pool.
+  int np_pad = 0;                     // proxies per cluster rounded up to kChunk
+  int32_t* pad_prefix = nullptr;      // [nleaves_s + 1] pool offset of each source leaf
+  int64_t pool_particles = 0, pool_len = 0;
+  void* pool = nullptr;               // float4 (FP32_BULK) or double4 (FP64) entries
+
+  // Work items of the interaction kernel, sorted by decreasing cost.
+  int4* items = nullptr;              // {cluster, row_begin, row_count, kind}
+  int32_t nitems = 0;
+  int32_t* item_counter = nullptr;
+  double executed_evaluations = 0.0;
+  int interact_grid = 0;
+
+  // Compute-phase arrays.
+  double* qhat = nullptr;             // [Cs][np] proxy charges
+  double* phit = nullptr;             // [Ct][np] proxy potentials
+  double* phi_near = nullptr;         // [M] PP + PC part of phi, target tree order
+  int* dev_err = nullptr;
+
+  // Statistics.
+  bldtt::Counters setup_counter, compute_counter;
+  float ms_tree = 0.f, ms_lists = 0.f;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool have_compute_events = false;
+};
+
+namespace bldtt {
+
+// ---- primitives (prims.cu) ----
+// Exclusive prefix sum of n int32 values; *total_host (if not NULL) receives
+// the sum (the call then synchronises the stream).
+int scan_exclusive(const int32_t* in, int32_t* out, int64_t n, int32_t* total_host,
+                   cudaStream_t s, Counters& c);
+// Stable ascending sort of (key, value) pairs on the low `bits` bits of key.
+int radix_sort_pairs(uint32_t* keys, int32_t* vals, int64_t n, int bits, cudaStream_t s,
+                     Counters& c);
+// Component-wise min/max of three coordinate arrays; writes 6 doubles to
+// out_dev (lo x,y,z, hi x,y,z) and raises *bad_dev if any value is not finite.
+int bbox_reduce(const double* x, const double* y, const double* z, int64_t n, double* out_dev,
+                int* bad_dev, cudaStream_t s, Counters& c);
+// Raise *bad_dev if any of n doubles is not finite.
+int check_finite(const double* v, int64_t n, int* bad_dev, cudaStream_t s, Counters& c);
+
+// ---- trees (tree.cu) ----
+int build_tree(Tree& T, const double* coords_user, int32_t n, int32_t max_leaf, int degree,
+               int* bad_dev, cudaStream_t s, Counters& c);
+void free_tree(Tree& T, cudaStream_t s);
+
+// ---- traversal, lists and work items (dtt.cu) ----
+int build_lists(bldtt_plan* p, cudaStream_t s);
+int build_work_items(bldtt_plan* p, cudaStream_t s);
+
+// ---- passes (passes.cu) ----
+int permute_charges(bldtt_plan* p, const double* charges_user, cudaStream_t s);
+int upward_pass(bldtt_plan* p, cudaStream_t s);
+int build_pool(bldtt_plan* p, cudaStream_t s);
+int downward_pass(bldtt_plan* p, double* phi_user, cudaStream_t s);
+int configure_pass_kernels();
+
+// ---- interactions (interact.cu) ----
+int interaction_grid(bldtt_plan* p, int* grid);
+int run_interactions(bldtt_plan* p, cudaStream_t s);
+
+// ---- direct sum (direct.cu) ----
+int direct_sum(const double* targets, int64_t M, const double* sources, int64_t N,
+               const double* charges, int kernel, double kappa, double* phi, cudaStream_t s);
+
+}  // namespace bldtt

@@ -1,0 +1,414 @@
+// Upward pass (Sec. 2.5, App. B), source-pool construction, and downward
+// pass (Sec. 2.7, App. C).
+//
+// The Lagrange basis is always evaluated in FP64 with the coincident-point
+// guard of the second barycentric form (Sec. 2.1, Eq. (3)); in FP32_BULK mode
+// the contractions that follow (leaf proxy charges and the leaf interpolation
+// to particles) run in FP32 over short runs that are summed in FP64.
+#include <type_traits>
+
+#include "internal.cuh"
+
+namespace bldtt {
+
+// Barycentric weight of Chebyshev points of the 2nd kind, Eq. (5).
+__device__ __forceinline__ double bary_weight(int k, int n) {
+  double w = (k == 0 || k == n) ? 0.5 : 1.0;
+  return (k & 1) ? -w : w;
+}
+
+// L_k(x), k = 0..n, of the 1D grid `nodes` (Eq. (3)), written to out[k*stride].
+// If x - t_k == 0 for some k, the result is one-hot at the first such k.
+template <typename T>
+__device__ __forceinline__ void basis_1d(double x, const double* nodes, int n, T* out, int stride) {
+  double r[kMaxP];
+  int hit = -1;
+  double sum = 0.0;
+#pragma unroll
+  for (int k = 0; k < kMaxP; ++k) {
+    if (k <= n) {
+      double d = x - nodes[k];
+      if (d == 0.0 && hit < 0) hit = k;
+      r[k] = d == 0.0 ? 0.0 : bary_weight(k, n) / d;
+      sum += r[k];
+    }
+  }
+  double inv = 1.0 / sum;
+#pragma unroll
+  for (int k = 0; k < kMaxP; ++k) {
+    if (k <= n) out[k * stride] = (T)(hit >= 0 ? (k == hit ? 1.0 : 0.0) : r[k] * inv);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Charges into source tree order
+// ---------------------------------------------------------------------------
+__global__ void k_permute(const double* __restrict__ src, const int32_t* __restrict__ perm, int64_t n,
+                          double* __restrict__ dst) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[perm[i]];
+}
+
+static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+int permute_charges(bldtt_plan* p, const double* charges, cudaStream_t s) {
+  k_permute<<<nblk(p->N, 256), 256, 0, s>>>(charges, p->st.perm, p->N, p->q_tree);
+  BL_LAUNCHED(p->setup_counter.launches);
+  return BLDTT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Upward pass
+// ---------------------------------------------------------------------------
+constexpr int kUpThreads = 256;
+constexpr int kUpChunk = 64;
+constexpr int kUpStride = kUpChunk + 1;        // odd row stride: no bank conflicts
+constexpr int kMaxOutPerThread = (kMaxP * kMaxP * kMaxP + kUpThreads - 1) / kUpThreads;
+
+// Eq. (9) for every source leaf: qhat_k = sum_j L_k1(y_j1) L_k2(y_j2) L_k3(y_j3) q_j.
+template <bool F32>
+__global__ void __launch_bounds__(kUpThreads) k_up_leaf(
+    const int32_t* __restrict__ leaf_ids, const int32_t* __restrict__ begin,
+    const int32_t* __restrict__ end, const double* __restrict__ x, const double* __restrict__ y,
+    const double* __restrict__ z, const double* __restrict__ q, const double* __restrict__ nodes,
+    int n, double* __restrict__ qhat) {
+  using T = typename std::conditional<F32, float, double>::type;
+  __shared__ double snodes[3][kMaxP];
+  __shared__ T sB[3][kMaxP][kUpStride];
+  __shared__ T sq[kUpChunk];
+  const int P = n + 1, np = P * P * P;
+  const int c = leaf_ids[blockIdx.x];
+  const int32_t b = begin[c], e = end[c];
+  if (threadIdx.x < 3 * P) snodes[threadIdx.x / P][threadIdx.x % P] = nodes[(int64_t)c * 3 * P + threadIdx.x];
+  double acc[kMaxOutPerThread];
+#pragma unroll
+  for (int r = 0; r < kMaxOutPerThread; ++r) acc[r] = 0.0;
+  const double* coord[3] = {x, y, z};
+  __syncthreads();
+  for (int32_t base = b; base < e; base += kUpChunk) {
+    const int cnt = min(kUpChunk, e - base);
+    for (int task = threadIdx.x; task < 3 * kUpChunk; task += kUpThreads) {
+      int d = task / kUpChunk, j = task % kUpChunk;
+      if (j < cnt) {
+        basis_1d<T>(coord[d][base + j], snodes[d], n, &sB[d][0][j], kUpStride);
+      } else {
+        for (int k = 0; k < P; ++k) sB[d][k][j] = (T)0;
+      }
+    }
+    if (threadIdx.x < kUpChunk) sq[threadIdx.x] = threadIdx.x < cnt ? (T)q[base + threadIdx.x] : (T)0;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kMaxOutPerThread; ++r) {
+      int o = threadIdx.x + r * kUpThreads;
+      if (o < np) {
+        int k1 = o / (P * P), k2 = (o / P) % P, k3 = o % P;
+        T sacc = (T)0;
+        for (int j = 0; j < cnt; ++j) sacc += sB[0][k1][j] * sB[1][k2][j] * (sB[2][k3][j] * sq[j]);
+        acc[r] += (double)sacc;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < kMaxOutPerThread; ++r) {
+    int o = threadIdx.x + r * kUpThreads;
+    if (o < np) qhat[(int64_t)c * np + o] = acc[r];
+  }
+}
+
+// Shared layout of the parent/child kernels (dynamic shared memory).
+struct TransferSmem {
+  double* pn;   // [3][P] parent nodes
+  double* cn;   // [3][P] child nodes
+  double* U;    // [3][P][P]  U[d][k][k'] = L^par_k(t^child_k')
+  double* A;    // [np]
+  double* B;    // [np]
+};
+__device__ __forceinline__ TransferSmem carve(double* base, int P) {
+  TransferSmem t;
+  t.pn = base;
+  t.cn = t.pn + 3 * P;
+  t.U = t.cn + 3 * P;
+  t.A = t.U + 3 * P * P;
+  t.B = t.A + P * P * P;
+  return t;
+}
+static size_t transfer_smem_bytes(int P) {
+  return sizeof(double) * (size_t)(6 * P + 3 * P * P + 2 * P * P * P);
+}
+
+__device__ void load_transfer_matrices(const TransferSmem& S, const double* __restrict__ nodes,
+                                       int par, int ch, int n) {
+  const int P = n + 1;
+  for (int t = threadIdx.x; t < 3 * P; t += blockDim.x) {
+    S.pn[t] = nodes[(int64_t)par * 3 * P + t];
+    S.cn[t] = nodes[(int64_t)ch * 3 * P + t];
+  }
+  __syncthreads();
+  // U[d][k][k'] = L^par_k(s^child_k'): the parent's basis at the child's nodes.
+  for (int t = threadIdx.x; t < 3 * P; t += blockDim.x) {
+    int d = t / P, kp = t % P;
+    basis_1d<double>(S.cn[d * P + kp], S.pn + d * P, n, S.U + (d * P) * P + kp, P);
+  }
+  __syncthreads();
+}
+
+// Eq. (16): qhat^par_k = sum_children sum_k' L^par_k(s^child_k') qhat^child_k',
+// as three mode products with the P x P matrices U_d.
+__global__ void k_up_parent(int32_t ls, const int32_t* __restrict__ nchild,
+                            const int32_t* __restrict__ first_child, const double* __restrict__ nodes,
+                            int n, double* __restrict__ qhat) {
+  extern __shared__ double smem[];
+  const int P = n + 1, np = P * P * P;
+  const int c = ls + blockIdx.x;
+  if (nchild[c] == 0) return;
+  TransferSmem S = carve(smem, P);
+  double acc[kMaxOutPerThread];
+#pragma unroll
+  for (int r = 0; r < kMaxOutPerThread; ++r) acc[r] = 0.0;
+  for (int ci = 0; ci < nchild[c]; ++ci) {
+    const int ch = first_child[c] + ci;
+    load_transfer_matrices(S, nodes, c, ch, n);
+    for (int o = threadIdx.x; o < np; o += blockDim.x) S.A[o] = qhat[(int64_t)ch * np + o];
+    __syncthreads();
+    // B[k1][k2'][k3'] = sum_k1' U1[k1][k1'] A[k1'][k2'][k3']
+    for (int o = threadIdx.x; o < np; o += blockDim.x) {
+      int k1 = o / (P * P), rest = o % (P * P);
+      double v = 0.0;
+      for (int a = 0; a < P; ++a) v += S.U[(0 * P + k1) * P + a] * S.A[a * P * P + rest];
+      S.B[o] = v;
+    }
+    __syncthreads();
+    // A[k1][k2][k3'] = sum_k2' U2[k2][k2'] B[k1][k2'][k3']
+    for (int o = threadIdx.x; o < np; o += blockDim.x) {
+      int k1 = o / (P * P), k2 = (o / P) % P, k3 = o % P;
+      double v = 0.0;
+      for (int a = 0; a < P; ++a) v += S.U[(1 * P + k2) * P + a] * S.B[(k1 * P + a) * P + k3];
+      S.A[o] = v;
+    }
+    __syncthreads();
+    // out[k1][k2][k3] += sum_k3' U3[k3][k3'] A[k1][k2][k3']
+#pragma unroll
+    for (int r = 0; r < kMaxOutPerThread; ++r) {
+      int o = threadIdx.x + r * blockDim.x;
+      if (o < np) {
+        int k12 = o / P, k3 = o % P;
+        double v = 0.0;
+        for (int a = 0; a < P; ++a) v += S.U[(2 * P + k3) * P + a] * S.A[k12 * P + a];
+        acc[r] += v;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < kMaxOutPerThread; ++r) {
+    int o = threadIdx.x + r * blockDim.x;
+    if (o < np) qhat[(int64_t)c * np + o] = acc[r];
+  }
+}
+
+int upward_pass(bldtt_plan* p, cudaStream_t s) {
+  Counters& cnt = p->compute_counter;
+  const Tree& T = p->st;
+  if (p->precision == BLDTT_FP32_BULK)
+    k_up_leaf<true><<<T.nleaves, kUpThreads, 0, s>>>(T.leaf_ids, T.begin, T.end, T.x, T.y, T.z,
+                                                      p->q_tree, T.nodes, p->n, p->qhat);
+  else
+    k_up_leaf<false><<<T.nleaves, kUpThreads, 0, s>>>(T.leaf_ids, T.begin, T.end, T.x, T.y, T.z,
+                                                       p->q_tree, T.nodes, p->n, p->qhat);
+  BL_LAUNCHED(cnt.launches);
+  size_t sm = transfer_smem_bytes(p->P);
+  for (int lvl = T.nlevels - 2; lvl >= 0; --lvl) {
+    int32_t ls = T.level_start[lvl], nl = T.level_start[lvl + 1] - ls;
+    k_up_parent<<<nl, kUpThreads, sm, s>>>(ls, T.nchild, T.first_child, T.nodes, p->n, p->qhat);
+    BL_LAUNCHED(cnt.launches);
+  }
+  return BLDTT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Source pool: leaf particles then proxy points, each block padded to kChunk
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void put(float4* pool, int64_t i, double x, double y, double z, double q,
+                                    const double* c) {
+  pool[i] = make_float4((float)(x - c[0]), (float)(y - c[1]), (float)(z - c[2]), (float)q);
+}
+__device__ __forceinline__ void put(double4* pool, int64_t i, double x, double y, double z, double q,
+                                    const double*) {
+  pool[i] = make_double4(x, y, z, q);
+}
+
+template <typename Vec>
+__global__ void k_pool_particles(const int32_t* __restrict__ leaf_ids, const int32_t* __restrict__ begin,
+                                 const int32_t* __restrict__ end, const int32_t* __restrict__ pad_prefix,
+                                 const double* __restrict__ center, const double* __restrict__ x,
+                                 const double* __restrict__ y, const double* __restrict__ z,
+                                 const double* __restrict__ q, Vec* __restrict__ pool) {
+  const int lf = blockIdx.x;
+  const int c = leaf_ids[lf];
+  const double* cc = center + (int64_t)c * 3;
+  const int64_t o = pad_prefix[lf];
+  for (int32_t i = begin[c] + threadIdx.x; i < end[c]; i += blockDim.x)
+    put(pool, o + (i - begin[c]), x[i], y[i], z[i], q[i], cc);
+}
+
+template <typename Vec>
+__global__ void k_pool_proxies(int n, int np_pad, int64_t base, const double* __restrict__ nodes,
+                               const double* __restrict__ center, const double* __restrict__ qhat,
+                               Vec* __restrict__ pool) {
+  const int c = blockIdx.x;
+  const int P = n + 1, np = P * P * P;
+  const double* nd = nodes + (int64_t)c * 3 * P;
+  const double* cc = center + (int64_t)c * 3;
+  for (int k = threadIdx.x; k < np; k += blockDim.x) {
+    int k1 = k / (P * P), k2 = (k / P) % P, k3 = k % P;
+    put(pool, base + (int64_t)c * np_pad + k, nd[k1], nd[P + k2], nd[2 * P + k3],
+        qhat[(int64_t)c * np + k], cc);
+  }
+}
+
+int build_pool(bldtt_plan* p, cudaStream_t s) {
+  Counters& cnt = p->compute_counter;
+  const Tree& T = p->st;
+  const bool f32 = p->precision == BLDTT_FP32_BULK;
+  size_t esz = f32 ? sizeof(float4) : sizeof(double4);
+  BL_CUDA(cudaMemsetAsync(p->pool, 0, (size_t)p->pool_len * esz, s));
+  if (f32) {
+    k_pool_particles<float4><<<T.nleaves, 256, 0, s>>>(T.leaf_ids, T.begin, T.end, p->pad_prefix,
+                                                       T.center, T.x, T.y, T.z, p->q_tree,
+                                                       (float4*)p->pool);
+    BL_LAUNCHED(cnt.launches);
+    k_pool_proxies<float4><<<T.nclusters, 256, 0, s>>>(p->n, p->np_pad, p->pool_particles, T.nodes,
+                                                       T.center, p->qhat, (float4*)p->pool);
+  } else {
+    k_pool_particles<double4><<<T.nleaves, 256, 0, s>>>(T.leaf_ids, T.begin, T.end, p->pad_prefix,
+                                                        T.center, T.x, T.y, T.z, p->q_tree,
+                                                        (double4*)p->pool);
+    BL_LAUNCHED(cnt.launches);
+    k_pool_proxies<double4><<<T.nclusters, 256, 0, s>>>(p->n, p->np_pad, p->pool_particles, T.nodes,
+                                                        T.center, p->qhat, (double4*)p->pool);
+  }
+  BL_LAUNCHED(cnt.launches);
+  return BLDTT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Downward pass
+// ---------------------------------------------------------------------------
+
+// Eq. (20): phi(t^child_k') += sum_k L^par_k(t^child_k') phi(t^par_k), three
+// mode products with the transposed U_d.
+__global__ void k_down_parent(int32_t ls, const int32_t* __restrict__ parent,
+                              const double* __restrict__ nodes, int n, double* __restrict__ phit) {
+  extern __shared__ double smem[];
+  const int P = n + 1, np = P * P * P;
+  const int c = ls + blockIdx.x;
+  const int par = parent[c];
+  TransferSmem S = carve(smem, P);
+  load_transfer_matrices(S, nodes, par, c, n);
+  for (int o = threadIdx.x; o < np; o += blockDim.x) S.A[o] = phit[(int64_t)par * np + o];
+  __syncthreads();
+  // B[k1'][k2][k3] = sum_k1 U1[k1][k1'] A[k1][k2][k3]
+  for (int o = threadIdx.x; o < np; o += blockDim.x) {
+    int k1 = o / (P * P), rest = o % (P * P);
+    double v = 0.0;
+    for (int a = 0; a < P; ++a) v += S.U[(0 * P + a) * P + k1] * S.A[a * P * P + rest];
+    S.B[o] = v;
+  }
+  __syncthreads();
+  // A[k1'][k2'][k3] = sum_k2 U2[k2][k2'] B[k1'][k2][k3]
+  for (int o = threadIdx.x; o < np; o += blockDim.x) {
+    int k1 = o / (P * P), k2 = (o / P) % P, k3 = o % P;
+    double v = 0.0;
+    for (int a = 0; a < P; ++a) v += S.U[(1 * P + a) * P + k2] * S.B[(k1 * P + a) * P + k3];
+    S.A[o] = v;
+  }
+  __syncthreads();
+  // phit^child[k1'][k2'][k3'] += sum_k3 U3[k3][k3'] A[k1'][k2'][k3]
+  for (int o = threadIdx.x; o < np; o += blockDim.x) {
+    int k12 = o / P, k3 = o % P;
+    double v = 0.0;
+    for (int a = 0; a < P; ++a) v += S.U[(2 * P + a) * P + k3] * S.A[k12 * P + a];
+    phit[(int64_t)c * np + o] += v;
+  }
+}
+
+constexpr int kDownThreads = 128;
+
+// Eq. (21) for every target leaf, then phi = (PP + PC part) + interpolated
+// proxy potentials, scattered back to input order.
+template <bool F32>
+__global__ void __launch_bounds__(kDownThreads) k_down_leaf(
+    const int32_t* __restrict__ leaf_ids, const int32_t* __restrict__ begin,
+    const int32_t* __restrict__ end, const double* __restrict__ x, const double* __restrict__ y,
+    const double* __restrict__ z, const int32_t* __restrict__ perm, const double* __restrict__ nodes,
+    int n, const double* __restrict__ phit, const double* __restrict__ phi_near,
+    double* __restrict__ phi_user) {
+  using T = typename std::conditional<F32, float, double>::type;
+  extern __shared__ double smem[];
+  const int P = n + 1, np = P * P * P;
+  const int stride = 3 * P + ((3 * P) % 2 == 0 ? 1 : 0);   // odd: conflict-free rows
+  double* snodes = smem;                                    // [3][P]
+  double* sL = snodes + 3 * P;                              // [threads][stride]
+  T* sphi = reinterpret_cast<T*>(sL + (size_t)kDownThreads * stride);   // [np]
+  const int c = leaf_ids[blockIdx.x];
+  for (int t = threadIdx.x; t < 3 * P; t += blockDim.x) snodes[t] = nodes[(int64_t)c * 3 * P + t];
+  for (int o = threadIdx.x; o < np; o += blockDim.x) sphi[o] = (T)phit[(int64_t)c * np + o];
+  __syncthreads();
+  double* L = sL + (size_t)threadIdx.x * stride;
+  for (int32_t i = begin[c] + threadIdx.x; i < end[c]; i += blockDim.x) {
+    basis_1d<double>(x[i], snodes, n, L, 1);
+    basis_1d<double>(y[i], snodes + P, n, L + P, 1);
+    basis_1d<double>(z[i], snodes + 2 * P, n, L + 2 * P, 1);
+    double acc = 0.0;
+    for (int k1 = 0; k1 < P; ++k1) {
+      double s1 = 0.0;
+      for (int k2 = 0; k2 < P; ++k2) {
+        const T* row = sphi + (k1 * P + k2) * P;
+        T s2 = (T)0;
+        for (int k3 = 0; k3 < P; ++k3) s2 += (T)L[2 * P + k3] * row[k3];
+        s1 += L[P + k2] * (double)s2;
+      }
+      acc += L[k1] * s1;
+    }
+    phi_user[perm[i]] = phi_near[i] + acc;
+  }
+}
+
+int downward_pass(bldtt_plan* p, double* phi_user, cudaStream_t s) {
+  Counters& cnt = p->compute_counter;
+  const Tree& T = p->tt;
+  size_t sm = transfer_smem_bytes(p->P);
+  for (int lvl = 1; lvl < T.nlevels; ++lvl) {
+    int32_t ls = T.level_start[lvl], nl = T.level_start[lvl + 1] - ls;
+    k_down_parent<<<nl, kUpThreads, sm, s>>>(ls, T.parent, T.nodes, p->n, p->phit);
+    BL_LAUNCHED(cnt.launches);
+  }
+  const int P = p->P, np = p->np;
+  const int stride = 3 * P + ((3 * P) % 2 == 0 ? 1 : 0);
+  if (p->precision == BLDTT_FP32_BULK) {
+    size_t bytes = sizeof(double) * (3 * P + (size_t)kDownThreads * stride) + sizeof(float) * np;
+    k_down_leaf<true><<<T.nleaves, kDownThreads, bytes, s>>>(T.leaf_ids, T.begin, T.end, T.x, T.y,
+                                                              T.z, T.perm, T.nodes, p->n, p->phit,
+                                                              p->phi_near, phi_user);
+  } else {
+    size_t bytes = sizeof(double) * (3 * P + (size_t)kDownThreads * stride + np);
+    k_down_leaf<false><<<T.nleaves, kDownThreads, bytes, s>>>(T.leaf_ids, T.begin, T.end, T.x, T.y,
+                                                               T.z, T.perm, T.nodes, p->n, p->phit,
+                                                               p->phi_near, phi_user);
+  }
+  BL_LAUNCHED(cnt.launches);
+  return BLDTT_OK;
+}
+
+// Opt the dynamic-shared-memory kernels in to large allocations (n up to 16).
+int configure_pass_kernels() {
+  int big = 200 * 1024;
+  BL_CUDA(cudaFuncSetAttribute(k_up_parent, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  BL_CUDA(cudaFuncSetAttribute(k_down_parent, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  BL_CUDA(cudaFuncSetAttribute(k_down_leaf<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  BL_CUDA(cudaFuncSetAttribute(k_down_leaf<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  return BLDTT_OK;
+}
+
+}  // namespace bldtt

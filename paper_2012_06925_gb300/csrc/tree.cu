@@ -1,0 +1,465 @@
+// Tree building (Sec. 2.3), level by level on the device.
+//
+// Each level: decide the split of every cluster of the level (count rule and
+// sqrt(2) aspect rule, midpoint of the shrunk box), cut every splitting
+// cluster's particle range into fixed chunks, count the 8 child codes per
+// chunk, turn the counts into stable destinations, scatter the particles
+// (a stable 8-way partition, so particles keep input order inside each
+// cluster), create the non-empty children and shrink each to the bounding
+// box of its particles.  All geometric decisions are made in FP64 with
+// explicitly rounded operations (no FMA contraction) so that they are the
+// decisions a plain FP64 evaluation of the same expressions makes.
+#include "internal.cuh"
+
+namespace bldtt {
+
+constexpr int kTreeChunk = 2048;
+constexpr int kTreeThreads = 256;
+
+// Chebyshev point of the 2nd kind, s_k = cos(pi k / n), symmetrised so that
+// s_0 = 1, s_n = -1, s_{n-k} = -s_k and s_{n/2} = 0 (Sec. 2.1, Eq. (4)).
+__device__ __forceinline__ double cheb_point(int k, int n) {
+  if (2 * k == n) return 0.0;
+  if (2 * k < n) return cos(__ddiv_rn(__dmul_rn(M_PI, (double)k), (double)n));
+  return -cos(__ddiv_rn(__dmul_rn(M_PI, (double)(n - k)), (double)n));
+}
+
+__global__ void k_tree_init(const double* __restrict__ coords, int32_t n, double* __restrict__ x,
+                            double* __restrict__ y, double* __restrict__ z,
+                            int32_t* __restrict__ perm) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  x[i] = coords[i];
+  y[i] = coords[(int64_t)n + i];
+  z[i] = coords[2 * (int64_t)n + i];
+  perm[i] = (int32_t)i;
+}
+
+__global__ void k_tree_root(int32_t n, int32_t* begin, int32_t* end, int32_t* parent,
+                            int32_t* level) {
+  begin[0] = 0;
+  end[0] = n;
+  parent[0] = -1;
+  level[0] = 0;
+}
+
+// Split decision of each cluster of the level (reading: leaf iff |C| <= M0 or
+// all extents zero; up to 1/2/3 dims by the count rule; eligible iff
+// L_d*L_d*2 >= L_max*L_max; longest eligible first, ties to the lower axis).
+__global__ void k_tree_decide(int32_t ls, int32_t nl, const int32_t* __restrict__ begin,
+                              const int32_t* __restrict__ end, const double* __restrict__ box,
+                              int32_t max_leaf, uint8_t* __restrict__ splitmask,
+                              double* __restrict__ mid, int32_t* __restrict__ nchunks,
+                              int32_t* __restrict__ first_child, int32_t* __restrict__ nchild) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nl) return;
+  int c = ls + j;
+  int64_t cnt = (int64_t)end[c] - begin[c];
+  first_child[c] = -1;
+  nchild[c] = 0;
+  const double* b = box + (int64_t)c * 6;
+  double ext[3];
+  for (int d = 0; d < 3; ++d) ext[d] = __dsub_rn(b[3 + d], b[d]);
+  uint8_t mask = 0;
+  if (cnt > (int64_t)max_leaf) {
+    double lmax = fmax(fmax(ext[0], ext[1]), ext[2]);
+    if (lmax > 0.0) {
+      int cap = cnt <= 2 * (int64_t)max_leaf ? 1 : (cnt <= 4 * (int64_t)max_leaf ? 2 : 3);
+      double lm2 = __dmul_rn(lmax, lmax);
+      int o[3] = {0, 1, 2};
+      for (int i = 0; i < 3; ++i)
+        for (int k = i + 1; k < 3; ++k)
+          if (ext[o[k]] > ext[o[i]] || (ext[o[k]] == ext[o[i]] && o[k] < o[i])) {
+            int t = o[i]; o[i] = o[k]; o[k] = t;
+          }
+      int taken = 0;
+      for (int i = 0; i < 3; ++i) {
+        int d = o[i];
+        bool eligible = __dmul_rn(__dmul_rn(ext[d], ext[d]), 2.0) >= lm2;
+        if (eligible && taken < cap) {
+          mask |= (uint8_t)(4 >> d);
+          ++taken;
+        }
+      }
+    }
+  }
+  splitmask[j] = mask;
+  for (int d = 0; d < 3; ++d) mid[(int64_t)j * 3 + d] = __dmul_rn(__dadd_rn(b[d], b[3 + d]), 0.5);
+  nchunks[j] = mask ? (int32_t)((cnt + kTreeChunk - 1) / kTreeChunk) : 0;
+}
+
+__global__ void k_tree_chunks(int32_t nl, int32_t ls, const int32_t* __restrict__ chunk_off,
+                              int32_t tc, const int32_t* __restrict__ begin,
+                              int32_t* __restrict__ chunk_cluster, int32_t* __restrict__ chunk_start) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= tc) return;
+  int lo = 0, hi = nl;   // first j with chunk_off[j] > q, minus one
+  while (lo < hi) {
+    int m = (lo + hi) >> 1;
+    if (chunk_off[m] <= q) lo = m + 1; else hi = m;
+  }
+  int j = lo - 1;
+  chunk_cluster[q] = j;
+  chunk_start[q] = begin[ls + j] + (q - chunk_off[j]) * kTreeChunk;
+}
+
+__device__ __forceinline__ int child_code(double px, double py, double pz, uint8_t mask,
+                                          const double* m) {
+  int code = 0;
+  if ((mask & 4) && px >= m[0]) code |= 4;
+  if ((mask & 2) && py >= m[1]) code |= 2;
+  if ((mask & 1) && pz >= m[2]) code |= 1;
+  return code;
+}
+
+__global__ void k_tree_count(int32_t ls, const int32_t* __restrict__ chunk_cluster,
+                             const int32_t* __restrict__ chunk_start, const int32_t* __restrict__ end,
+                             const double* __restrict__ x, const double* __restrict__ y,
+                             const double* __restrict__ z, const uint8_t* __restrict__ splitmask,
+                             const double* __restrict__ mid, uint8_t* __restrict__ code,
+                             int32_t* __restrict__ counts) {
+  __shared__ int32_t cnt[8];
+  if (threadIdx.x < 8) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  int q = blockIdx.x;
+  int j = chunk_cluster[q];
+  int32_t s0 = chunk_start[q];
+  int32_t s1 = min(s0 + kTreeChunk, end[ls + j]);
+  uint8_t mask = splitmask[j];
+  double m[3] = {mid[(int64_t)j * 3], mid[(int64_t)j * 3 + 1], mid[(int64_t)j * 3 + 2]};
+  for (int32_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
+    int c = child_code(x[i], y[i], z[i], mask, m);
+    code[i] = (uint8_t)c;
+    atomicAdd(&cnt[c], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < 8) counts[(int64_t)q * 8 + threadIdx.x] = cnt[threadIdx.x];
+}
+
+__global__ void k_tree_combine(int32_t nl, int32_t ls, const uint8_t* __restrict__ splitmask,
+                               const int32_t* __restrict__ chunk_off,
+                               const int32_t* __restrict__ nchunks,
+                               const int32_t* __restrict__ counts, int32_t* __restrict__ chunk_base,
+                               int32_t* __restrict__ child_cnt, int32_t* __restrict__ nch,
+                               const int32_t* __restrict__ begin) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nl) return;
+  if (!splitmask[j]) {
+    nch[j] = 0;
+    return;
+  }
+  int32_t run[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int32_t q0 = chunk_off[j], q1 = q0 + nchunks[j];
+  for (int32_t q = q0; q < q1; ++q)
+    for (int b = 0; b < 8; ++b) {
+      chunk_base[(int64_t)q * 8 + b] = run[b];
+      run[b] += counts[(int64_t)q * 8 + b];
+    }
+  int32_t cb[8];
+  int32_t pos = begin[ls + j];
+  int k = 0;
+  for (int b = 0; b < 8; ++b) {
+    cb[b] = pos;
+    pos += run[b];
+    child_cnt[(int64_t)j * 8 + b] = run[b];
+    k += run[b] > 0;
+  }
+  for (int32_t q = q0; q < q1; ++q)
+    for (int b = 0; b < 8; ++b) chunk_base[(int64_t)q * 8 + b] += cb[b];
+  nch[j] = k;
+}
+
+__global__ void k_tree_children(int32_t nl, int32_t ls, int32_t le, int32_t lvl,
+                                const uint8_t* __restrict__ splitmask,
+                                const int32_t* __restrict__ child_off,
+                                const int32_t* __restrict__ child_cnt, int32_t* __restrict__ begin,
+                                int32_t* __restrict__ end, int32_t* __restrict__ parent,
+                                int32_t* __restrict__ level, int32_t* __restrict__ first_child,
+                                int32_t* __restrict__ nchild) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nl || !splitmask[j]) return;
+  int c = ls + j;
+  int32_t fc = le + child_off[j];
+  int32_t pos = begin[c];
+  int k = 0;
+  for (int b = 0; b < 8; ++b) {
+    int32_t cnt = child_cnt[(int64_t)j * 8 + b];
+    if (cnt == 0) continue;
+    int32_t id = fc + k++;
+    begin[id] = pos;
+    end[id] = pos + cnt;
+    parent[id] = c;
+    level[id] = lvl + 1;
+    pos += cnt;
+  }
+  first_child[c] = fc;
+  nchild[c] = k;
+}
+
+__global__ void k_tree_scatter(int32_t ls, const int32_t* __restrict__ chunk_cluster,
+                               const int32_t* __restrict__ chunk_start,
+                               const int32_t* __restrict__ end, const uint8_t* __restrict__ code,
+                               const int32_t* __restrict__ chunk_base, const double* __restrict__ x,
+                               const double* __restrict__ y, const double* __restrict__ z,
+                               const int32_t* __restrict__ perm, double* __restrict__ x2,
+                               double* __restrict__ y2, double* __restrict__ z2,
+                               int32_t* __restrict__ perm2) {
+  constexpr int W = kTreeThreads / 32;
+  __shared__ int32_t warp_cnt[W][9];
+  __shared__ int32_t running[8];
+  __shared__ int32_t base[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int q = blockIdx.x;
+  int32_t s0 = chunk_start[q];
+  int32_t s1 = min(s0 + kTreeChunk, end[ls + chunk_cluster[q]]);
+  if (threadIdx.x < 8) {
+    running[threadIdx.x] = 0;
+    base[threadIdx.x] = chunk_base[(int64_t)q * 8 + threadIdx.x];
+  }
+  for (int r = 0; r < kTreeChunk / kTreeThreads; ++r) {
+    for (int i = threadIdx.x; i < W * 9; i += kTreeThreads) (&warp_cnt[0][0])[i] = 0;
+    __syncthreads();
+    int32_t i = s0 + r * kTreeThreads + threadIdx.x;
+    bool valid = i < s1;
+    int d = valid ? code[i] : 8;
+    unsigned peers = __match_any_sync(0xffffffffu, d);
+    int rank = __popc(peers & ((1u << lane) - 1u));
+    if (rank == 0) warp_cnt[warp][d] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      int32_t dst = base[d] + running[d] + rank;
+      for (int w = 0; w < warp; ++w) dst += warp_cnt[w][d];
+      x2[dst] = x[i];
+      y2[dst] = y[i];
+      z2[dst] = z[i];
+      perm2[dst] = perm[i];
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+      int32_t t = 0;
+      for (int w = 0; w < W; ++w) t += warp_cnt[w][threadIdx.x];
+      running[threadIdx.x] += t;
+    }
+    __syncthreads();
+  }
+}
+
+// Shrink every new cluster to the bounding box of its particles (Sec. 2.3).
+__global__ void k_tree_child_bbox(int32_t first, const int32_t* __restrict__ begin,
+                                  const int32_t* __restrict__ end, const double* __restrict__ x,
+                                  const double* __restrict__ y, const double* __restrict__ z,
+                                  double* __restrict__ box) {
+  int c = first + blockIdx.x;
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int32_t i = begin[c] + threadIdx.x; i < end[c]; i += blockDim.x) {
+    double v[3] = {x[i], y[i], z[i]};
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = fmin(lo[d], v[d]);
+      hi[d] = fmax(hi[d], v[d]);
+    }
+  }
+  __shared__ double sm[kTreeThreads / 32][6];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int d = 0; d < 3; ++d)
+    for (int off = 16; off; off >>= 1) {
+      lo[d] = fmin(lo[d], __shfl_down_sync(0xffffffffu, lo[d], off));
+      hi[d] = fmax(hi[d], __shfl_down_sync(0xffffffffu, hi[d], off));
+    }
+  if (lane == 0)
+    for (int d = 0; d < 3; ++d) {
+      sm[warp][d] = lo[d];
+      sm[warp][3 + d] = hi[d];
+    }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double r = sm[0][threadIdx.x];
+    for (int w = 1; w < kTreeThreads / 32; ++w)
+      r = threadIdx.x < 3 ? fmin(r, sm[w][threadIdx.x]) : fmax(r, sm[w][threadIdx.x]);
+    box[(int64_t)c * 6 + threadIdx.x] = r;
+  }
+}
+
+// Centre = box centre, radius = half the diagonal, proxy points c + h s_k.
+__global__ void k_tree_geometry(int32_t C, int degree, const double* __restrict__ box,
+                                double* __restrict__ center, double* __restrict__ radius,
+                                double* __restrict__ nodes) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  const int P = degree + 1;
+  const double* b = box + (int64_t)c * 6;
+  double e[3];
+  for (int d = 0; d < 3; ++d) {
+    double lo = b[d], hi = b[3 + d];
+    double cc = __dmul_rn(__dadd_rn(lo, hi), 0.5);
+    double h = __dmul_rn(__dsub_rn(hi, lo), 0.5);
+    e[d] = __dsub_rn(hi, lo);
+    center[(int64_t)c * 3 + d] = cc;
+    for (int k = 0; k < P; ++k)
+      nodes[((int64_t)c * 3 + d) * P + k] = __dadd_rn(cc, __dmul_rn(h, cheb_point(k, degree)));
+  }
+  double s2 = __dadd_rn(__dadd_rn(__dmul_rn(e[0], e[0]), __dmul_rn(e[1], e[1])), __dmul_rn(e[2], e[2]));
+  radius[c] = __dmul_rn(__dsqrt_rn(s2), 0.5);
+}
+
+__global__ void k_tree_leaf_flags(int32_t C, const int32_t* __restrict__ nchild,
+                                  const int32_t* __restrict__ begin, int32_t* __restrict__ flag) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < C && nchild[c] == 0) flag[begin[c]] = 1;
+}
+
+__global__ void k_tree_leaf_order(int32_t C, int32_t n, int32_t nleaves,
+                                  const int32_t* __restrict__ nchild,
+                                  const int32_t* __restrict__ begin, const int32_t* __restrict__ end,
+                                  const int32_t* __restrict__ excl, int32_t* __restrict__ leaf_ids,
+                                  int32_t* __restrict__ leaf_first, int32_t* __restrict__ leaf_last) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  leaf_first[c] = excl[begin[c]];
+  leaf_last[c] = end[c] < n ? excl[end[c]] : nleaves;
+  if (nchild[c] == 0) leaf_ids[excl[begin[c]]] = c;
+}
+
+static int grow_clusters(Tree& T, size_t need, size_t keep, cudaStream_t s) {
+  if (need <= T.cap && T.begin) return BLDTT_OK;
+  size_t ncap = T.cap ? T.cap : 64;
+  while (ncap < need) ncap *= 2;
+  int32_t** iarr[6] = {&T.begin, &T.end, &T.parent, &T.first_child, &T.nchild, &T.level};
+  for (auto a : iarr) {
+    size_t c = T.cap;
+    BL_TRY(dgrow(a, &c, ncap, keep, s));
+  }
+  size_t c6 = T.cap * 6;
+  BL_TRY(dgrow(&T.box, &c6, ncap * 6, keep * 6, s));
+  T.cap = ncap;
+  return BLDTT_OK;
+}
+
+static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+int build_tree(Tree& T, const double* coords, int32_t n, int32_t max_leaf, int degree,
+               int* bad_dev, cudaStream_t s, Counters& cnt) {
+  T.n = n;
+  double *x2 = nullptr, *y2 = nullptr, *z2 = nullptr;
+  int32_t* perm2 = nullptr;
+  uint8_t* code = nullptr;
+  BL_TRY(dalloc_n(&T.x, n, s));
+  BL_TRY(dalloc_n(&T.y, n, s));
+  BL_TRY(dalloc_n(&T.z, n, s));
+  BL_TRY(dalloc_n(&T.perm, n, s));
+  BL_TRY(dalloc_n(&x2, n, s));
+  BL_TRY(dalloc_n(&y2, n, s));
+  BL_TRY(dalloc_n(&z2, n, s));
+  BL_TRY(dalloc_n(&perm2, n, s));
+  BL_TRY(dalloc_n(&code, n, s));
+  k_tree_init<<<nblk(n, 256), 256, 0, s>>>(coords, n, T.x, T.y, T.z, T.perm);
+  BL_LAUNCHED(cnt.launches);
+  BL_TRY(grow_clusters(T, 1024, 0, s));
+  k_tree_root<<<1, 1, 0, s>>>(n, T.begin, T.end, T.parent, T.level);
+  BL_LAUNCHED(cnt.launches);
+  BL_TRY(bbox_reduce(T.x, T.y, T.z, n, T.box, bad_dev, s, cnt));
+
+  T.level_start.assign({0, 1});
+  for (int lvl = 0;; ++lvl) {
+    int32_t ls = T.level_start[lvl], le = T.level_start[lvl + 1], nl = le - ls;
+    uint8_t* splitmask = nullptr;
+    double* mid = nullptr;
+    int32_t *nchunks = nullptr, *chunk_off = nullptr;
+    BL_TRY(dalloc_n(&splitmask, nl, s));
+    BL_TRY(dalloc_n(&mid, (size_t)nl * 3, s));
+    BL_TRY(dalloc_n(&nchunks, nl, s));
+    BL_TRY(dalloc_n(&chunk_off, nl, s));
+    k_tree_decide<<<nblk(nl, 128), 128, 0, s>>>(ls, nl, T.begin, T.end, T.box, max_leaf, splitmask,
+                                                mid, nchunks, T.first_child, T.nchild);
+    BL_LAUNCHED(cnt.launches);
+    int32_t tc = 0;
+    BL_TRY(scan_exclusive(nchunks, chunk_off, nl, &tc, s, cnt));
+    if (tc == 0) {
+      dfree(splitmask, s); dfree(mid, s); dfree(nchunks, s); dfree(chunk_off, s);
+      break;
+    }
+    int32_t *chunk_cluster = nullptr, *chunk_start = nullptr, *counts = nullptr,
+            *chunk_base = nullptr, *child_cnt = nullptr, *nch = nullptr, *child_off = nullptr;
+    BL_TRY(dalloc_n(&chunk_cluster, tc, s));
+    BL_TRY(dalloc_n(&chunk_start, tc, s));
+    BL_TRY(dalloc_n(&counts, (size_t)tc * 8, s));
+    BL_TRY(dalloc_n(&chunk_base, (size_t)tc * 8, s));
+    BL_TRY(dalloc_n(&child_cnt, (size_t)nl * 8, s));
+    BL_TRY(dalloc_n(&nch, nl, s));
+    BL_TRY(dalloc_n(&child_off, nl, s));
+    k_tree_chunks<<<nblk(tc, 256), 256, 0, s>>>(nl, ls, chunk_off, tc, T.begin, chunk_cluster,
+                                                chunk_start);
+    BL_LAUNCHED(cnt.launches);
+    k_tree_count<<<tc, kTreeThreads, 0, s>>>(ls, chunk_cluster, chunk_start, T.end, T.x, T.y, T.z,
+                                             splitmask, mid, code, counts);
+    BL_LAUNCHED(cnt.launches);
+    k_tree_combine<<<nblk(nl, 128), 128, 0, s>>>(nl, ls, splitmask, chunk_off, nchunks, counts,
+                                                 chunk_base, child_cnt, nch, T.begin);
+    BL_LAUNCHED(cnt.launches);
+    int32_t nc = 0;
+    BL_TRY(scan_exclusive(nch, child_off, nl, &nc, s, cnt));
+    BL_TRY(grow_clusters(T, (size_t)le + nc, (size_t)le, s));
+    k_tree_children<<<nblk(nl, 128), 128, 0, s>>>(nl, ls, le, lvl, splitmask, child_off, child_cnt,
+                                                  T.begin, T.end, T.parent, T.level, T.first_child,
+                                                  T.nchild);
+    BL_LAUNCHED(cnt.launches);
+    BL_CUDA(cudaMemcpyAsync(x2, T.x, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+    BL_CUDA(cudaMemcpyAsync(y2, T.y, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+    BL_CUDA(cudaMemcpyAsync(z2, T.z, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+    BL_CUDA(cudaMemcpyAsync(perm2, T.perm, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+    k_tree_scatter<<<tc, kTreeThreads, 0, s>>>(ls, chunk_cluster, chunk_start, T.end, code,
+                                               chunk_base, T.x, T.y, T.z, T.perm, x2, y2, z2, perm2);
+    BL_LAUNCHED(cnt.launches);
+    { double* t = T.x; T.x = x2; x2 = t; }
+    { double* t = T.y; T.y = y2; y2 = t; }
+    { double* t = T.z; T.z = z2; z2 = t; }
+    { int32_t* t = T.perm; T.perm = perm2; perm2 = t; }
+    k_tree_child_bbox<<<nc, kTreeThreads, 0, s>>>(le, T.begin, T.end, T.x, T.y, T.z, T.box);
+    BL_LAUNCHED(cnt.launches);
+    T.level_start.push_back(le + nc);
+    dfree(splitmask, s); dfree(mid, s); dfree(nchunks, s); dfree(chunk_off, s);
+    dfree(chunk_cluster, s); dfree(chunk_start, s); dfree(counts, s); dfree(chunk_base, s);
+    dfree(child_cnt, s); dfree(nch, s); dfree(child_off, s);
+  }
+  dfree(x2, s); dfree(y2, s); dfree(z2, s); dfree(perm2, s); dfree(code, s);
+
+  T.nclusters = T.level_start.back();
+  T.nlevels = (int32_t)T.level_start.size() - 1;
+  const int C = T.nclusters;
+  BL_TRY(dalloc_n(&T.center, (size_t)C * 3, s));
+  BL_TRY(dalloc_n(&T.radius, (size_t)C, s));
+  BL_TRY(dalloc_n(&T.nodes, (size_t)C * 3 * (degree + 1), s));
+  k_tree_geometry<<<nblk(C, 128), 128, 0, s>>>(C, degree, T.box, T.center, T.radius, T.nodes);
+  BL_LAUNCHED(cnt.launches);
+
+  int32_t *flag = nullptr, *excl = nullptr;
+  BL_TRY(dalloc_n(&flag, n, s));
+  BL_TRY(dalloc_n(&excl, n, s));
+  BL_CUDA(cudaMemsetAsync(flag, 0, (size_t)n * 4, s));
+  k_tree_leaf_flags<<<nblk(C, 128), 128, 0, s>>>(C, T.nchild, T.begin, flag);
+  BL_LAUNCHED(cnt.launches);
+  int32_t nleaves = 0;
+  BL_TRY(scan_exclusive(flag, excl, n, &nleaves, s, cnt));
+  T.nleaves = nleaves;
+  BL_TRY(dalloc_n(&T.leaf_ids, nleaves, s));
+  BL_TRY(dalloc_n(&T.leaf_first, C, s));
+  BL_TRY(dalloc_n(&T.leaf_last, C, s));
+  k_tree_leaf_order<<<nblk(C, 128), 128, 0, s>>>(C, n, nleaves, T.nchild, T.begin, T.end, excl,
+                                                 T.leaf_ids, T.leaf_first, T.leaf_last);
+  BL_LAUNCHED(cnt.launches);
+  dfree(flag, s);
+  dfree(excl, s);
+  return BLDTT_OK;
+}
+
+void free_tree(Tree& T, cudaStream_t s) {
+  dfree_ptr(T.x, s); dfree_ptr(T.y, s); dfree_ptr(T.z, s); dfree_ptr(T.perm, s);
+  dfree_ptr(T.begin, s); dfree_ptr(T.end, s); dfree_ptr(T.parent, s);
+  dfree_ptr(T.first_child, s); dfree_ptr(T.nchild, s); dfree_ptr(T.level, s);
+  dfree_ptr(T.box, s); dfree_ptr(T.center, s); dfree_ptr(T.radius, s); dfree_ptr(T.nodes, s);
+  dfree_ptr(T.leaf_ids, s); dfree_ptr(T.leaf_first, s); dfree_ptr(T.leaf_last, s);
+  T.cap = 0;
+  T.nclusters = T.nlevels = T.nleaves = 0;
+  T.level_start.clear();
+}
+
+}  // namespace bldtt

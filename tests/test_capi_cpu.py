@@ -1,0 +1,84 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every
+symbol include/bldtt.h declares, and validates arguments before any device
+work."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import __graft_entry__
+from paper_2012_06925_gb300 import binding as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bldtt.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    __graft_entry__.build()
+    return B.load_library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bldtt_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("bldtt_setup", "bldtt_compute", "bldtt_set_charges", "bldtt_stats",
+                     "bldtt_destroy", "bldtt_status_string"):
+        assert required in names
+    assert set(names) == set(B.EXPORTED)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_stats_struct_size_matches_header(lib):
+    assert ctypes.sizeof(B.Stats) == 168
+
+
+def test_status_strings(lib):
+    assert B.status_string(0) == "BLDTT_OK"
+    assert B.status_string(1) == "BLDTT_EINVAL"
+    assert B.status_string(4) == "BLDTT_ETIMEOUT"
+    assert B.status_string(12345) == "BLDTT_UNKNOWN_STATUS"
+
+
+DUMMY = ctypes.c_void_p(0x1000)   # never dereferenced: validation fails first
+GOOD = dict(kernel=0, kappa=0.0, n=4, theta=0.7, N0=10, M0=10, precision=1)
+
+
+@pytest.mark.parametrize("change", [
+    dict(n=0), dict(n=17), dict(theta=-0.1), dict(theta=float("nan")), dict(N0=0), dict(M0=0),
+    dict(kernel=5), dict(kernel=1, kappa=-1.0), dict(kernel=1, kappa=float("inf")),
+    dict(precision=2), dict(M=0), dict(N=0), dict(M=2 ** 31),
+])
+def test_setup_rejects_invalid_arguments(lib, change):
+    args = dict(GOOD, M=100, N=100)
+    args.update(change)
+    st = B.setup_status(DUMMY, args["M"], DUMMY, args["N"], DUMMY, args["kernel"], args["kappa"],
+                        args["n"], args["theta"], args["N0"], args["M0"], args["precision"])
+    assert st == 1
+    assert lib.bldtt_last_error().decode() != ""
+
+
+def test_setup_rejects_null_pointers(lib):
+    st = B.setup_status(None, 10, DUMMY, 10, DUMMY, 0, 0.0, 4, 0.7, 5, 5, 1)
+    assert st == 1
+    h = ctypes.c_void_p()
+    assert lib.bldtt_setup(None, DUMMY, 10, DUMMY, 10, DUMMY, 0, 0.0, 4, 0.7, 5, 5, 1, None) == 1
+    assert lib.bldtt_compute(None, None, None) == 1
+    assert lib.bldtt_stats(None, None) == 1
+    lib.bldtt_destroy(None)
+    assert not h
+
+
+def test_direct_sum_rejects_bad_arguments(lib):
+    assert lib.bldtt_direct_sum(None, 1, DUMMY, 1, DUMMY, 0, 0.0, DUMMY, None) == 1
+    assert lib.bldtt_direct_sum(DUMMY, 1, DUMMY, 1, DUMMY, 7, 0.0, DUMMY, None) == 1
