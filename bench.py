@@ -1,0 +1,399 @@
+"""Benchmark of the BLDTT compute phase on GB300.
+
+Workload: 1E6 particles uniform in [-1,1]^3 (targets = sources), charges
+uniform in [-1,1], Coulomb kernel, n=8, theta=0.7, leaves of 2000, FP32-bulk
+kernel evaluations (FP64 accumulation).  One step is the whole hot path:
+bldtt_setup (both trees, traversal, work lists) and bldtt_compute (upward
+pass, PP/PC/CP/CC interactions, downward pass, potentials in input order) on
+inputs already resident in device memory.  The plain FP64 BLDTT is run on the
+same inputs to check the rel-l2 error (<= 1e-6) and timed as the FP64
+comparator.
+
+Multi-GPU: one process per GPU (torchrun); the path has no exchange step, so
+every rank solves its own replica of the workload and `value` counts the
+targets of all ranks (weak scaling).
+
+`--impl reference` times the CPU oracle (FP64, numpy) instead, on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "targets/sec at rel. L2 error ≤1e-6 vs plain FP64 BLDTT, 1 GB300; % FP32 peak"
+UNIT = "targets/s"
+WORKLOAD = "uniform_n1e6"
+FLOPS_PER_EVAL = {0: 20.0, 1: 28.0}   # Coulomb, Yukawa (stated flop counts)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparator timing")
+    return ap.parse_args()
+
+
+def workload():
+    from paper_2012_06925_gb300 import workloads as W
+    cfg = dict(W.CONFIGS[WORKLOAD])
+    tgt, _, q = W.make_problem(cfg["kind"], cfg["M"], seed=cfg["seed"])
+    kw = dict(kernel=cfg["kernel"], kappa=cfg["kappa"], n=cfg["n"], theta=cfg["theta"],
+              N0=cfg["N0"], M0=cfg["M0"])
+    return cfg, tgt, q, kw
+
+
+def config_dict(cfg):
+    return {"workload": f"{WORKLOAD}: M=N={cfg['M']:.0e} uniform in [-1,1]^3, targets=sources, "
+                        f"charges U[-1,1], Coulomb, n={cfg['n']}, theta={cfg['theta']}, "
+                        f"N0=M0={cfg['N0']}, FP32-bulk evaluation with FP64 accumulation",
+            "M": cfg["M"], "N": cfg["M"], "n": cfg["n"], "theta": cfg["theta"],
+            "leaf": cfg["N0"], "kernel": "coulomb",
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, %(root)r)
+import numpy as np
+import oracle as O
+from paper_2012_06925_gb300 import workloads as W
+cfg = W.CONFIGS[%(wl)r]
+tgt, _, q = W.make_problem(cfg["kind"], cfg["M"], seed=cfg["seed"])
+kw = dict(kernel=cfg["kernel"], kappa=cfg["kappa"], n=cfg["n"], theta=cfg["theta"],
+          N0=cfg["N0"], M0=cfg["M0"])
+t0 = time.perf_counter()
+samp = O.SampledBLDTT(tgt, tgt, q, **kw)
+t1 = time.perf_counter()
+leaf = samp.tt.leaves()[%(leaf)d]
+pos = np.arange(samp.tt.begin[leaf], samp.tt.end[leaf])[:%(count)d]
+idx = samp.tt.perm[pos]
+phi = samp.potentials(idx)
+t2 = time.perf_counter()
+print(json.dumps(dict(setup_s=t1 - t0, sample_s=t2 - t1, sample=int(idx.size), M=int(cfg["M"]))))
+"""
+
+
+def oracle_rate(leaf=0, count=400):
+    """Time the oracle single-threaded on one target leaf's first `count`
+    targets; the trees/lists/upward pass are charged pro rata (sample/M)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ORACLE_SNIPPET % dict(root=ROOT, wl=WORKLOAD, leaf=leaf, count=count)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("oracle timing failed:\n" + r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    t = d["sample_s"] + d["setup_s"] * d["sample"] / d["M"]
+    return dict(value=d["sample"] / t, unit=UNIT, cores=1, kind="oracle",
+                sample=(f"{d['sample']} targets of one target leaf of the {WORKLOAD} workload "
+                        f"(FP64 numpy oracle, one thread): per-target PP/PC along the cluster chain "
+                        f"plus that chain's CP/CC proxy potentials ({d['sample_s']:.1f} s); trees, "
+                        f"traversal and upward pass for all 1e6 particles ({d['setup_s']:.1f} s) "
+                        f"charged pro rata"),
+                seconds=d["sample_s"] + d["setup_s"])
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2012_06925_gb300 import workloads as W
+    cfg = W.CONFIGS[WORKLOAD]
+    rates = []
+    for i in range(args.warmup + args.steps):
+        r = oracle_rate(leaf=i % 7, count=150)
+        if i >= args.warmup:
+            rates.append(r)
+    value = statistics.median([r["value"] for r in rates])
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * statistics.median([r["seconds"] for r in rates]),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(cfg),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": rates[0]["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}",
+                                          f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = [r for r in self.rows if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = [nm for k, nm in enumerate(names) if any(r[5 + k] == "Active" for r in rows)]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def interact_traffic():
+    """DRAM bytes per launch of the interaction kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2012_06925_gb300", "csrc", "interact.cu")
+    path = os.path.join(ROOT, "profiles", "interact_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        with open(src, "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()
+        if d.get("interact_cu_sha256") == h:
+            return d.get("dram_bytes_per_launch_full_size")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2012_06925_gb300 import binding as B
+    from paper_2012_06925_gb300 import build as builder
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    builder.build()
+    B.load_library()
+
+    cfg, tgt, q, kw = workload()
+    M = tgt.shape[1]
+    dt = torch.from_numpy(tgt).cuda()
+    dq = torch.from_numpy(q).cuda()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def step(precision, phi):
+        plan = B.Plan(dt, dt, dq, precision=precision, stream=stream, **kw)
+        plan.compute(phi, stream=stream)
+        return plan
+
+    # Accuracy gate: FP32-bulk against the plain FP64 BLDTT on the same inputs.
+    phi64 = torch.empty(M, dtype=torch.float64, device="cuda")
+    phi32 = torch.empty(M, dtype=torch.float64, device="cuda")
+    p64 = step(B.FP64, phi64)
+    p64.check_error()
+    st64 = p64.stats()
+    p64.close()
+    p32 = step(B.FP32_BULK, phi32)
+    p32.check_error()
+    p32.close()
+    a64, a32 = phi64.cpu().numpy(), phi32.cpu().numpy()
+    rel_l2 = float(np.sqrt(np.sum((a64 - a32) ** 2) / np.sum(a64 ** 2)))
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step(B.FP32_BULK, phi32).close()
+
+    barrier()
+    times, st_list = [], []
+    with ClockSampler(local) as clocks:
+        for _ in range(args.steps):
+            flush.fill_(float(len(times)))                   # evict L2 between steps
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan = step(B.FP32_BULK, phi32)
+            e1.record(stream)
+            st_list.append(plan.stats())                     # synchronises
+            plan.close()
+            times.append(e0.elapsed_time(e1))
+    barrier()
+    total_ms = sum(times)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    st = st_list[-1]
+    value = M * args.steps * world / (total_ms / 1000.0)
+    ms_interact = statistics.mean(s["ms_interact"] for s in st_list)
+    evals = sum(st["interactions"])
+    flops = FLOPS_PER_EVAL.get(kw["kernel"], 20.0) * evals
+    achieved = flops / (ms_interact / 1000.0) / 1e12
+    props = torch.cuda.get_device_properties(local)
+    sm_max = measured_peaks().get("sm_max_mhz", 2070.0)
+    peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    csum = clocks.summary()
+    launches = sum(s["launches_setup"] + s["launches_compute"] for s in st_list)
+
+    # FP64 comparator: the plain FP64 BLDTT step.
+    fp64 = None
+    if not args.no_fp64:
+        flush.fill_(3.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan = step(B.FP64, phi64)
+        e1.record(stream)
+        s64 = plan.stats()
+        plan.close()
+        ms64 = e0.elapsed_time(e1)
+        fp64 = {"value": M / (ms64 / 1000.0), "unit": UNIT, "ms_per_step": ms64,
+                "ms_interact": s64["ms_interact"]}
+
+    # End to end through the public API from pinned host buffers.
+    ht = torch.from_numpy(tgt).pin_memory()
+    hq = torch.from_numpy(q).pin_memory()
+    host_phi = torch.empty(M, dtype=torch.float64).pin_memory()
+    e2e_times = []
+    import ctypes
+    lib = B.load_library()
+    st_buf = B.Stats()
+    for i in range(1 + max(1, min(3, args.steps))):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc = lib.bldtt_solve_host(ctypes.cast(ht.data_ptr(), ctypes.POINTER(ctypes.c_double)), M,
+                                  ctypes.cast(ht.data_ptr(), ctypes.POINTER(ctypes.c_double)), M,
+                                  ctypes.cast(hq.data_ptr(), ctypes.POINTER(ctypes.c_double)),
+                                  kw["kernel"], kw["kappa"], kw["n"], kw["theta"], kw["N0"],
+                                  kw["M0"], B.FP32_BULK,
+                                  ctypes.cast(host_phi.data_ptr(), ctypes.POINTER(ctypes.c_double)),
+                                  ctypes.byref(st_buf))
+        t1 = time.perf_counter()
+        B._check(rc)
+        if i > 0:
+            e2e_times.append(t1 - t0)
+    e2e = {"value": M / statistics.median(e2e_times), "unit": UNIT,
+           "h2d_bytes_per_step": int(ht.numel() * 8 + hq.numel() * 8),
+           "d2h_bytes_per_step": int(M * 8), "seconds": statistics.median(e2e_times)}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            cb = oracle_rate(leaf=0, count=2000)
+            cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        except Exception as exc:   # reported, not fatal
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"failed: {exc}"[:300]}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_dict(cfg),
+        "rel_l2_vs_fp64": rel_l2, "accuracy_ok": rel_l2 <= 1e-6,
+        "phases_ms": {"tree": st["ms_tree"], "lists": st["ms_lists"], "upward": st["ms_upward"],
+                      "interact": st["ms_interact"], "downward": st["ms_downward"],
+                      "compute": st["ms_compute"]},
+        "interactions": {"PP": st["interactions"][0], "PC": st["interactions"][1],
+                         "CP": st["interactions"][2], "CC": st["interactions"][3],
+                         "executed_with_padding": st["executed_evaluations"]},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": interact_traffic(),
+                     "kernel": "k_interact<FP32,Coulomb>",
+                     "flops_per_launch": flops, "ms_per_launch": ms_interact,
+                     "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
+                                   f"{sm_max:.0f} MHz",
+                     "frac_at_sampled_clock": (achieved / peak * sm_max / csum["sm_mhz"])
+                     if csum.get("sm_mhz") else None},
+        "fp64_plain": fp64,
+        "speedup_vs_fp64": (value / world) / fp64["value"] if fp64 else None,
+        "e2e": e2e, "gpu_launches": launches, "clocks": csum, "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

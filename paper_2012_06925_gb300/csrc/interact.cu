@@ -19,9 +19,11 @@
 // targets per thread against every staged source.
 //
 // FP32_BULK: pool entries are float4 (y - c, q) in the frame of the source
-// segment's centre c (a leaf centre or a cluster centre).  Targets are held
-// as double-float pairs and moved into that frame once per segment, so the
-// coordinate rounding error is relative to the cluster size, not to |x|.
+// segment's centre c (a leaf centre or a cluster centre), rounded once from
+// the FP64 difference.  Targets keep FP64 coordinates and are moved into each
+// segment's frame with the same expression, (float)(x - c), so the coordinate
+// rounding error is relative to the cluster size, not to |x|, and a target
+// that coincides with a source gets exactly the same FP32 coordinates (r = 0).
 // Each chunk is summed in FP32 and added to an FP64 accumulator.
 // FP64: pool entries are double4 (y, q) in absolute coordinates.
 //
@@ -72,8 +74,7 @@ struct InteractView {
 struct StageMeta {
   int item;
   int flags;
-  float ch[3];   // segment centre, high parts
-  float cl[3];   // segment centre, low parts
+  double c[3];   // segment centre (frame origin of the staged FP32 sources)
 };
 
 // ---- PTX helpers: mbarrier, bulk copy, timer -------------------------------
@@ -213,11 +214,7 @@ struct Producer {
 
   // Stream one segment (pool offset, entries, centre) in kChunk pieces.
   __device__ bool segment(int64_t off, int64_t len, const double* c) {
-    float ch[3], cl[3];
-    for (int d = 0; d < 3; ++d) {
-      ch[d] = (float)c[d];
-      cl[d] = (float)(c[d] - (double)ch[d]);
-    }
+    const double c0 = c[0], c1 = c[1], c2 = c[2];
     const Vec* src = reinterpret_cast<const Vec*>(v.pool) + off;
     for (int64_t k = 0; k < len; k += kChunk) {
       int s;
@@ -225,10 +222,9 @@ struct Producer {
       StageMeta& m = meta[s];
       m.item = cur_item;
       m.flags = k == 0 ? kFlagNewSegment : 0;
-      for (int d = 0; d < 3; ++d) {
-        m.ch[d] = ch[d];
-        m.cl[d] = cl[d];
-      }
+      m.c[0] = c0;
+      m.c[1] = c1;
+      m.c[2] = c2;
       mbar_arrive_tx(&full[s], (uint32_t)(kChunk * sizeof(Vec)));
       bulk_copy_g2s(buf[s], src + k, (uint32_t)(kChunk * sizeof(Vec)), &full[s]);
       ++it;
@@ -417,7 +413,7 @@ __global__ void __launch_bounds__(kThreads) k_interact(InteractView v) {
   int4 item = make_int4(0, 0, 0, 0);
   double acc[kTargetsPerThread];
   double X[kTargetsPerThread][3];
-  float xh[kTargetsPerThread][3], xl[kTargetsPerThread][3], xr[kTargetsPerThread][3];
+  float xr[kTargetsPerThread][3];
   for (uint32_t it = 0;; ++it) {
     const int s = (int)(it % kStages);
     if (!mbar_wait(&full[s], (it / kStages) & 1u, v.err)) return;
@@ -431,24 +427,17 @@ __global__ void __launch_bounds__(kThreads) k_interact(InteractView v) {
       for (int k = 0; k < kTargetsPerThread; ++k) {
         acc[k] = 0.0;
         target_coords(v, item, k * kConsumers + ct, X[k][0], X[k][1], X[k][2]);
-        if (F32) {
-          for (int d = 0; d < 3; ++d) {
-            xh[k][d] = (float)X[k][d];
-            xl[k][d] = (float)(X[k][d] - (double)xh[k][d]);
-          }
-        }
       }
     }
     if (F32) {
       if (smeta[s].flags & kFlagNewSegment) {
-        float ch[3], cl[3];
-        for (int d = 0; d < 3; ++d) {
-          ch[d] = smeta[s].ch[d];
-          cl[d] = smeta[s].cl[d];
-        }
+        const double c0 = smeta[s].c[0], c1 = smeta[s].c[1], c2 = smeta[s].c[2];
 #pragma unroll
-        for (int k = 0; k < kTargetsPerThread; ++k)
-          for (int d = 0; d < 3; ++d) xr[k][d] = (xh[k][d] - ch[d]) + (xl[k][d] - cl[d]);
+        for (int k = 0; k < kTargetsPerThread; ++k) {
+          xr[k][0] = (float)(X[k][0] - c0);
+          xr[k][1] = (float)(X[k][1] - c1);
+          xr[k][2] = (float)(X[k][2] - c2);
+        }
       }
       float a[kTargetsPerThread];
       const float4* sb = reinterpret_cast<const float4*>(sbuf[s]);
