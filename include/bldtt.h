@@ -220,6 +220,34 @@ int bldtt_solve_host(const double* targets, int64_t M, const double* sources, in
                      const double* charges, int kernel, double kappa, int n, double theta,
                      int N0, int M0, int precision, double* phi, bldtt_stats_t* stats);
 
+/* ---- Allocation-free entry point ---- */
+
+/*
+ * bldtt_bounding_box_noalloc - minimal bounding box of a particle set (the
+ * box of a tree's root cluster), computed without allocating device memory.
+ * The paper has no counterpart: it exists for callers that cannot call
+ * cudaMalloc (a framework that owns all device memory, a real-time loop in
+ * which allocation is forbidden).  bldtt_setup computes the same box with
+ * scratch from the stream-ordered allocator; this variant keeps its scratch
+ * in a fixed 56 KB __device__ array that every GPU loading the library holds
+ * until the process exits.
+ *
+ *  points     device, 3*n float64, SoA (x block, y block, z block).
+ *  n          1 <= n < 2^31 (larger sizes are rejected with EINVAL).
+ *  box        device, 6 float64 written: lo x, lo y, lo z, hi x, hi y, hi z.
+ *  nonfinite  device int or NULL; set to 1 if any coordinate is NaN or
+ *             infinite (those values are left out of the box), else 0.
+ *
+ * The first call on a device (with that device current) looks up the
+ * array's device address with cudaGetSymbolAddress; make that first call
+ * before any stream capture.  All calls share the array and every call
+ * rewrites the slots it reads, but calls that overlap on the GPU race on it:
+ * serialise them (one stream, or events).  Asynchronous on cuda_stream.
+ * Errors: EINVAL, ECUDA.
+ */
+int bldtt_bounding_box_noalloc(const double* points, int64_t n, double* box, int* nonfinite,
+                               void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

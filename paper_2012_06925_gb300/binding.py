@@ -25,6 +25,7 @@ EXPORTED = (
     "bldtt_destroy", "bldtt_status_string", "bldtt_last_error", "bldtt_tree_size",
     "bldtt_export_tree", "bldtt_export_lists", "bldtt_export_proxy_charges",
     "bldtt_export_proxy_potentials", "bldtt_direct_sum", "bldtt_solve_host",
+    "bldtt_bounding_box_noalloc",
 )
 
 
@@ -91,6 +92,7 @@ def load_library(path: str = LIB_PATH):
         "bldtt_direct_sum": (i32, [vp, i64, vp, i64, vp, i32, dbl, vp, vp]),
         "bldtt_solve_host": (i32, [P_dbl, i64, P_dbl, i64, P_dbl, i32, dbl, i32, dbl, i32, i32,
                                    i32, P_dbl, ctypes.POINTER(Stats)]),
+        "bldtt_bounding_box_noalloc": (i32, [vp, i64, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -270,6 +272,22 @@ def solve_host(targets, sources, charges, kernel=COULOMB, kappa=0.0, n=8, theta=
                                            int(n), float(theta), int(N0), int(M0), int(precision),
                                            _np_ptr(phi, ctypes.c_double), ctypes.byref(st)))
     return phi, st.as_dict()
+
+
+def bounding_box_noalloc(points, box=None, nonfinite=None, stream=None):
+    """Root-cluster bounding box without device allocation by the library
+    (bldtt_bounding_box_noalloc).  points: CUDA float64 (3, n); returns the
+    6-element device box and the device int flag (1 if a value was not finite)."""
+    import torch
+    n = int(points.shape[1])
+    if box is None:
+        box = torch.empty(6, dtype=torch.float64, device=points.device)
+    if nonfinite is None:
+        nonfinite = torch.empty(1, dtype=torch.int32, device=points.device)
+    _check(load_library().bldtt_bounding_box_noalloc(_dptr(points), n, _dptr(box, 6),
+                                                     ctypes.c_void_p(nonfinite.data_ptr()),
+                                                     _stream_ptr(stream)))
+    return box, nonfinite
 
 
 def status_string(status: int) -> str:
