@@ -1,5 +1,6 @@
 // C ABI of the library (declared, with argument conventions, in include/bldtt.h).
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -73,6 +74,7 @@ void release(bldtt_plan* p) {
   p->pool = nullptr;
   dfree_ptr(p->items, s);
   dfree_ptr(p->item_counter, s);
+  dfree_ptr(p->chunk_frame, s);
   dfree_ptr(p->qhat, s);
   dfree_ptr(p->phit, s);
   dfree_ptr(p->phi_near, s);
@@ -97,6 +99,7 @@ int setup_impl(bldtt_plan* p, const double* targets, const double* sources, cons
   BL_CUDA(cudaEventRecord(p->ev[0], s));
   BL_TRY(build_tree(p->tt, targets, (int32_t)p->M, p->M0, p->n, bad, s, p->setup_counter));
   BL_TRY(build_tree(p->st, sources, (int32_t)p->N, p->N0, p->n, bad, s, p->setup_counter));
+  BL_TRY(morton_order_leaves(p->st, s, p->setup_counter));
   BL_TRY(dalloc_n(&p->q_tree, p->N, s));
   BL_TRY(permute_charges(p, charges, s));
   BL_TRY(check_finite(p->q_tree, p->N, bad, s, p->setup_counter));
@@ -117,6 +120,9 @@ int setup_impl(bldtt_plan* p, const double* targets, const double* sources, cons
   BL_TRY(dalloc_n(&p->phit, (size_t)p->tt.nclusters * p->np, s));
   BL_TRY(dalloc_n(&p->phi_near, (size_t)p->M, s));
   BL_TRY(dalloc_n(&p->item_counter, 1, s));
+  BL_TRY(build_chunk_frames(p, s));
+  p->interact_layout = 0;
+  if (const char* lay = std::getenv("BLDTT_INTERACT_LAYOUT")) p->interact_layout = std::atoi(lay) ? 1 : 0;
   BL_TRY(interaction_grid(p, &p->interact_grid));
   BL_CUDA(cudaEventRecord(p->ev[2], s));
   BL_CUDA(cudaStreamSynchronize(s));
@@ -274,7 +280,7 @@ int bldtt_stats(bldtt_plan* p, bldtt_stats_t* out) {
   out->executed_evaluations = p->executed_evaluations;
   out->work_items = p->nitems;
   out->interact_grid = p->interact_grid;
-  out->interact_threads = (kConsumerWarps + 1) * 32;
+  out->interact_threads = p->interact_threads;
   out->ms_tree = p->ms_tree;
   out->ms_lists = p->ms_lists;
   if (p->have_compute_events) {

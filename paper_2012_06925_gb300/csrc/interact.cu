@@ -15,20 +15,27 @@
 // Per CTA, one producer warp grabs items from a global counter, walks their
 // lists and streams the sources, kChunk at a time, from the source pool into
 // a kStages-deep shared-memory ring with cp.async.bulk (TMA) copies that
-// complete on mbarriers; four consumer warps evaluate G for kTargetsPerThread
-// targets per thread against every staged source.
+// complete on mbarriers; NCW consumer warps evaluate G for K targets per
+// thread against every staged source (NCW * 32 * K == kTile).
 //
-// FP32_BULK: pool entries are float4 (y - c, q) in the frame of the source
-// segment's centre c (a leaf centre or a cluster centre), rounded once from
-// the FP64 difference.  Targets keep FP64 coordinates and are moved into each
-// segment's frame with the same expression, (float)(x - c), so the coordinate
-// rounding error is relative to the cluster size, not to |x|, and a target
-// that coincides with a source gets exactly the same FP32 coordinates (r = 0).
-// Each chunk is summed in FP32 and added to an FP64 accumulator.
+// FP32_BULK: every chunk of kChunk pool entries has its own frame centre c, a
+// float near the chunk (particles inside a source leaf are in Morton order, so
+// a chunk is spatially compact).  Entries hold y - c in FP32, formed from the
+// split y = hi + lo (hi = fl(y), lo = fl(y - hi)) as fl(fl(hi - c) + lo), and
+// are stored as pair records {x0,x1, y0,y1, z0,z1, q0,q1} so that one target
+// meets two sources in packed f32x2 arithmetic (7 packed FP32 instructions and
+// 2 MUFU.RSQ per two Coulomb evaluations).  Targets keep the same split and
+// are moved into each chunk's frame with the same expression, so the
+// coordinate rounding error is relative to the chunk size, and a target that
+// coincides with a source gets exactly the same FP32 coordinates (r = 0).
+// The two halves of the packed accumulator are two interleaved partial sums;
+// each chunk's sum is added into an FP64 accumulator.
 // FP64: pool entries are double4 (y, q) in absolute coordinates.
+// Chunks carry their real source count, so padding is neither copied nor
+// evaluated.
 //
 // A pair at distance 0 contributes nothing.  The fast path evaluates
-// 1/sqrt(r^2) unguarded; a chunk whose FP32/FP64 partial is not finite (only
+// 1/sqrt(r^2) unguarded; a chunk whose partial sum is not finite (only
 // possible when some r^2 == 0) is recomputed by the warp with the guard.
 #include <type_traits>
 
@@ -36,10 +43,7 @@
 
 namespace bldtt {
 
-constexpr int kThreads = (kConsumerWarps + 1) * 32;
-constexpr int kConsumers = kConsumerWarps * 32;
 constexpr uint64_t kWaitNs = 20ull * 1000ull * 1000ull * 1000ull;   // 20 s bound on any wait
-constexpr int kFlagNewSegment = 1;
 
 struct InteractView {
   const int4* items;
@@ -52,9 +56,8 @@ struct InteractView {
   const int32_t* t_parent;
   const int32_t* s_leaf_first;
   const int32_t* s_leaf_last;
-  const int32_t* s_leaf_ids;
   const int32_t* pad_prefix;
-  const double* s_center;
+  const float4* chunk_frame;   // [chunks]: frame centre x, y, z (FP32) and the real count (int bits)
   int32_t np_pad;
   int64_t proxy_base;
   const void* pool;
@@ -73,8 +76,8 @@ struct InteractView {
 
 struct StageMeta {
   int item;
-  int flags;
-  double c[3];   // segment centre (frame origin of the staged FP32 sources)
+  int count;                    // real sources in the staged chunk
+  unsigned long long c2[3];     // frame centre, each component duplicated (f32x2)
 };
 
 // ---- PTX helpers: mbarrier, bulk copy, timer -------------------------------
@@ -145,51 +148,62 @@ __device__ __forceinline__ bool not_finite(double v) {
   return (__double_as_longlong(v) & 0x7ff0000000000000LL) == 0x7ff0000000000000LL;
 }
 
+// ---- packed FP32 (f32x2) helpers: low half = first element -----------------
+typedef unsigned long long f2_t;
+__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b) {
+  f2_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b) {
+  f2_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b) {
+  f2_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
+  f2_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2_t f2_pack(float lo, float hi) {
+  f2_t d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+__device__ __forceinline__ void f2_unpack(f2_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
 // ---- kernel functions (Sec. 4.6); d = x - y -------------------------------
-template <int KERN, typename T>
+template <typename T>
 __device__ __forceinline__ T poly_kernel(T dx, T dy, T dz) {
   return (T)1 + dx - (T)2 * dy + (T)3 * dz + dx * dy - dy * dz + dx * dx * dz * dz -
          (T)0.5 * dy * dy;
 }
 
-// Unguarded FP32 evaluation of q * G.
-template <int KERN>
+// q * G in FP32; GUARD makes a pair at r^2 == 0 contribute 0.
+template <int KERN, bool GUARD>
 __device__ __forceinline__ float pair_f32(float dx, float dy, float dz, float q, float nk) {
   float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-  if (KERN == BLDTT_COULOMB) {
-    return q * rsqrt_approx(r2);
-  } else if (KERN == BLDTT_YUKAWA) {
-    float ri = rsqrt_approx(r2);
-    return (q * ri) * exp2_approx(r2 * ri * nk);
-  } else {
-    return r2 > 0.f ? q * poly_kernel<KERN, float>(dx, dy, dz) : 0.f;
-  }
+  if (KERN == BLDTT_TEST_POLY) return r2 > 0.f ? q * poly_kernel<float>(dx, dy, dz) : 0.f;
+  if (GUARD && !(r2 > 0.f)) return 0.f;
+  float ri = rsqrt_approx(r2);
+  if (KERN == BLDTT_COULOMB) return q * ri;
+  return (q * ri) * exp2_approx(r2 * ri * nk);
 }
-// Guarded FP32 evaluation (r^2 == 0 contributes 0).
-template <int KERN>
-__device__ __forceinline__ float pair_f32_guarded(float dx, float dy, float dz, float q, float nk) {
-  float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-  if (!(r2 > 0.f)) return 0.f;
-  return pair_f32<KERN>(dx, dy, dz, q, nk);
-}
-template <int KERN>
+template <int KERN, bool GUARD>
 __device__ __forceinline__ double pair_f64(double dx, double dy, double dz, double q, double kappa) {
   double r2 = dx * dx + dy * dy + dz * dz;
-  if (KERN == BLDTT_COULOMB) {
-    return q * rsqrt(r2);
-  } else if (KERN == BLDTT_YUKAWA) {
-    double ri = rsqrt(r2);
-    return q * ri * exp(-kappa * (r2 * ri));
-  } else {
-    return r2 > 0.0 ? q * poly_kernel<KERN, double>(dx, dy, dz) : 0.0;
-  }
-}
-template <int KERN>
-__device__ __forceinline__ double pair_f64_guarded(double dx, double dy, double dz, double q,
-                                                   double kappa) {
-  double r2 = dx * dx + dy * dy + dz * dz;
-  if (!(r2 > 0.0)) return 0.0;
-  return pair_f64<KERN>(dx, dy, dz, q, kappa);
+  if (KERN == BLDTT_TEST_POLY) return r2 > 0.0 ? q * poly_kernel<double>(dx, dy, dz) : 0.0;
+  if (GUARD && !(r2 > 0.0)) return 0.0;
+  double ri = rsqrt(r2);
+  if (KERN == BLDTT_COULOMB) return q * ri;
+  return q * ri * exp(-kappa * (r2 * ri));
 }
 
 // ---- producer: walks an item's segments ------------------------------------
@@ -212,34 +226,39 @@ struct Producer {
     return mbar_wait(&empty[s], ((it / kStages) & 1u) ^ 1u, v.err);
   }
 
-  // Stream one segment (pool offset, entries, centre) in kChunk pieces.
-  __device__ bool segment(int64_t off, int64_t len, const double* c) {
-    const double c0 = c[0], c1 = c[1], c2 = c[2];
-    const Vec* src = reinterpret_cast<const Vec*>(v.pool) + off;
+  // Stream pool entries [off, off + len) in kChunk pieces (real entries only).
+  __device__ bool segment(int64_t off, int64_t len) {
     for (int64_t k = 0; k < len; k += kChunk) {
       int s;
       if (!acquire(s)) return false;
+      const int64_t q = (off + k) / kChunk;
+      const float4 f = v.chunk_frame[q];
+      const int count = __float_as_int(f.w);
       StageMeta& m = meta[s];
       m.item = cur_item;
-      m.flags = k == 0 ? kFlagNewSegment : 0;
-      m.c[0] = c0;
-      m.c[1] = c1;
-      m.c[2] = c2;
-      mbar_arrive_tx(&full[s], (uint32_t)(kChunk * sizeof(Vec)));
-      bulk_copy_g2s(buf[s], src + k, (uint32_t)(kChunk * sizeof(Vec)), &full[s]);
+      m.count = count;
+      uint32_t bytes;
+      if (std::is_same<Vec, float4>::value) {
+        m.c2[0] = f2_pack(f.x, f.x);
+        m.c2[1] = f2_pack(f.y, f.y);
+        m.c2[2] = f2_pack(f.z, f.z);
+        bytes = (uint32_t)(((count + 1) / 2) * 32);          // whole pair records
+      } else {
+        bytes = (uint32_t)(count * sizeof(Vec));
+      }
+      const char* src = reinterpret_cast<const char*>(v.pool) + (off + k) * (int64_t)sizeof(Vec);
+      mbar_arrive_tx(&full[s], bytes);
+      bulk_copy_g2s(buf[s], src, bytes, &full[s]);
       ++it;
     }
     return true;
   }
 
-  // Particles of every source leaf under cluster s (one segment per leaf).
+  // Particles of all source leaves under cluster s: one contiguous pool range,
+  // because leaves under a cluster are consecutive in leaf order.
   __device__ bool leaves_of(int32_t s) {
-    for (int32_t lf = v.s_leaf_first[s]; lf < v.s_leaf_last[s]; ++lf) {
-      int64_t o = v.pad_prefix[lf];
-      int64_t len = v.pad_prefix[lf + 1] - o;
-      if (!segment(o, len, v.s_center + (int64_t)v.s_leaf_ids[lf] * 3)) return false;
-    }
-    return true;
+    int64_t o = v.pad_prefix[v.s_leaf_first[s]];
+    return segment(o, v.pad_prefix[v.s_leaf_last[s]] - o);
   }
 
   __device__ bool lists(int type_particles, int type_proxies, int32_t c) {
@@ -247,11 +266,8 @@ struct Producer {
     for (int32_t e = v.list_ptr[k0]; e < v.list_ptr[k0 + 1]; ++e)
       if (!leaves_of(v.list_src[e])) return false;
     int64_t k1 = (int64_t)type_proxies * v.nct + c;
-    for (int32_t e = v.list_ptr[k1]; e < v.list_ptr[k1 + 1]; ++e) {
-      int32_t s = v.list_src[e];
-      if (!segment(v.proxy_base + (int64_t)s * v.np_pad, v.np_pad, v.s_center + (int64_t)s * 3))
-        return false;
-    }
+    for (int32_t e = v.list_ptr[k1]; e < v.list_ptr[k1 + 1]; ++e)
+      if (!segment(v.proxy_base + (int64_t)v.list_src[e] * v.np_pad, v.np_pad)) return false;
     return true;
   }
 
@@ -273,7 +289,6 @@ struct Producer {
       int s;
       if (acquire(s)) {
         meta[s].item = -1;
-        meta[s].flags = 0;
         mbar_arrive(&full[s]);
         ++it;
         return;
@@ -286,63 +301,87 @@ struct Producer {
 };
 
 // ---- consumers --------------------------------------------------------------
+// Packed evaluation of target k against the source pair (s0, s1):
+// acc += (q0 G(x - s0), q1 G(x - s1)).
 template <int KERN>
-__device__ __forceinline__ void chunk_f32(const float4* __restrict__ sb, const float (&xr)[kTargetsPerThread][3],
-                                          float (&a)[kTargetsPerThread], float nk) {
+__device__ __forceinline__ f2_t pair2_f32(f2_t tx, f2_t ty, f2_t tz, const ulonglong2& a,
+                                          const ulonglong2& b, f2_t acc, f2_t nk2) {
+  const f2_t dx = f2_sub(tx, a.x), dy = f2_sub(ty, a.y), dz = f2_sub(tz, b.x);
+  const f2_t r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
+  float r0, r1;
+  f2_unpack(r2, r0, r1);
+  const f2_t ri = f2_pack(rsqrt_approx(r0), rsqrt_approx(r1));
+  if (KERN == BLDTT_COULOMB) return f2_fma(b.y, ri, acc);
+  // Yukawa: q ri exp2(-kappa log2(e) r), r = r2 ri
+  float e0, e1;
+  f2_unpack(f2_mul(f2_mul(r2, ri), nk2), e0, e1);
+  return f2_fma(f2_mul(b.y, ri), f2_pack(exp2_approx(e0), exp2_approx(e1)), acc);
+}
+
+// Sum over the staged chunk of q G for K targets; two partial sums per target.
+template <int KERN, int K>
+__device__ __forceinline__ void chunk_f32(const ulonglong2* __restrict__ sb, int npairs,
+                                          const f2_t (&x2)[K][3], float (&a)[K], float nk) {
+  f2_t acc[K];
+  const f2_t nk2 = f2_pack(nk, nk);
 #pragma unroll
-  for (int k = 0; k < kTargetsPerThread; ++k) a[k] = 0.f;
+  for (int k = 0; k < K; ++k) acc[k] = 0ull;
+  if (npairs == kChunk / 2) {
 #pragma unroll 8
-  for (int j = 0; j < kChunk; ++j) {
-    const float4 p = sb[j];
+    for (int jp = 0; jp < kChunk / 2; ++jp) {
+      const ulonglong2 A = sb[2 * jp], Bq = sb[2 * jp + 1];
 #pragma unroll
-    for (int k = 0; k < kTargetsPerThread; ++k) {
-      float dx = xr[k][0] - p.x, dy = xr[k][1] - p.y, dz = xr[k][2] - p.z;
-      if (KERN == BLDTT_COULOMB) {
-        float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        a[k] = fmaf(p.w, rsqrt_approx(r2), a[k]);
-      } else {
-        a[k] += pair_f32<KERN>(dx, dy, dz, p.w, nk);
-      }
+      for (int k = 0; k < K; ++k) acc[k] = pair2_f32<KERN>(x2[k][0], x2[k][1], x2[k][2], A, Bq, acc[k], nk2);
+    }
+  } else {
+    for (int jp = 0; jp < npairs; ++jp) {
+      const ulonglong2 A = sb[2 * jp], Bq = sb[2 * jp + 1];
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[k] = pair2_f32<KERN>(x2[k][0], x2[k][1], x2[k][2], A, Bq, acc[k], nk2);
     }
   }
-}
-
-template <int KERN>
-__device__ __noinline__ void chunk_f32_guarded(const float4* __restrict__ sb,
-                                               const float (&xr)[kTargetsPerThread][3],
-                                               float (&a)[kTargetsPerThread], float nk) {
-  for (int k = 0; k < kTargetsPerThread; ++k) a[k] = 0.f;
-  for (int j = 0; j < kChunk; ++j) {
-    const float4 p = sb[j];
-    for (int k = 0; k < kTargetsPerThread; ++k)
-      a[k] += pair_f32_guarded<KERN>(xr[k][0] - p.x, xr[k][1] - p.y, xr[k][2] - p.z, p.w, nk);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    float lo, hi;
+    f2_unpack(acc[k], lo, hi);
+    a[k] = lo + hi;
   }
 }
 
-template <int KERN>
-__device__ __forceinline__ void chunk_f64(const double4* __restrict__ sb,
-                                          const double (&x)[kTargetsPerThread][3],
-                                          double (&a)[kTargetsPerThread], double kappa) {
+// Scalar re-evaluation with the r = 0 guard (rare: only chunks that produced a
+// non-finite partial sum), and the test kernel.
+template <int KERN, int K>
+__device__ __forceinline__ void chunk_f32_guarded(const float* __restrict__ sf, int count,
+                                                  const f2_t (&x2)[K][3], float (&a)[K], float nk) {
+  float xs[K][3];
 #pragma unroll
-  for (int k = 0; k < kTargetsPerThread; ++k) a[k] = 0.0;
+  for (int k = 0; k < K; ++k) {
+    float hi;
+    f2_unpack(x2[k][0], xs[k][0], hi);
+    f2_unpack(x2[k][1], xs[k][1], hi);
+    f2_unpack(x2[k][2], xs[k][2], hi);
+    a[k] = 0.f;
+  }
+  for (int j = 0; j < count; ++j) {
+    const float* r = sf + (j >> 1) * 8 + (j & 1);   // pair record: x0 x1 y0 y1 z0 z1 q0 q1
+    const float sx = r[0], sy = r[2], sz = r[4], q = r[6];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      a[k] += pair_f32<KERN, true>(xs[k][0] - sx, xs[k][1] - sy, xs[k][2] - sz, q, nk);
+  }
+}
+
+template <int KERN, bool GUARD, int K>
+__device__ __forceinline__ void chunk_f64(const double4* __restrict__ sb, int count,
+                                          const double (&x)[K][3], double (&a)[K], double kappa) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) a[k] = 0.0;
 #pragma unroll 4
-  for (int j = 0; j < kChunk; ++j) {
+  for (int j = 0; j < count; ++j) {
     const double4 p = sb[j];
 #pragma unroll
-    for (int k = 0; k < kTargetsPerThread; ++k)
-      a[k] += pair_f64<KERN>(x[k][0] - p.x, x[k][1] - p.y, x[k][2] - p.z, p.w, kappa);
-  }
-}
-
-template <int KERN>
-__device__ __noinline__ void chunk_f64_guarded(const double4* __restrict__ sb,
-                                               const double (&x)[kTargetsPerThread][3],
-                                               double (&a)[kTargetsPerThread], double kappa) {
-  for (int k = 0; k < kTargetsPerThread; ++k) a[k] = 0.0;
-  for (int j = 0; j < kChunk; ++j) {
-    const double4 p = sb[j];
-    for (int k = 0; k < kTargetsPerThread; ++k)
-      a[k] += pair_f64_guarded<KERN>(x[k][0] - p.x, x[k][1] - p.y, x[k][2] - p.z, p.w, kappa);
+    for (int k = 0; k < K; ++k)
+      a[k] += pair_f64<KERN, GUARD>(x[k][0] - p.x, x[k][1] - p.y, x[k][2] - p.z, p.w, kappa);
   }
 }
 
@@ -369,38 +408,36 @@ __device__ __forceinline__ void target_coords(const InteractView& v, const int4&
   }
 }
 
-__device__ __forceinline__ void store_outputs(const InteractView& v, const int4& item, int ct,
-                                              const double (&acc)[kTargetsPerThread]) {
-#pragma unroll
-  for (int k = 0; k < kTargetsPerThread; ++k) {
-    int r = k * kConsumers + ct;
-    if (r < item.z) {
-      if (item.w == kItemParticles)
-        v.phi_near[(int64_t)item.y + r] = acc[k];
-      else
-        v.phit[(int64_t)item.x * v.np + item.y + r] = acc[k];
-    }
+__device__ __forceinline__ void store_output(const InteractView& v, const int4& item, int r,
+                                             double value) {
+  if (r < item.z) {
+    if (item.w == kItemParticles)
+      v.phi_near[(int64_t)item.y + r] = value;
+    else
+      v.phit[(int64_t)item.x * v.np + item.y + r] = value;
   }
 }
 
-template <bool F32, int KERN>
-__global__ void __launch_bounds__(kThreads) k_interact(InteractView v) {
+template <bool F32, int KERN, int NCW, int K>
+__global__ void __launch_bounds__((NCW + 1) * 32) k_interact(InteractView v) {
+  static_assert(NCW * 32 * K == kTile, "a CTA covers exactly one work-item tile");
+  constexpr int kConsumers = NCW * 32;
   using Vec = typename std::conditional<F32, float4, double4>::type;
   __shared__ __align__(128) Vec sbuf[kStages][kChunk];
-  __shared__ StageMeta smeta[kStages];
+  __shared__ __align__(16) StageMeta smeta[kStages];
   __shared__ __align__(8) uint64_t full[kStages];
   __shared__ __align__(8) uint64_t empty[kStages];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kConsumerWarps);
+      mbar_init(&empty[s], NCW);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
 
-  if (warp == kConsumerWarps) {
+  if (warp == NCW) {
     if (lane == 0) {
       Producer<Vec> prod(v, sbuf, smeta, full, empty);
       prod.run();
@@ -411,82 +448,112 @@ __global__ void __launch_bounds__(kThreads) k_interact(InteractView v) {
   const int ct = threadIdx.x;   // consumer thread 0..kConsumers-1
   int cur = -1;
   int4 item = make_int4(0, 0, 0, 0);
-  double acc[kTargetsPerThread];
-  double X[kTargetsPerThread][3];
-  float xr[kTargetsPerThread][3];
+  double X[K][3];               // FP64 targets (FP64 path)
+  f2_t xh2[K][3], xl2[K][3];    // FP32 split of the targets, each duplicated (FP32 path)
+  double acc[K];
   for (uint32_t it = 0;; ++it) {
     const int s = (int)(it % kStages);
     if (!mbar_wait(&full[s], (it / kStages) & 1u, v.err)) return;
     const int mi = smeta[s].item;
     if (mi != cur) {
-      if (cur >= 0) store_outputs(v, item, ct, acc);
+      if (cur >= 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) store_output(v, item, k * kConsumers + ct, acc[k]);
+      }
       if (mi < 0) return;
       cur = mi;
       item = v.items[mi];
 #pragma unroll
-      for (int k = 0; k < kTargetsPerThread; ++k) {
+      for (int k = 0; k < K; ++k) {
         acc[k] = 0.0;
         target_coords(v, item, k * kConsumers + ct, X[k][0], X[k][1], X[k][2]);
-      }
-    }
-    if (F32) {
-      if (smeta[s].flags & kFlagNewSegment) {
-        const double c0 = smeta[s].c[0], c1 = smeta[s].c[1], c2 = smeta[s].c[2];
+        if (F32) {
 #pragma unroll
-        for (int k = 0; k < kTargetsPerThread; ++k) {
-          xr[k][0] = (float)(X[k][0] - c0);
-          xr[k][1] = (float)(X[k][1] - c1);
-          xr[k][2] = (float)(X[k][2] - c2);
+          for (int d = 0; d < 3; ++d) {
+            const float h = (float)X[k][d];
+            const float l = (float)(X[k][d] - (double)h);
+            xh2[k][d] = f2_pack(h, h);
+            xl2[k][d] = f2_pack(l, l);
+          }
         }
       }
-      float a[kTargetsPerThread];
-      const float4* sb = reinterpret_cast<const float4*>(sbuf[s]);
-      chunk_f32<KERN>(sb, xr, a, v.neg_kappa_log2e);
-      bool bad = false;
+    }
+    const int count = smeta[s].count;
+    if (F32) {
+      f2_t x2[K][3];
 #pragma unroll
-      for (int k = 0; k < kTargetsPerThread; ++k) bad = bad || not_finite(a[k]);
-      if (__any_sync(0xffffffffu, bad)) chunk_f32_guarded<KERN>(sb, xr, a, v.neg_kappa_log2e);
+      for (int d = 0; d < 3; ++d) {
+        const f2_t c2 = smeta[s].c2[d];
 #pragma unroll
-      for (int k = 0; k < kTargetsPerThread; ++k) acc[k] += (double)a[k];
+        for (int k = 0; k < K; ++k) x2[k][d] = f2_add(f2_sub(xh2[k][d], c2), xl2[k][d]);
+      }
+      float a[K];
+      if (KERN == BLDTT_TEST_POLY) {
+        chunk_f32_guarded<KERN, K>(reinterpret_cast<const float*>(sbuf[s]), count, x2, a,
+                                   v.neg_kappa_log2e);
+      } else {
+        chunk_f32<KERN, K>(reinterpret_cast<const ulonglong2*>(sbuf[s]), (count + 1) / 2, x2, a,
+                           v.neg_kappa_log2e);
+        bool bad = false;
+#pragma unroll
+        for (int k = 0; k < K; ++k) bad = bad || not_finite(a[k]);
+        if (__any_sync(0xffffffffu, bad))
+          chunk_f32_guarded<KERN, K>(reinterpret_cast<const float*>(sbuf[s]), count, x2, a,
+                                     v.neg_kappa_log2e);
+      }
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[k] += (double)a[k];
     } else {
-      double a[kTargetsPerThread];
       const double4* sb = reinterpret_cast<const double4*>(sbuf[s]);
-      chunk_f64<KERN>(sb, X, a, v.kappa);
-      bool bad = false;
+      double a[K];
+      chunk_f64<KERN, false, K>(sb, count, X, a, v.kappa);
+      if (KERN != BLDTT_TEST_POLY) {
+        bool bad = false;
 #pragma unroll
-      for (int k = 0; k < kTargetsPerThread; ++k) bad = bad || not_finite(a[k]);
-      if (__any_sync(0xffffffffu, bad)) chunk_f64_guarded<KERN>(sb, X, a, v.kappa);
+        for (int k = 0; k < K; ++k) bad = bad || not_finite(a[k]);
+        if (__any_sync(0xffffffffu, bad)) chunk_f64<KERN, true, K>(sb, count, X, a, v.kappa);
+      }
 #pragma unroll
-      for (int k = 0; k < kTargetsPerThread; ++k) acc[k] += a[k];
+      for (int k = 0; k < K; ++k) acc[k] += a[k];
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
   }
 }
 
+// Consumer layouts the kernel is instantiated for (NCW warps x K targets).
+struct Layout {
+  int ncw, k;
+};
+static const Layout kLayouts[] = {{4, 2}, {2, 4}};
+
 template <bool F32, int KERN>
-static const void* kernel_ptr() {
-  return reinterpret_cast<const void*>(&k_interact<F32, KERN>);
+static const void* kernel_for(int layout) {
+  return layout == 0 ? reinterpret_cast<const void*>(&k_interact<F32, KERN, 4, 2>)
+                     : reinterpret_cast<const void*>(&k_interact<F32, KERN, 2, 4>);
 }
 
-static const void* select_kernel(const bldtt_plan* p) {
+static const void* select_kernel(const bldtt_plan* p, int layout) {
   bool f32 = p->precision == BLDTT_FP32_BULK;
   switch (p->kernel) {
-    case BLDTT_COULOMB: return f32 ? kernel_ptr<true, BLDTT_COULOMB>() : kernel_ptr<false, BLDTT_COULOMB>();
-    case BLDTT_YUKAWA: return f32 ? kernel_ptr<true, BLDTT_YUKAWA>() : kernel_ptr<false, BLDTT_YUKAWA>();
-    default: return f32 ? kernel_ptr<true, BLDTT_TEST_POLY>() : kernel_ptr<false, BLDTT_TEST_POLY>();
+    case BLDTT_COULOMB: return f32 ? kernel_for<true, BLDTT_COULOMB>(layout) : kernel_for<false, BLDTT_COULOMB>(layout);
+    case BLDTT_YUKAWA: return f32 ? kernel_for<true, BLDTT_YUKAWA>(layout) : kernel_for<false, BLDTT_YUKAWA>(layout);
+    default: return f32 ? kernel_for<true, BLDTT_TEST_POLY>(layout) : kernel_for<false, BLDTT_TEST_POLY>(layout);
   }
 }
 
 int interaction_grid(bldtt_plan* p, int* grid) {
   int dev = 0, sms = 0, per_sm = 0;
+  const int threads = (kLayouts[p->interact_layout].ncw + 1) * 32;
   BL_CUDA(cudaGetDevice(&dev));
   BL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_kernel(p), kThreads, 0));
+  BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_kernel(p, p->interact_layout),
+                                                        threads, 0));
   if (per_sm < 1) per_sm = 1;
   int g = sms * per_sm;
   if (p->nitems > 0 && g > p->nitems) g = p->nitems;
   *grid = g < 1 ? 1 : g;
+  p->interact_threads = threads;
   return BLDTT_OK;
 }
 
@@ -504,9 +571,8 @@ int run_interactions(bldtt_plan* p, cudaStream_t s) {
   v.t_parent = tt.parent;
   v.s_leaf_first = st.leaf_first;
   v.s_leaf_last = st.leaf_last;
-  v.s_leaf_ids = st.leaf_ids;
   v.pad_prefix = p->pad_prefix;
-  v.s_center = st.center;
+  v.chunk_frame = p->chunk_frame;
   v.np_pad = p->np_pad;
   v.proxy_base = p->pool_particles;
   v.pool = p->pool;
@@ -523,7 +589,8 @@ int run_interactions(bldtt_plan* p, cudaStream_t s) {
   v.neg_kappa_log2e = (float)(-p->kappa * 1.4426950408889634);
   BL_CUDA(cudaMemsetAsync(p->item_counter, 0, sizeof(int32_t), s));
   void* args[] = {&v};
-  BL_CUDA(cudaLaunchKernel(select_kernel(p), dim3(p->interact_grid), dim3(kThreads), args, 0, s));
+  BL_CUDA(cudaLaunchKernel(select_kernel(p, p->interact_layout), dim3(p->interact_grid),
+                           dim3(p->interact_threads), args, 0, s));
   BL_LAUNCHED(p->compute_counter.launches);
   return BLDTT_OK;
 }

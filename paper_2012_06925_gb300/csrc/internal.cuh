@@ -29,9 +29,7 @@ namespace bldtt {
 constexpr int kMaxDegree = 16;                 // n <= 16  ->  P = n + 1 <= 17
 constexpr int kMaxP = kMaxDegree + 1;
 constexpr int kChunk = 64;                     // sources per staged chunk
-constexpr int kConsumerWarps = 4;              // interaction kernel: consumer warps per CTA
-constexpr int kTargetsPerThread = 2;           // interaction kernel: targets per consumer thread
-constexpr int kTile = kConsumerWarps * 32 * kTargetsPerThread;   // targets per work item
+constexpr int kTile = 256;                     // targets per work item of the interaction kernel
 constexpr int kStages = 6;                     // depth of the shared-memory ring
 
 enum ItemKind { kItemParticles = 0, kItemProxies = 1 };
@@ -142,6 +140,9 @@ struct bldtt_plan {
   int32_t* item_counter = nullptr;
   double executed_evaluations = 0.0;
   int interact_grid = 0;
+  int interact_threads = 0;
+  int interact_layout = 0;            // consumer layout: 0 = 4 warps x 2 targets, 1 = 2 warps x 4
+  float4* chunk_frame = nullptr;      // [pool chunks]: FP32 frame centre, real entries (int bits)
 
   // Compute-phase arrays.
   double* qhat = nullptr;             // [Cs][np] proxy charges
@@ -176,6 +177,8 @@ int check_finite(const double* v, int64_t n, int* bad_dev, cudaStream_t s, Count
 // ---- trees (tree.cu) ----
 int build_tree(Tree& T, const double* coords_user, int32_t n, int32_t max_leaf, int degree,
                int* bad_dev, cudaStream_t s, Counters& c);
+// Reorder the particles inside every leaf along a Morton curve of the leaf's box.
+int morton_order_leaves(Tree& T, cudaStream_t s, Counters& c);
 void free_tree(Tree& T, cudaStream_t s);
 
 // ---- traversal, lists and work items (dtt.cu) ----
@@ -186,6 +189,7 @@ int build_work_items(bldtt_plan* p, cudaStream_t s);
 int permute_charges(bldtt_plan* p, const double* charges_user, cudaStream_t s);
 int upward_pass(bldtt_plan* p, cudaStream_t s);
 int build_pool(bldtt_plan* p, cudaStream_t s);
+int build_chunk_frames(bldtt_plan* p, cudaStream_t s);
 int downward_pass(bldtt_plan* p, double* phi_user, cudaStream_t s);
 int configure_pass_kernels();
 

@@ -229,41 +229,56 @@ int upward_pass(bldtt_plan* p, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Source pool: leaf particles then proxy points, each block padded to kChunk
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void put(float4* pool, int64_t i, double x, double y, double z, double q,
-                                    const double* c) {
-  pool[i] = make_float4((float)(x - c[0]), (float)(y - c[1]), (float)(z - c[2]), (float)q);
+// FP32_BULK pool entries are relative to the frame centre c (a float) of their
+// chunk of kChunk entries: with the split v = hi + lo (hi = fl(v),
+// lo = fl(v - hi)) the entry is fl(fl(hi - c) + lo); the interaction kernel
+// moves its targets into each chunk's frame with the same expression.  A
+// chunk is stored as 32 pair records {x0,x1, y0,y1, z0,z1, q0,q1}.
+__device__ __forceinline__ float frame_coord(double v, float c) {
+  float vh = (float)v;
+  float vl = (float)(v - (double)vh);
+  return __fadd_rn(__fsub_rn(vh, c), vl);
 }
-__device__ __forceinline__ void put(double4* pool, int64_t i, double x, double y, double z, double q,
-                                    const double*) {
+
+__device__ __forceinline__ void put(float4* pool, const float4* frame, int64_t i, double x, double y,
+                                    double z, double q) {
+  const float4 f = frame[i / kChunk];
+  const int64_t j = i % kChunk;
+  float* r = reinterpret_cast<float*>(pool) + ((i / kChunk) * (kChunk / 2) + j / 2) * 8 + (j & 1);
+  r[0] = frame_coord(x, f.x);
+  r[2] = frame_coord(y, f.y);
+  r[4] = frame_coord(z, f.z);
+  r[6] = (float)q;
+}
+__device__ __forceinline__ void put(double4* pool, const float4*, int64_t i, double x, double y,
+                                    double z, double q) {
   pool[i] = make_double4(x, y, z, q);
 }
 
 template <typename Vec>
 __global__ void k_pool_particles(const int32_t* __restrict__ leaf_ids, const int32_t* __restrict__ begin,
                                  const int32_t* __restrict__ end, const int32_t* __restrict__ pad_prefix,
-                                 const double* __restrict__ center, const double* __restrict__ x,
+                                 const float4* __restrict__ frame, const double* __restrict__ x,
                                  const double* __restrict__ y, const double* __restrict__ z,
                                  const double* __restrict__ q, Vec* __restrict__ pool) {
   const int lf = blockIdx.x;
   const int c = leaf_ids[lf];
-  const double* cc = center + (int64_t)c * 3;
   const int64_t o = pad_prefix[lf];
   for (int32_t i = begin[c] + threadIdx.x; i < end[c]; i += blockDim.x)
-    put(pool, o + (i - begin[c]), x[i], y[i], z[i], q[i], cc);
+    put(pool, frame, o + (i - begin[c]), x[i], y[i], z[i], q[i]);
 }
 
 template <typename Vec>
 __global__ void k_pool_proxies(int n, int np_pad, int64_t base, const double* __restrict__ nodes,
-                               const double* __restrict__ center, const double* __restrict__ qhat,
+                               const float4* __restrict__ frame, const double* __restrict__ qhat,
                                Vec* __restrict__ pool) {
   const int c = blockIdx.x;
   const int P = n + 1, np = P * P * P;
   const double* nd = nodes + (int64_t)c * 3 * P;
-  const double* cc = center + (int64_t)c * 3;
   for (int k = threadIdx.x; k < np; k += blockDim.x) {
     int k1 = k / (P * P), k2 = (k / P) % P, k3 = k % P;
-    put(pool, base + (int64_t)c * np_pad + k, nd[k1], nd[P + k2], nd[2 * P + k3],
-        qhat[(int64_t)c * np + k], cc);
+    put(pool, frame, base + (int64_t)c * np_pad + k, nd[k1], nd[P + k2], nd[2 * P + k3],
+        qhat[(int64_t)c * np + k]);
   }
 }
 
@@ -275,19 +290,93 @@ int build_pool(bldtt_plan* p, cudaStream_t s) {
   BL_CUDA(cudaMemsetAsync(p->pool, 0, (size_t)p->pool_len * esz, s));
   if (f32) {
     k_pool_particles<float4><<<T.nleaves, 256, 0, s>>>(T.leaf_ids, T.begin, T.end, p->pad_prefix,
-                                                       T.center, T.x, T.y, T.z, p->q_tree,
+                                                       p->chunk_frame, T.x, T.y, T.z, p->q_tree,
                                                        (float4*)p->pool);
     BL_LAUNCHED(cnt.launches);
     k_pool_proxies<float4><<<T.nclusters, 256, 0, s>>>(p->n, p->np_pad, p->pool_particles, T.nodes,
-                                                       T.center, p->qhat, (float4*)p->pool);
+                                                       p->chunk_frame, p->qhat, (float4*)p->pool);
   } else {
     k_pool_particles<double4><<<T.nleaves, 256, 0, s>>>(T.leaf_ids, T.begin, T.end, p->pad_prefix,
-                                                        T.center, T.x, T.y, T.z, p->q_tree,
+                                                        p->chunk_frame, T.x, T.y, T.z, p->q_tree,
                                                         (double4*)p->pool);
     BL_LAUNCHED(cnt.launches);
     k_pool_proxies<double4><<<T.nclusters, 256, 0, s>>>(p->n, p->np_pad, p->pool_particles, T.nodes,
-                                                        T.center, p->qhat, (double4*)p->pool);
+                                                        p->chunk_frame, p->qhat, (double4*)p->pool);
   }
+  BL_LAUNCHED(cnt.launches);
+  return BLDTT_OK;
+}
+
+// Frame of every pool chunk: a float centre (the rounded centre of the chunk's
+// bounding box for particles; the rounded cluster centre for proxies) and the
+// number of real entries (bit-cast into .w).
+__device__ __forceinline__ void store_frame(float4* frame, int64_t q, const double* c, int count) {
+  frame[q] = make_float4((float)c[0], (float)c[1], (float)c[2], __int_as_float(count));
+}
+
+__global__ void k_frames_particles(int32_t nleaves, const int32_t* __restrict__ leaf_ids,
+                                   const int32_t* __restrict__ begin, const int32_t* __restrict__ end,
+                                   const int32_t* __restrict__ pad_prefix, const double* __restrict__ x,
+                                   const double* __restrict__ y, const double* __restrict__ z,
+                                   float4* __restrict__ frame) {
+  // one warp per chunk
+  const int64_t q = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const int64_t first = q * kChunk;
+  if (first >= pad_prefix[nleaves]) return;
+  int lo = 0, hi = nleaves;   // leaf holding pool entry `first`
+  while (hi - lo > 1) {
+    int m = (lo + hi) >> 1;
+    if (pad_prefix[m] <= first) lo = m; else hi = m;
+  }
+  const int c = leaf_ids[lo];
+  const int64_t b = begin[c] + (first - pad_prefix[lo]);
+  const int64_t e = min((int64_t)end[c], b + kChunk);
+  double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t i = b + lane; i < e; i += 32) {
+    double v[3] = {x[i], y[i], z[i]};
+    for (int d = 0; d < 3; ++d) {
+      mn[d] = fmin(mn[d], v[d]);
+      mx[d] = fmax(mx[d], v[d]);
+    }
+  }
+  for (int d = 0; d < 3; ++d)
+    for (int off = 16; off; off >>= 1) {
+      mn[d] = fmin(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], off));
+      mx[d] = fmax(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], off));
+    }
+  if (lane == 0) {
+    double c3[3];
+    for (int d = 0; d < 3; ++d) c3[d] = b < e ? 0.5 * (mn[d] + mx[d]) : 0.0;
+    store_frame(frame, q, c3, (int)(e > b ? e - b : 0));
+  }
+}
+
+__global__ void k_frames_proxies(int32_t nclusters, int64_t first_chunk, int32_t chunks_per_cluster,
+                                 int32_t np, const double* __restrict__ center,
+                                 float4* __restrict__ frame) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nclusters * chunks_per_cluster) return;
+  const int64_t c = t / chunks_per_cluster;
+  const int k = (int)(t % chunks_per_cluster);
+  store_frame(frame, first_chunk + t, center + c * 3, min(kChunk, np - k * kChunk));
+}
+
+int build_chunk_frames(bldtt_plan* p, cudaStream_t s) {
+  Counters& cnt = p->setup_counter;
+  const Tree& T = p->st;
+  const int64_t nchunks = p->pool_len / kChunk;
+  BL_TRY(dalloc_n(&p->chunk_frame, (size_t)nchunks, s));
+  const int64_t pchunks = p->pool_particles / kChunk;
+  if (pchunks > 0) {
+    k_frames_particles<<<nblk(pchunks, 4), 128, 0, s>>>(T.nleaves, T.leaf_ids, T.begin, T.end,
+                                                        p->pad_prefix, T.x, T.y, T.z, p->chunk_frame);
+    BL_LAUNCHED(cnt.launches);
+  }
+  const int32_t cpc = p->np_pad / kChunk;
+  k_frames_proxies<<<nblk((int64_t)T.nclusters * cpc, 256), 256, 0, s>>>(T.nclusters, pchunks, cpc,
+                                                                          p->np, T.center,
+                                                                          p->chunk_frame);
   BL_LAUNCHED(cnt.launches);
   return BLDTT_OK;
 }
@@ -348,9 +437,11 @@ __global__ void __launch_bounds__(kDownThreads) k_down_leaf(
   extern __shared__ double smem[];
   const int P = n + 1, np = P * P * P;
   const int stride = 3 * P + ((3 * P) % 2 == 0 ? 1 : 0);   // odd: conflict-free rows
+  const int tstride = P | 1;
   double* snodes = smem;                                    // [3][P]
   double* sL = snodes + 3 * P;                              // [threads][stride]
   T* sphi = reinterpret_cast<T*>(sL + (size_t)kDownThreads * stride);   // [np]
+  T* sLz = sphi + np;                                       // [threads][tstride] z factors in T
   const int c = leaf_ids[blockIdx.x];
   for (int t = threadIdx.x; t < 3 * P; t += blockDim.x) snodes[t] = nodes[(int64_t)c * 3 * P + t];
   for (int o = threadIdx.x; o < np; o += blockDim.x) sphi[o] = (T)phit[(int64_t)c * np + o];
@@ -360,13 +451,15 @@ __global__ void __launch_bounds__(kDownThreads) k_down_leaf(
     basis_1d<double>(x[i], snodes, n, L, 1);
     basis_1d<double>(y[i], snodes + P, n, L + P, 1);
     basis_1d<double>(z[i], snodes + 2 * P, n, L + 2 * P, 1);
+    T* Lz = sLz + (size_t)threadIdx.x * tstride;
+    for (int k3 = 0; k3 < P; ++k3) Lz[k3] = (T)L[2 * P + k3];
     double acc = 0.0;
     for (int k1 = 0; k1 < P; ++k1) {
       double s1 = 0.0;
       for (int k2 = 0; k2 < P; ++k2) {
         const T* row = sphi + (k1 * P + k2) * P;
         T s2 = (T)0;
-        for (int k3 = 0; k3 < P; ++k3) s2 += (T)L[2 * P + k3] * row[k3];
+        for (int k3 = 0; k3 < P; ++k3) s2 += Lz[k3] * row[k3];
         s1 += L[P + k2] * (double)s2;
       }
       acc += L[k1] * s1;
@@ -386,13 +479,14 @@ int downward_pass(bldtt_plan* p, double* phi_user, cudaStream_t s) {
   }
   const int P = p->P, np = p->np;
   const int stride = 3 * P + ((3 * P) % 2 == 0 ? 1 : 0);
+  const size_t tz = (size_t)kDownThreads * (P | 1);
   if (p->precision == BLDTT_FP32_BULK) {
-    size_t bytes = sizeof(double) * (3 * P + (size_t)kDownThreads * stride) + sizeof(float) * np;
+    size_t bytes = sizeof(double) * (3 * P + (size_t)kDownThreads * stride) + sizeof(float) * (np + tz);
     k_down_leaf<true><<<T.nleaves, kDownThreads, bytes, s>>>(T.leaf_ids, T.begin, T.end, T.x, T.y,
                                                               T.z, T.perm, T.nodes, p->n, p->phit,
                                                               p->phi_near, phi_user);
   } else {
-    size_t bytes = sizeof(double) * (3 * P + (size_t)kDownThreads * stride + np);
+    size_t bytes = sizeof(double) * (3 * P + (size_t)kDownThreads * stride + np + tz);
     k_down_leaf<false><<<T.nleaves, kDownThreads, bytes, s>>>(T.leaf_ids, T.begin, T.end, T.x, T.y,
                                                                T.z, T.perm, T.nodes, p->n, p->phit,
                                                                p->phi_near, phi_user);

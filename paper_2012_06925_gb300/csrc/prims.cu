@@ -317,10 +317,26 @@ __global__ void k_bbox_partial(const double* __restrict__ x, const double* __res
 }
 
 __global__ void k_bbox_final(const double* __restrict__ part, int nparts, double* __restrict__ out) {
+  double v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x)
+    for (int k = 0; k < 6; ++k) {
+      double p = part[b * 6 + k];
+      v[k] = k < 3 ? fmin(v[k], p) : fmax(v[k], p);
+    }
+  __shared__ double sm[kRedThreads / 32][6];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = 0; k < 6; ++k)
+    for (int off = 16; off; off >>= 1) {
+      double o = __shfl_down_sync(0xffffffffu, v[k], off);
+      v[k] = k < 3 ? fmin(v[k], o) : fmax(v[k], o);
+    }
+  if (lane == 0)
+    for (int k = 0; k < 6; ++k) sm[warp][k] = v[k];
+  __syncthreads();
   if (threadIdx.x < 6) {
-    double r = part[threadIdx.x];
-    for (int b = 1; b < nparts; ++b)
-      r = threadIdx.x < 3 ? fmin(r, part[b * 6 + threadIdx.x]) : fmax(r, part[b * 6 + threadIdx.x]);
+    double r = sm[0][threadIdx.x];
+    for (int w = 1; w < kRedThreads / 32; ++w)
+      r = threadIdx.x < 3 ? fmin(r, sm[w][threadIdx.x]) : fmax(r, sm[w][threadIdx.x]);
     out[threadIdx.x] = r;
   }
 }
@@ -334,7 +350,7 @@ int bbox_reduce(const double* x, const double* y, const double* z, int64_t n, do
   BL_TRY(dalloc_n(&part, (size_t)blocks * 6, s));
   k_bbox_partial<<<blocks, kRedThreads, 0, s>>>(x, y, z, n, part, bad_dev);
   BL_LAUNCHED(c.launches);
-  k_bbox_final<<<1, 32, 0, s>>>(part, blocks, out_dev);
+  k_bbox_final<<<1, kRedThreads, 0, s>>>(part, blocks, out_dev);
   BL_LAUNCHED(c.launches);
   dfree(part, s);
   return BLDTT_OK;

@@ -9,6 +9,8 @@
 // box of its particles.  All geometric decisions are made in FP64 with
 // explicitly rounded operations (no FMA contraction) so that they are the
 // decisions a plain FP64 evaluation of the same expressions makes.
+#include <utility>
+
 #include "internal.cuh"
 
 namespace bldtt {
@@ -136,37 +138,79 @@ __global__ void k_tree_count(int32_t ls, const int32_t* __restrict__ chunk_clust
   if (threadIdx.x < 8) counts[(int64_t)q * 8 + threadIdx.x] = cnt[threadIdx.x];
 }
 
-__global__ void k_tree_combine(int32_t nl, int32_t ls, const uint8_t* __restrict__ splitmask,
-                               const int32_t* __restrict__ chunk_off,
-                               const int32_t* __restrict__ nchunks,
-                               const int32_t* __restrict__ counts, int32_t* __restrict__ chunk_base,
-                               int32_t* __restrict__ child_cnt, int32_t* __restrict__ nch,
-                               const int32_t* __restrict__ begin) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= nl) return;
+// One CTA per splitting cluster: totals per child code, then stable
+// destinations of every chunk's particles (exclusive scan over the chunks).
+constexpr int kCombineThreads = 256;
+
+__device__ __forceinline__ void block_scan8(const int32_t (&v)[8], int32_t (&ex)[8],
+                                            int32_t (&tot)[8], int32_t (*warp_sums)[8]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t inc[8];
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    int32_t x = v[b];
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      int32_t y = __shfl_up_sync(0xffffffffu, x, off);
+      if (lane >= off) x += y;
+    }
+    inc[b] = x;
+  }
+  if (lane == 31)
+    for (int b = 0; b < 8; ++b) warp_sums[warp][b] = inc[b];
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    int32_t pre = 0, all = 0;
+    for (int w = 0; w < kCombineThreads / 32; ++w) {
+      int32_t ws = warp_sums[w][b];
+      if (w < warp) pre += ws;
+      all += ws;
+    }
+    ex[b] = pre + inc[b] - v[b];
+    tot[b] = all;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kCombineThreads) k_tree_combine(
+    int32_t ls, const uint8_t* __restrict__ splitmask, const int32_t* __restrict__ chunk_off,
+    const int32_t* __restrict__ nchunks, const int32_t* __restrict__ counts,
+    int32_t* __restrict__ chunk_base, int32_t* __restrict__ child_cnt, int32_t* __restrict__ nch,
+    const int32_t* __restrict__ begin) {
+  __shared__ int32_t warp_sums[kCombineThreads / 32][8];
+  const int j = blockIdx.x;
   if (!splitmask[j]) {
-    nch[j] = 0;
+    if (threadIdx.x == 0) nch[j] = 0;
     return;
   }
-  int32_t run[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  int32_t q0 = chunk_off[j], q1 = q0 + nchunks[j];
-  for (int32_t q = q0; q < q1; ++q)
-    for (int b = 0; b < 8; ++b) {
-      chunk_base[(int64_t)q * 8 + b] = run[b];
-      run[b] += counts[(int64_t)q * 8 + b];
-    }
-  int32_t cb[8];
+  const int32_t q0 = chunk_off[j], nq = nchunks[j];
+  int32_t v[8], ex[8], tot[8], cb[8], run[8];
+  // totals per code
+  for (int b = 0; b < 8; ++b) v[b] = 0;
+  for (int32_t t = threadIdx.x; t < nq; t += kCombineThreads)
+    for (int b = 0; b < 8; ++b) v[b] += counts[(int64_t)(q0 + t) * 8 + b];
+  block_scan8(v, ex, tot, warp_sums);
   int32_t pos = begin[ls + j];
   int k = 0;
   for (int b = 0; b < 8; ++b) {
     cb[b] = pos;
-    pos += run[b];
-    child_cnt[(int64_t)j * 8 + b] = run[b];
-    k += run[b] > 0;
+    pos += tot[b];
+    run[b] = 0;
+    k += tot[b] > 0;
   }
-  for (int32_t q = q0; q < q1; ++q)
-    for (int b = 0; b < 8; ++b) chunk_base[(int64_t)q * 8 + b] += cb[b];
-  nch[j] = k;
+  if (threadIdx.x < 8) child_cnt[(int64_t)j * 8 + threadIdx.x] = tot[threadIdx.x];
+  if (threadIdx.x == 0) nch[j] = k;
+  // stable destinations: chunk-order exclusive scan per code
+  for (int32_t base = 0; base < nq; base += kCombineThreads) {
+    const int32_t t = base + threadIdx.x;
+    for (int b = 0; b < 8; ++b) v[b] = t < nq ? counts[(int64_t)(q0 + t) * 8 + b] : 0;
+    int32_t tile[8];
+    block_scan8(v, ex, tile, warp_sums);
+    if (t < nq)
+      for (int b = 0; b < 8; ++b) chunk_base[(int64_t)(q0 + t) * 8 + b] = cb[b] + run[b] + ex[b];
+    for (int b = 0; b < 8; ++b) run[b] += tile[b];
+  }
 }
 
 __global__ void k_tree_children(int32_t nl, int32_t ls, int32_t le, int32_t lvl,
@@ -244,14 +288,22 @@ __global__ void k_tree_scatter(int32_t ls, const int32_t* __restrict__ chunk_clu
   }
 }
 
-// Shrink every new cluster to the bounding box of its particles (Sec. 2.3).
+// Shrink every new cluster to the bounding box of its particles (Sec. 2.3):
+// each cluster is cut into kBoxSlices slices reduced by separate CTAs, then
+// one warp per cluster combines the slices.  Min/max are exact, so the result
+// does not depend on the split.
+constexpr int kBoxSlices = 32;
+
 __global__ void k_tree_child_bbox(int32_t first, const int32_t* __restrict__ begin,
                                   const int32_t* __restrict__ end, const double* __restrict__ x,
                                   const double* __restrict__ y, const double* __restrict__ z,
-                                  double* __restrict__ box) {
-  int c = first + blockIdx.x;
+                                  double* __restrict__ part) {
+  const int c = first + blockIdx.x;
+  const int32_t b = begin[c], cnt = end[c] - b;
+  const int32_t len = (cnt + kBoxSlices - 1) / kBoxSlices;
+  const int32_t s0 = b + blockIdx.y * len, s1 = min(s0 + len, b + cnt);
   double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  for (int32_t i = begin[c] + threadIdx.x; i < end[c]; i += blockDim.x) {
+  for (int32_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
     double v[3] = {x[i], y[i], z[i]};
     for (int d = 0; d < 3; ++d) {
       lo[d] = fmin(lo[d], v[d]);
@@ -275,7 +327,22 @@ __global__ void k_tree_child_bbox(int32_t first, const int32_t* __restrict__ beg
     double r = sm[0][threadIdx.x];
     for (int w = 1; w < kTreeThreads / 32; ++w)
       r = threadIdx.x < 3 ? fmin(r, sm[w][threadIdx.x]) : fmax(r, sm[w][threadIdx.x]);
-    box[(int64_t)c * 6 + threadIdx.x] = r;
+    part[((int64_t)blockIdx.x * kBoxSlices + blockIdx.y) * 6 + threadIdx.x] = r;
+  }
+}
+
+__global__ void k_tree_child_bbox_combine(int32_t first, int32_t nc, const double* __restrict__ part,
+                                          double* __restrict__ box) {
+  const int j = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (j >= nc) return;
+  for (int k = 0; k < 6; ++k) {
+    double r = part[((int64_t)j * kBoxSlices + lane) * 6 + k];
+    for (int off = 16; off; off >>= 1) {
+      double o = __shfl_down_sync(0xffffffffu, r, off);
+      r = k < 3 ? fmin(r, o) : fmax(r, o);
+    }
+    if (lane == 0) box[(int64_t)(first + j) * 6 + k] = r;
   }
 }
 
@@ -392,8 +459,8 @@ int build_tree(Tree& T, const double* coords, int32_t n, int32_t max_leaf, int d
     k_tree_count<<<tc, kTreeThreads, 0, s>>>(ls, chunk_cluster, chunk_start, T.end, T.x, T.y, T.z,
                                              splitmask, mid, code, counts);
     BL_LAUNCHED(cnt.launches);
-    k_tree_combine<<<nblk(nl, 128), 128, 0, s>>>(nl, ls, splitmask, chunk_off, nchunks, counts,
-                                                 chunk_base, child_cnt, nch, T.begin);
+    k_tree_combine<<<nl, kCombineThreads, 0, s>>>(ls, splitmask, chunk_off, nchunks, counts,
+                                                  chunk_base, child_cnt, nch, T.begin);
     BL_LAUNCHED(cnt.launches);
     int32_t nc = 0;
     BL_TRY(scan_exclusive(nch, child_off, nl, &nc, s, cnt));
@@ -413,8 +480,14 @@ int build_tree(Tree& T, const double* coords, int32_t n, int32_t max_leaf, int d
     { double* t = T.y; T.y = y2; y2 = t; }
     { double* t = T.z; T.z = z2; z2 = t; }
     { int32_t* t = T.perm; T.perm = perm2; perm2 = t; }
-    k_tree_child_bbox<<<nc, kTreeThreads, 0, s>>>(le, T.begin, T.end, T.x, T.y, T.z, T.box);
+    double* part = nullptr;
+    BL_TRY(dalloc_n(&part, (size_t)nc * kBoxSlices * 6, s));
+    k_tree_child_bbox<<<dim3(nc, kBoxSlices), kTreeThreads, 0, s>>>(le, T.begin, T.end, T.x, T.y,
+                                                                    T.z, part);
     BL_LAUNCHED(cnt.launches);
+    k_tree_child_bbox_combine<<<nblk(nc, 4), 128, 0, s>>>(le, nc, part, T.box);
+    BL_LAUNCHED(cnt.launches);
+    dfree(part, s);
     T.level_start.push_back(le + nc);
     dfree(splitmask, s); dfree(mid, s); dfree(nchunks, s); dfree(chunk_off, s);
     dfree(chunk_cluster, s); dfree(chunk_start, s); dfree(counts, s); dfree(chunk_base, s);
@@ -448,6 +521,114 @@ int build_tree(Tree& T, const double* coords, int32_t n, int32_t max_leaf, int d
   BL_LAUNCHED(cnt.launches);
   dfree(flag, s);
   dfree(excl, s);
+  return BLDTT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Morton order inside leaves
+// ---------------------------------------------------------------------------
+// The order of particles inside a leaf is not part of the method; putting
+// them along a Morton curve of the leaf box makes every run of 64 consecutive
+// sources spatially compact, which the FP32 interaction path exploits (its
+// coordinate frames are per run of 64).  Leaves above kMortonMax particles
+// keep their order.
+constexpr int kMortonMax = 4096;
+constexpr int kMortonThreads = 512;
+
+__device__ __forceinline__ uint32_t spread10(uint32_t v) {
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000ffu;
+  v = (v | (v << 8)) & 0x0300f00fu;
+  v = (v | (v << 4)) & 0x030c30c3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+__device__ __forceinline__ uint32_t quantize10(double v, double lo, double hi) {
+  double e = hi - lo;
+  if (!(e > 0.0)) return 0u;
+  double t = (v - lo) / e * 1024.0;
+  int q = (int)t;
+  return (uint32_t)(q < 0 ? 0 : (q > 1023 ? 1023 : q));
+}
+
+__global__ void __launch_bounds__(kMortonThreads) k_leaf_morton(
+    const int32_t* __restrict__ leaf_ids, const int32_t* __restrict__ begin,
+    const int32_t* __restrict__ end, const double* __restrict__ box, const double* __restrict__ x,
+    const double* __restrict__ y, const double* __restrict__ z, const int32_t* __restrict__ perm,
+    double* __restrict__ x2, double* __restrict__ y2, double* __restrict__ z2,
+    int32_t* __restrict__ perm2) {
+  __shared__ unsigned long long key[kMortonMax];
+  const int c = leaf_ids[blockIdx.x];
+  const int32_t b = begin[c];
+  const int m = end[c] - b;
+  if (m > kMortonMax || m < 2) {   // keep the order
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      x2[b + i] = x[b + i];
+      y2[b + i] = y[b + i];
+      z2[b + i] = z[b + i];
+      perm2[b + i] = perm[b + i];
+    }
+    return;
+  }
+  int n2 = 1;
+  while (n2 < m) n2 <<= 1;
+  const double* bx = box + (int64_t)c * 6;
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+    if (i < m) {
+      uint32_t code = (spread10(quantize10(x[b + i], bx[0], bx[3])) << 2) |
+                      (spread10(quantize10(y[b + i], bx[1], bx[4])) << 1) |
+                      spread10(quantize10(z[b + i], bx[2], bx[5]));
+      key[i] = ((unsigned long long)code << 32) | (unsigned)i;   // unique: ties by position
+    } else {
+      key[i] = ~0ull;
+    }
+  }
+  __syncthreads();
+  for (int k = 2; k <= n2; k <<= 1) {        // bitonic sort, ascending
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        int ixj = i ^ j;
+        if (ixj > i) {
+          unsigned long long a = key[i], bb = key[ixj];
+          bool up = (i & k) == 0;
+          if ((a > bb) == up) {
+            key[i] = bb;
+            key[ixj] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    int src = b + (int)(key[i] & 0xffffffffu);
+    x2[b + i] = x[src];
+    y2[b + i] = y[src];
+    z2[b + i] = z[src];
+    perm2[b + i] = perm[src];
+  }
+}
+
+int morton_order_leaves(Tree& T, cudaStream_t s, Counters& cnt) {
+  if (T.nleaves == 0) return BLDTT_OK;
+  double *x2 = nullptr, *y2 = nullptr, *z2 = nullptr;
+  int32_t* perm2 = nullptr;
+  BL_TRY(dalloc_n(&x2, T.n, s));
+  BL_TRY(dalloc_n(&y2, T.n, s));
+  BL_TRY(dalloc_n(&z2, T.n, s));
+  BL_TRY(dalloc_n(&perm2, T.n, s));
+  k_leaf_morton<<<T.nleaves, kMortonThreads, 0, s>>>(T.leaf_ids, T.begin, T.end, T.box, T.x, T.y,
+                                                     T.z, T.perm, x2, y2, z2, perm2);
+  BL_LAUNCHED(cnt.launches);
+  std::swap(T.x, x2);
+  std::swap(T.y, y2);
+  std::swap(T.z, z2);
+  std::swap(T.perm, perm2);
+  dfree(x2, s);
+  dfree(y2, s);
+  dfree(z2, s);
+  dfree(perm2, s);
   return BLDTT_OK;
 }
 

@@ -65,3 +65,14 @@ def rel_l2(ref, got):
 
 def max_rel(ref, got):
     return O.max_norm_error(ref, got)
+
+
+def same_leaf_members(gtree: dict, otree: O.Tree) -> bool:
+    """The GPU orders particles inside each source leaf along a Morton curve;
+    the leaf memberships (sets) must still equal the oracle's."""
+    gperm, operm = gtree["perm"], otree.perm
+    for c in otree.leaves():
+        b, e = otree.begin[c], otree.end[c]
+        if sorted(gperm[b:e].tolist()) != sorted(operm[b:e].tolist()):
+            return False
+    return True
