@@ -82,8 +82,10 @@ typedef struct bldtt_stats {
     double interactions[4];             /* kernel evaluations per type, as defined by
                                            Eqs. (6), (8), (12), (15): |C_t||C_s|,
                                            |C_t| n_p, n_p |C_s|, n_p^2 per entry */
-    double executed_evaluations;        /* evaluations the interaction kernel performs,
-                                           padding of tiles and chunks included */
+    double executed_evaluations;        /* evaluations the interaction kernel performs:
+                                           every target slot of a 256-target tile meets
+                                           every real source (idle slots of partial tiles
+                                           included) */
     int64_t work_items;                 /* target tiles drained by the interaction kernel */
     int32_t interact_grid;              /* CTAs of the persistent interaction kernel */
     int32_t interact_threads;           /* threads per CTA of that kernel */

@@ -122,7 +122,10 @@ int setup_impl(bldtt_plan* p, const double* targets, const double* sources, cons
   BL_TRY(dalloc_n(&p->item_counter, 1, s));
   BL_TRY(build_chunk_frames(p, s));
   p->interact_layout = 0;
-  if (const char* lay = std::getenv("BLDTT_INTERACT_LAYOUT")) p->interact_layout = std::atoi(lay) ? 1 : 0;
+  if (const char* lay = std::getenv("BLDTT_INTERACT_LAYOUT")) {
+    int l = std::atoi(lay);
+    p->interact_layout = (l >= 0 && l < 3) ? l : 0;
+  }
   BL_TRY(interaction_grid(p, &p->interact_grid));
   BL_CUDA(cudaEventRecord(p->ev[2], s));
   BL_CUDA(cudaStreamSynchronize(s));

@@ -246,6 +246,18 @@ struct ListView {
   int32_t np_pad;
 };
 
+// Real sources (no padding) a target cluster's own lists of two types contribute.
+__device__ __forceinline__ int64_t list_sources(const ListView& L, const int32_t* s_begin,
+                                                const int32_t* s_end, int32_t np, int type_particles,
+                                                int type_proxies, int32_t c) {
+  int64_t n = 0;
+  int64_t k0 = (int64_t)type_particles * L.nct + c;
+  for (int32_t e = L.ptr[k0]; e < L.ptr[k0 + 1]; ++e) n += s_end[L.src[e]] - s_begin[L.src[e]];
+  int64_t k1 = (int64_t)type_proxies * L.nct + c;
+  n += (int64_t)(L.ptr[k1 + 1] - L.ptr[k1]) * np;
+  return n;
+}
+
 // Chunks a target cluster's own lists of two types contribute.
 __device__ __forceinline__ int64_t list_chunks(const ListView& L, int type_particles, int type_proxies,
                                                int32_t c) {
@@ -262,32 +274,39 @@ __device__ __forceinline__ int64_t list_chunks(const ListView& L, int type_parti
 
 __global__ void k_item_count(int32_t nct, ListView L, const int32_t* __restrict__ parent,
                              const int32_t* __restrict__ nchild, const int32_t* __restrict__ begin,
-                             const int32_t* __restrict__ end, int32_t np,
+                             const int32_t* __restrict__ end, const int32_t* __restrict__ s_begin,
+                             const int32_t* __restrict__ s_end, int32_t np,
                              int32_t* __restrict__ nitems, int64_t* __restrict__ cost_part,
-                             int64_t* __restrict__ cost_prox) {
+                             int64_t* __restrict__ cost_prox, unsigned long long* __restrict__ executed) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nct) return;
-  int64_t cp = 0;
+  int64_t cp = 0, sp = 0;
   if (nchild[c] == 0)   // PP + PC of the leaf and of all its ancestors (Sec. 2.7 chain)
-    for (int32_t a = c; a >= 0; a = parent[a]) cp += list_chunks(L, 0, 1, a);
+    for (int32_t a = c; a >= 0; a = parent[a]) {
+      cp += list_chunks(L, 0, 1, a);
+      sp += list_sources(L, s_begin, s_end, np, 0, 1, a);
+    }
   int64_t cq = list_chunks(L, 2, 3, c);   // CP + CC of the cluster itself
+  int64_t sq = list_sources(L, s_begin, s_end, np, 2, 3, c);
   int32_t tp = cp > 0 ? (end[c] - begin[c] + kTile - 1) / kTile : 0;
   int32_t tq = cq > 0 ? (np + kTile - 1) / kTile : 0;
   nitems[c] = tp + tq;
   cost_part[c] = cp;
   cost_prox[c] = cq;
+  // evaluations the kernel performs: every target slot of every tile meets every real source
+  unsigned long long ex = (unsigned long long)tp * kTile * sp + (unsigned long long)tq * kTile * sq;
+  if (ex) atomicAdd(executed, ex);
 }
 
 __global__ void k_item_fill(int32_t nct, const int32_t* __restrict__ off,
                             const int64_t* __restrict__ cost_part, const int64_t* __restrict__ cost_prox,
                             const int32_t* __restrict__ begin, const int32_t* __restrict__ end,
                             int32_t np, int4* __restrict__ items, uint32_t* __restrict__ keys,
-                            int32_t* __restrict__ vals, unsigned long long* __restrict__ executed) {
+                            int32_t* __restrict__ vals) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nct) return;
   int32_t o = off[c];
   const uint32_t kKeyMax = (1u << 24) - 1u;
-  unsigned long long ex = 0;
   if (cost_part[c] > 0) {
     uint32_t k = kKeyMax - (uint32_t)min((int64_t)kKeyMax, cost_part[c]);
     for (int32_t r = begin[c]; r < end[c]; r += kTile) {
@@ -295,7 +314,6 @@ __global__ void k_item_fill(int32_t nct, const int32_t* __restrict__ off,
       keys[o] = k;
       vals[o] = o;
       ++o;
-      ex += (unsigned long long)cost_part[c];
     }
   }
   if (cost_prox[c] > 0) {
@@ -305,10 +323,8 @@ __global__ void k_item_fill(int32_t nct, const int32_t* __restrict__ off,
       keys[o] = k;
       vals[o] = o;
       ++o;
-      ex += (unsigned long long)cost_prox[c];
     }
   }
-  if (ex) atomicAdd(executed, ex * (unsigned long long)kChunk * (unsigned long long)kTile);
 }
 
 __global__ void k_gather_items(const int4* __restrict__ src, const int32_t* __restrict__ idx,
@@ -350,8 +366,12 @@ int build_work_items(bldtt_plan* p, cudaStream_t s) {
   BL_TRY(dalloc_n(&off, nct, s));
   BL_TRY(dalloc_n(&cost_part, nct, s));
   BL_TRY(dalloc_n(&cost_prox, nct, s));
-  k_item_count<<<nblk(nct, 128), 128, 0, s>>>(nct, L, tt.parent, tt.nchild, tt.begin, tt.end, p->np,
-                                              nitems, cost_part, cost_prox);
+  unsigned long long* executed = nullptr;
+  BL_TRY(dalloc_n(&executed, 1, s));
+  BL_CUDA(cudaMemsetAsync(executed, 0, sizeof(unsigned long long), s));
+  k_item_count<<<nblk(nct, 128), 128, 0, s>>>(nct, L, tt.parent, tt.nchild, tt.begin, tt.end,
+                                              st.begin, st.end, p->np, nitems, cost_part, cost_prox,
+                                              executed);
   BL_LAUNCHED(cnt.launches);
   int32_t ni = 0;
   BL_TRY(scan_exclusive(nitems, off, nct, &ni, s, cnt));
@@ -359,15 +379,12 @@ int build_work_items(bldtt_plan* p, cudaStream_t s) {
   int4* items = nullptr;
   uint32_t* keys = nullptr;
   int32_t* vals = nullptr;
-  unsigned long long* executed = nullptr;
   BL_TRY(dalloc_n(&items, ni, s));
   BL_TRY(dalloc_n(&keys, ni, s));
   BL_TRY(dalloc_n(&vals, ni, s));
-  BL_TRY(dalloc_n(&executed, 1, s));
   BL_TRY(dalloc_n(&p->items, ni, s));
-  BL_CUDA(cudaMemsetAsync(executed, 0, sizeof(unsigned long long), s));
   k_item_fill<<<nblk(nct, 128), 128, 0, s>>>(nct, off, cost_part, cost_prox, tt.begin, tt.end, p->np,
-                                             items, keys, vals, executed);
+                                             items, keys, vals);
   BL_LAUNCHED(cnt.launches);
   // Longest items first (stable), so the persistent kernel's tail is short.
   BL_TRY(radix_sort_pairs(keys, vals, ni, 24, s, cnt));

@@ -418,8 +418,8 @@ __device__ __forceinline__ void store_output(const InteractView& v, const int4& 
   }
 }
 
-template <bool F32, int KERN, int NCW, int K>
-__global__ void __launch_bounds__((NCW + 1) * 32) k_interact(InteractView v) {
+template <bool F32, int KERN, int NCW, int K, int MINB>
+__global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_interact(InteractView v) {
   static_assert(NCW * 32 * K == kTile, "a CTA covers exactly one work-item tile");
   constexpr int kConsumers = NCW * 32;
   using Vec = typename std::conditional<F32, float4, double4>::type;
@@ -451,6 +451,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32) k_interact(InteractView v) {
   double X[K][3];               // FP64 targets (FP64 path)
   f2_t xh2[K][3], xl2[K][3];    // FP32 split of the targets, each duplicated (FP32 path)
   double acc[K];
+  bool warp_full = true;
   for (uint32_t it = 0;; ++it) {
     const int s = (int)(it % kStages);
     if (!mbar_wait(&full[s], (it / kStages) & 1u, v.err)) return;
@@ -463,6 +464,8 @@ __global__ void __launch_bounds__((NCW + 1) * 32) k_interact(InteractView v) {
       if (mi < 0) return;
       cur = mi;
       item = v.items[mi];
+      // does any row of this warp's last target slot hold a real target?
+      warp_full = (K - 1) * kConsumers + (warp * 32) < item.z;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         acc[k] = 0.0;
@@ -492,8 +495,18 @@ __global__ void __launch_bounds__((NCW + 1) * 32) k_interact(InteractView v) {
         chunk_f32_guarded<KERN, K>(reinterpret_cast<const float*>(sbuf[s]), count, x2, a,
                                    v.neg_kappa_log2e);
       } else {
-        chunk_f32<KERN, K>(reinterpret_cast<const ulonglong2*>(sbuf[s]), (count + 1) / 2, x2, a,
-                           v.neg_kappa_log2e);
+        if (K > 1 && !warp_full) {
+          // the warp's last target row lies beyond a partial tile: evaluate the others only
+          float a1[K > 1 ? K - 1 : 1];
+          const f2_t(&x2s)[K > 1 ? K - 1 : 1][3] = *reinterpret_cast<const f2_t(*)[K > 1 ? K - 1 : 1][3]>(&x2);
+          chunk_f32<KERN, (K > 1 ? K - 1 : 1)>(reinterpret_cast<const ulonglong2*>(sbuf[s]),
+                                               (count + 1) / 2, x2s, a1, v.neg_kappa_log2e);
+#pragma unroll
+          for (int k = 0; k < K; ++k) a[k] = k < K - 1 ? a1[k < K - 1 ? k : 0] : 0.f;
+        } else {
+          chunk_f32<KERN, K>(reinterpret_cast<const ulonglong2*>(sbuf[s]), (count + 1) / 2, x2, a,
+                             v.neg_kappa_log2e);
+        }
         bool bad = false;
 #pragma unroll
         for (int k = 0; k < K; ++k) bad = bad || not_finite(a[k]);
@@ -521,16 +534,21 @@ __global__ void __launch_bounds__((NCW + 1) * 32) k_interact(InteractView v) {
   }
 }
 
-// Consumer layouts the kernel is instantiated for (NCW warps x K targets).
+// Consumer layouts the kernel is instantiated for (NCW warps x K targets, and
+// the CTAs per SM the register allocation is sized for).
 struct Layout {
-  int ncw, k;
+  int ncw, k, minb;
 };
-static const Layout kLayouts[] = {{4, 2}, {2, 4}};
+static const Layout kLayouts[] = {{4, 2, 6}, {2, 4, 6}, {4, 2, 8}};
+constexpr int kNumLayouts = 3;
 
 template <bool F32, int KERN>
 static const void* kernel_for(int layout) {
-  return layout == 0 ? reinterpret_cast<const void*>(&k_interact<F32, KERN, 4, 2>)
-                     : reinterpret_cast<const void*>(&k_interact<F32, KERN, 2, 4>);
+  switch (layout) {
+    case 1: return reinterpret_cast<const void*>(&k_interact<F32, KERN, 2, 4, 6>);
+    case 2: return reinterpret_cast<const void*>(&k_interact<F32, KERN, 4, 2, 8>);
+    default: return reinterpret_cast<const void*>(&k_interact<F32, KERN, 4, 2, 6>);
+  }
 }
 
 static const void* select_kernel(const bldtt_plan* p, int layout) {
