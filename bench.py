@@ -38,6 +38,9 @@ FLOPS_PER_EVAL = {0: 20.0, 1: 28.0}   # Coulomb, Yukawa (stated flop counts)
 
 def parse():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=["uniform_n1e6", "unequal_yukawa", "plain_fp64_n2e4", "uniform_n1e8"],
+                    help="workload to time (default: the 1E6 uniform Coulomb workload)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -47,21 +50,29 @@ def parse():
     return ap.parse_args()
 
 
-def workload():
+def workload(name=WORKLOAD):
     from paper_2012_06925_gb300 import workloads as W
-    cfg = dict(W.CONFIGS[WORKLOAD])
-    tgt, _, q = W.make_problem(cfg["kind"], cfg["M"], seed=cfg["seed"])
+    cfg = dict(W.CONFIGS[name])
+    cfg["name"] = name
+    tgt, src, q = W.make_problem(cfg["kind"], cfg["M"], cfg["N"], seed=cfg["seed"],
+                                 sources_kind=cfg.get("sources_kind"))
     kw = dict(kernel=cfg["kernel"], kappa=cfg["kappa"], n=cfg["n"], theta=cfg["theta"],
               N0=cfg["N0"], M0=cfg["M0"])
-    return cfg, tgt, q, kw
+    return cfg, tgt, src, q, kw
 
 
 def config_dict(cfg):
-    return {"workload": f"{WORKLOAD}: M=N={cfg['M']:.0e} uniform in [-1,1]^3, targets=sources, "
-                        f"charges U[-1,1], Coulomb, n={cfg['n']}, theta={cfg['theta']}, "
-                        f"N0=M0={cfg['N0']}, FP32-bulk evaluation with FP64 accumulation",
-            "M": cfg["M"], "N": cfg["M"], "n": cfg["n"], "theta": cfg["theta"],
-            "leaf": cfg["N0"], "kernel": "coulomb",
+    kern = "Coulomb" if cfg["kernel"] == 0 else f"Yukawa kappa={cfg['kappa']}"
+    if cfg["N"] is None:
+        sets = f"M=N={cfg['M']:.0e} {cfg['kind']} in [-1,1]^3, targets=sources"
+    else:
+        sets = (f"M={cfg['M']:.0e} {cfg['kind']} targets, N={cfg['N']:.0e} "
+                f"{cfg.get('sources_kind') or cfg['kind']} sources")
+    return {"workload": f"{cfg['name']}: {sets}, charges U[-1,1], {kern}, n={cfg['n']}, "
+                        f"theta={cfg['theta']}, N0=M0={cfg['N0']}, FP32-bulk evaluation with FP64 "
+                        f"accumulation",
+            "M": cfg["M"], "N": cfg["N"] or cfg["M"], "n": cfg["n"], "theta": cfg["theta"],
+            "leaf": cfg["N0"], "kernel": "coulomb" if cfg["kernel"] == 0 else "yukawa",
             "l2": "flushed between timed steps (256 MiB write)"}
 
 
@@ -115,7 +126,8 @@ def run_reference(args):
     if rank != 0:
         return 0
     from paper_2012_06925_gb300 import workloads as W
-    cfg = W.CONFIGS[WORKLOAD]
+    cfg = dict(W.CONFIGS[WORKLOAD])
+    cfg["name"] = WORKLOAD
     rates = []
     for i in range(args.warmup + args.steps):
         r = oracle_rate(leaf=i % 7, count=150)
@@ -237,9 +249,12 @@ def run_gpu(args):
     builder.build()
     B.load_library()
 
-    cfg, tgt, q, kw = workload()
+    cfg, tgt, src, q, kw = workload(args.workload)
     M = tgt.shape[1]
+    N = src.shape[1]
+    same = src is tgt
     dt = torch.from_numpy(tgt).cuda()
+    ds = dt if same else torch.from_numpy(src).cuda()
     dq = torch.from_numpy(q).cuda()
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -250,7 +265,7 @@ def run_gpu(args):
             dist.barrier()
 
     def step(precision, phi):
-        plan = B.Plan(dt, dt, dq, precision=precision, stream=stream, **kw)
+        plan = B.Plan(dt, ds, dq, precision=precision, stream=stream, **kw)
         plan.compute(phi, stream=stream)
         return plan
 
@@ -324,6 +339,7 @@ def run_gpu(args):
 
     # End to end through the public API from pinned host buffers.
     ht = torch.from_numpy(tgt).pin_memory()
+    hs = ht if same else torch.from_numpy(src).pin_memory()
     hq = torch.from_numpy(q).pin_memory()
     host_phi = torch.empty(M, dtype=torch.float64).pin_memory()
     e2e_times = []
@@ -335,7 +351,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         rc = lib.bldtt_solve_host(ctypes.cast(ht.data_ptr(), ctypes.POINTER(ctypes.c_double)), M,
-                                  ctypes.cast(ht.data_ptr(), ctypes.POINTER(ctypes.c_double)), M,
+                                  ctypes.cast(hs.data_ptr(), ctypes.POINTER(ctypes.c_double)), N,
                                   ctypes.cast(hq.data_ptr(), ctypes.POINTER(ctypes.c_double)),
                                   kw["kernel"], kw["kappa"], kw["n"], kw["theta"], kw["N0"],
                                   kw["M0"], B.FP32_BULK,
@@ -346,11 +362,11 @@ def run_gpu(args):
         if i > 0:
             e2e_times.append(t1 - t0)
     e2e = {"value": M / statistics.median(e2e_times), "unit": UNIT,
-           "h2d_bytes_per_step": int(ht.numel() * 8 + hq.numel() * 8),
+           "h2d_bytes_per_step": int(ht.numel() * 8 + (0 if same else hs.numel() * 8) + hq.numel() * 8),
            "d2h_bytes_per_step": int(M * 8), "seconds": statistics.median(e2e_times)}
 
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD:
         try:
             cb = oracle_rate(leaf=0, count=2000)
             cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
@@ -372,7 +388,7 @@ def run_gpu(args):
                          "executed_with_padding": st["executed_evaluations"]},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": interact_traffic(),
-                     "kernel": "k_interact<FP32,Coulomb>",
+                     "kernel": f"k_interact<FP32,{'Coulomb' if kw['kernel'] == 0 else 'Yukawa'}>",
                      "flops_per_launch": flops, "ms_per_launch": ms_interact,
                      "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
                                    f"{sm_max:.0f} MHz",
