@@ -53,6 +53,9 @@ enum bldtt_status {
 enum bldtt_kernel {
     BLDTT_COULOMB = 0,    /* G = 1/r */
     BLDTT_YUKAWA = 1,     /* G = exp(-kappa r)/r, kappa >= 0 */
+    BLDTT_OSCILLATORY = 2,   /* G = sin(kappa r)/r, kappa >= 0 (Sec. 4.6 uses kappa = pi) */
+    BLDTT_REG_COULOMB = 3,   /* G = 1/sqrt(r^2 + kappa^2), kappa >= 0 (Sec. 4.6: 0.005);
+                                a pair at r = 0 still contributes nothing */
     BLDTT_TEST_POLY = 99  /* test kernel of degree 2 in each coordinate, d = x - y:
                              G = 1 + d1 - 2 d2 + 3 d3 + d1 d2 - d2 d3 + d1^2 d3^2 - d2^2/2.
                              Interpolation of degree n >= 2 reproduces it exactly. */
@@ -67,6 +70,11 @@ enum bldtt_precision {
                              coincident-point guard, proxy points, proxy charges,
                              proxy potentials and the final phi stay FP64 */
 };
+
+/* Traversal variants.  BLDTT_VARIANT_CC_PP_ONLY is the ablation of Sec. 4.3:
+ * a well-separated pair interacts by CC when both clusters hold more than n_p
+ * particles and by PP otherwise (no PC or CP). */
+enum bldtt_variant { BLDTT_VARIANT_FULL = 0, BLDTT_VARIANT_CC_PP_ONLY = 1 };
 
 /* Interaction types (Sec. 2.4), used to index the list arrays below. */
 enum bldtt_interaction { BLDTT_PP = 0, BLDTT_PC = 1, BLDTT_CP = 2, BLDTT_CC = 3 };
@@ -123,6 +131,29 @@ int bldtt_setup(bldtt_plan** plan,
                 const double* charges,
                 int kernel, double kappa, int n, double theta, int N0, int M0,
                 int precision, void* cuda_stream);
+
+/* Parameters of bldtt_setup_ex: the method parameters of bldtt_setup plus
+ * the traversal variant (enum bldtt_variant). */
+typedef struct bldtt_params {
+    int kernel;
+    double kappa;
+    int n;
+    double theta;
+    int N0, M0;
+    int precision;
+    int variant;
+} bldtt_params_t;
+
+/*
+ * bldtt_setup_ex - bldtt_setup with the parameters in a struct, adding the
+ * traversal variant.  Same arguments, ownership and errors as bldtt_setup;
+ * EINVAL also for an unknown variant or a NULL params pointer.
+ */
+int bldtt_setup_ex(bldtt_plan** plan,
+                   const double* targets, int64_t M,
+                   const double* sources, int64_t N,
+                   const double* charges,
+                   const bldtt_params_t* params, void* cuda_stream);
 
 /*
  * bldtt_set_charges - replace the source charges of a plan (device, N

@@ -5,5 +5,5 @@ CPU-baseline leg of bench.py, never by the library.  See bldtt_oracle.py for
 the passages of the paper each function follows and the readings taken.
 """
 from .bldtt_oracle import *  # noqa: F401,F403
-from .bldtt_oracle import (COULOMB, YUKAWA, TEST_POLY, PP, PC, CP, CC, Result,  # noqa: F401
-                           SampledBLDTT, Tree)
+from .bldtt_oracle import (COULOMB, YUKAWA, OSCILLATORY, REG_COULOMB, TEST_POLY, PP, PC,  # noqa: F401
+                           CP, CC, FULL, CC_PP_ONLY, Result, SampledBLDTT, Tree)

@@ -59,7 +59,13 @@ independently, by the CUDA path):
       (Eq. (1) would otherwise divide by zero for i == j).
   R9  Eq. (16) sums over the actual (2, 4 or 8) children; the upper limit
       'b' in Eq. (14) is n.
-  R10 G = 1/r (no 4 pi) and Yukawa G = exp(-kappa r)/r (Sec. 4.6).
+  R10 G = 1/r (no 4 pi) and Yukawa G = exp(-kappa r)/r (Sec. 4.6).  The other
+      kernels of Sec. 4.6 take their parameter from kappa: oscillatory
+      G = sin(kappa r)/r (the paper's case is kappa = pi) and regularized
+      Coulomb G = 1/sqrt(r^2 + kappa^2) (the paper's eps = 0.005).  R8 applies
+      to every kernel, including the two that are finite at r = 0.
+  R12 The CC+PP-only variant (Sec. 4.3): a well-separated pair is CC when both
+      clusters hold more than n_p particles and PP otherwise.
   R11 Every cluster of both trees carries proxies; proxy potentials of
       clusters without CP/CC interactions stay zero but are still passed
       down.
@@ -73,7 +79,14 @@ import numpy as np
 
 COULOMB = 0
 YUKAWA = 1
+OSCILLATORY = 2
+REG_COULOMB = 3
 TEST_POLY = 99
+
+# Traversal variants: the full method, and the ablation of Sec. 4.3 that uses
+# only CC and PP (PC/CP candidates are computed directly).
+FULL = 0
+CC_PP_ONLY = 1
 
 PP, PC, CP, CC = 0, 1, 2, 3
 TYPE_NAMES = ("PP", "PC", "CP", "CC")
@@ -102,6 +115,11 @@ def kernel_values(kernel: int, kappa: float, dx, dy, dz):
         elif kernel == YUKAWA:
             r = np.sqrt(r2)
             g = np.exp(-kappa * r) / r
+        elif kernel == OSCILLATORY:
+            r = np.sqrt(r2)
+            g = np.sin(kappa * r) / r
+        elif kernel == REG_COULOMB:
+            g = 1.0 / np.sqrt(r2 + kappa * kappa)
         elif kernel == TEST_POLY:
             g = (1.0 + dx - 2.0 * dy + 3.0 * dz + dx * dy - dy * dz
                  + dx * dx * dz * dz - 0.5 * dy * dy)
@@ -371,8 +389,11 @@ def well_separated(tt: Tree, t: int, st: Tree, s: int, theta: float) -> bool:
     return tt.radius(t) + st.radius(s) < theta * R
 
 
-def dual_tree_traversal(tt: Tree, st: Tree, n: int, theta: float):
-    """Algorithm 2 from the root pair.  Returns four lists of (t, s) pairs."""
+def dual_tree_traversal(tt: Tree, st: Tree, n: int, theta: float, variant: int = FULL):
+    """Algorithm 2 from the root pair.  Returns four lists of (t, s) pairs.
+
+    variant CC_PP_ONLY is the ablation of Sec. 4.3 (reading R12).
+    """
     n_p = (n + 1) ** 3
     lists = ([], [], [], [])
     if tt.num_clusters == 0 or st.num_clusters == 0:
@@ -384,6 +405,8 @@ def dual_tree_traversal(tt: Tree, st: Tree, n: int, theta: float):
             big_s = st.count(s) > n_p
             if big_t and big_s:
                 lists[CC].append((t, s))
+            elif variant == CC_PP_ONLY:
+                lists[PP].append((t, s))
             elif big_t and not big_s:
                 lists[CP].append((t, s))
             elif not big_t and big_s:
@@ -533,11 +556,11 @@ class Result:
     counts: tuple              # kernel evaluations per type (PP, PC, CP, CC)
 
 
-def build_lists(targets, sources, n, theta, N0, M0):
+def build_lists(targets, sources, n, theta, N0, M0, variant=FULL):
     """Alg. 1 line 6 plus Alg. 2: trees and the four interaction lists."""
     tt = build_tree(targets, M0)
     st = build_tree(sources, N0)
-    lists = dual_tree_traversal(tt, st, n, theta)
+    lists = dual_tree_traversal(tt, st, n, theta, variant)
     return tt, st, lists
 
 
@@ -551,13 +574,13 @@ def interaction_counts(tt, st, lists, n):
 
 
 def bldtt(targets, sources, charges, kernel=COULOMB, kappa=0.0, n=8, theta=0.7,
-          N0=2000, M0=2000) -> Result:
+          N0=2000, M0=2000, variant=FULL) -> Result:
     """Algorithm 1: trees, upward pass, dual tree traversal, downward pass."""
     xs_in = np.asarray(targets, dtype=np.float64)
     ys_in = np.asarray(sources, dtype=np.float64)
     q_in = np.asarray(charges, dtype=np.float64)
     P = n + 1
-    tt, st, lists = build_lists(xs_in, ys_in, n, theta, N0, M0)
+    tt, st, lists = build_lists(xs_in, ys_in, n, theta, N0, M0, variant)
     xs = xs_in[:, tt.perm]
     ys = ys_in[:, st.perm]
     qs = q_in[st.perm]
@@ -636,12 +659,12 @@ class SampledBLDTT:
     """
 
     def __init__(self, targets, sources, charges, kernel=COULOMB, kappa=0.0, n=8,
-                 theta=0.7, N0=2000, M0=2000):
+                 theta=0.7, N0=2000, M0=2000, variant=FULL):
         self.kernel, self.kappa, self.n = kernel, kappa, n
         self.xs_in = np.asarray(targets, dtype=np.float64)
         ys_in = np.asarray(sources, dtype=np.float64)
         q_in = np.asarray(charges, dtype=np.float64)
-        self.tt, self.st, self.lists = build_lists(self.xs_in, ys_in, n, theta, N0, M0)
+        self.tt, self.st, self.lists = build_lists(self.xs_in, ys_in, n, theta, N0, M0, variant)
         self.xs = self.xs_in[:, self.tt.perm]
         self.ys = ys_in[:, self.st.perm]
         self.qs = q_in[self.st.perm]

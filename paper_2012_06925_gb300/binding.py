@@ -16,12 +16,13 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbldtt.so")
 
-COULOMB, YUKAWA, TEST_POLY = 0, 1, 99
+COULOMB, YUKAWA, OSCILLATORY, REG_COULOMB, TEST_POLY = 0, 1, 2, 3, 99
+VARIANT_FULL, VARIANT_CC_PP_ONLY = 0, 1
 FP64, FP32_BULK = 0, 1
 PP, PC, CP, CC = 0, 1, 2, 3
 
 EXPORTED = (
-    "bldtt_setup", "bldtt_set_charges", "bldtt_compute", "bldtt_check_error", "bldtt_stats",
+    "bldtt_setup", "bldtt_setup_ex", "bldtt_set_charges", "bldtt_compute", "bldtt_check_error", "bldtt_stats",
     "bldtt_destroy", "bldtt_status_string", "bldtt_last_error", "bldtt_tree_size",
     "bldtt_export_tree", "bldtt_export_lists", "bldtt_export_proxy_charges",
     "bldtt_export_proxy_potentials", "bldtt_direct_sum", "bldtt_solve_host",
@@ -33,6 +34,12 @@ class BLDTTError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
         super().__init__(what)
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("kappa", ctypes.c_double), ("n", ctypes.c_int),
+                ("theta", ctypes.c_double), ("N0", ctypes.c_int), ("M0", ctypes.c_int),
+                ("precision", ctypes.c_int), ("variant", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -77,6 +84,7 @@ def load_library(path: str = LIB_PATH):
     sig = {
         "bldtt_setup": (i32, [ctypes.POINTER(vp), vp, i64, vp, i64, vp, i32, dbl, i32, dbl, i32,
                                i32, i32, vp]),
+        "bldtt_setup_ex": (i32, [ctypes.POINTER(vp), vp, i64, vp, i64, vp, ctypes.POINTER(Params), vp]),
         "bldtt_set_charges": (i32, [vp, vp, vp]),
         "bldtt_compute": (i32, [vp, vp, vp]),
         "bldtt_check_error": (i32, [vp]),
@@ -136,7 +144,7 @@ class Plan:
     """A set-up BLDTT problem (bldtt_setup); compute() runs the compute phase."""
 
     def __init__(self, targets, sources, charges, kernel=COULOMB, kappa=0.0, n=8, theta=0.7,
-                 N0=2000, M0=2000, precision=FP32_BULK, stream=None):
+                 N0=2000, M0=2000, precision=FP32_BULK, stream=None, variant=VARIANT_FULL):
         lib = load_library()
         if targets.dim() != 2 or targets.shape[0] != 3 or sources.dim() != 2 or sources.shape[0] != 3:
             raise ValueError("targets and sources must have shape (3, count)")
@@ -146,10 +154,17 @@ class Plan:
         self.P = self.n + 1
         self.np = self.P ** 3
         self._h = ctypes.c_void_p()
-        _check(lib.bldtt_setup(ctypes.byref(self._h), _dptr(targets), self.M, _dptr(sources),
-                               self.N, _dptr(charges, self.N), int(kernel), float(kappa),
-                               self.n, float(theta), int(N0), int(M0), int(precision),
-                               _stream_ptr(stream)))
+        if variant == VARIANT_FULL:
+            _check(lib.bldtt_setup(ctypes.byref(self._h), _dptr(targets), self.M, _dptr(sources),
+                                   self.N, _dptr(charges, self.N), int(kernel), float(kappa),
+                                   self.n, float(theta), int(N0), int(M0), int(precision),
+                                   _stream_ptr(stream)))
+        else:
+            prm = Params(int(kernel), float(kappa), self.n, float(theta), int(N0), int(M0),
+                         int(precision), int(variant))
+            _check(lib.bldtt_setup_ex(ctypes.byref(self._h), _dptr(targets), self.M,
+                                      _dptr(sources), self.N, _dptr(charges, self.N),
+                                      ctypes.byref(prm), _stream_ptr(stream)))
 
     def _handle(self):
         if not self._h:

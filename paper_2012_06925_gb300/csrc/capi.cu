@@ -24,12 +24,14 @@ int validate(int64_t M, int64_t N, int kernel, double kappa, int n, double theta
     set_error("M=%lld and N=%lld must lie in [1, 2^31-1)", (long long)M, (long long)N);
     return BLDTT_EINVAL;
   }
-  if (kernel != BLDTT_COULOMB && kernel != BLDTT_YUKAWA && kernel != BLDTT_TEST_POLY) {
+  if (kernel != BLDTT_COULOMB && kernel != BLDTT_YUKAWA && kernel != BLDTT_OSCILLATORY &&
+      kernel != BLDTT_REG_COULOMB && kernel != BLDTT_TEST_POLY) {
     set_error("unknown kernel %d", kernel);
     return BLDTT_EINVAL;
   }
-  if (kernel == BLDTT_YUKAWA && !(finite(kappa) && kappa >= 0.0)) {
-    set_error("Yukawa kappa must be finite and >= 0 (got %g)", kappa);
+  if ((kernel == BLDTT_YUKAWA || kernel == BLDTT_OSCILLATORY || kernel == BLDTT_REG_COULOMB) &&
+      !(finite(kappa) && kappa >= 0.0)) {
+    set_error("kernel parameter kappa must be finite and >= 0 (got %g)", kappa);
     return BLDTT_EINVAL;
   }
   if (n < 1 || n > kMaxDegree) {
@@ -171,9 +173,10 @@ const char* bldtt_status_string(int status) {
 
 const char* bldtt_last_error(void) { return bldtt::last_error(); }
 
-int bldtt_setup(bldtt_plan** plan, const double* targets, int64_t M, const double* sources,
-                int64_t N, const double* charges, int kernel, double kappa, int n, double theta,
-                int N0, int M0, int precision, void* cuda_stream) {
+static int setup_common(bldtt_plan** plan, const double* targets, int64_t M, const double* sources,
+                        int64_t N, const double* charges, int kernel, double kappa, int n,
+                        double theta, int N0, int M0, int precision, int variant,
+                        void* cuda_stream) {
   if (!plan) {
     set_error("plan out-pointer is NULL");
     return BLDTT_EINVAL;
@@ -184,6 +187,10 @@ int bldtt_setup(bldtt_plan** plan, const double* targets, int64_t M, const doubl
     return BLDTT_EINVAL;
   }
   BL_TRY(validate(M, N, kernel, kappa, n, theta, N0, M0, precision));
+  if (variant != BLDTT_VARIANT_FULL && variant != BLDTT_VARIANT_CC_PP_ONLY) {
+    set_error("unknown traversal variant %d", variant);
+    return BLDTT_EINVAL;
+  }
   bldtt_plan* p = new (std::nothrow) bldtt_plan;
   if (!p) {
     set_error("host allocation of the plan failed");
@@ -192,7 +199,9 @@ int bldtt_setup(bldtt_plan** plan, const double* targets, int64_t M, const doubl
   p->M = M;
   p->N = N;
   p->kernel = kernel;
-  p->kappa = kernel == BLDTT_YUKAWA ? kappa : 0.0;
+  p->kappa = (kernel == BLDTT_YUKAWA || kernel == BLDTT_OSCILLATORY || kernel == BLDTT_REG_COULOMB)
+                 ? kappa : 0.0;
+  p->variant = variant;
   p->n = n;
   p->P = n + 1;
   p->np = p->P * p->P * p->P;
@@ -208,6 +217,25 @@ int bldtt_setup(bldtt_plan** plan, const double* targets, int64_t M, const doubl
   }
   *plan = p;
   return BLDTT_OK;
+}
+
+int bldtt_setup(bldtt_plan** plan, const double* targets, int64_t M, const double* sources,
+                int64_t N, const double* charges, int kernel, double kappa, int n, double theta,
+                int N0, int M0, int precision, void* cuda_stream) {
+  return setup_common(plan, targets, M, sources, N, charges, kernel, kappa, n, theta, N0, M0,
+                      precision, BLDTT_VARIANT_FULL, cuda_stream);
+}
+
+int bldtt_setup_ex(bldtt_plan** plan, const double* targets, int64_t M, const double* sources,
+                   int64_t N, const double* charges, const bldtt_params_t* prm,
+                   void* cuda_stream) {
+  if (!prm) {
+    if (plan) *plan = nullptr;
+    set_error("params pointer is NULL");
+    return BLDTT_EINVAL;
+  }
+  return setup_common(plan, targets, M, sources, N, charges, prm->kernel, prm->kappa, prm->n,
+                      prm->theta, prm->N0, prm->M0, prm->precision, prm->variant, cuda_stream);
 }
 
 int bldtt_set_charges(bldtt_plan* p, const double* charges, void* cuda_stream) {
@@ -380,7 +408,8 @@ int bldtt_direct_sum(const double* targets, int64_t M, const double* sources, in
     set_error("direct sum: NULL pointer or negative size");
     return BLDTT_EINVAL;
   }
-  if (kernel != BLDTT_COULOMB && kernel != BLDTT_YUKAWA && kernel != BLDTT_TEST_POLY) {
+  if (kernel != BLDTT_COULOMB && kernel != BLDTT_YUKAWA && kernel != BLDTT_OSCILLATORY &&
+      kernel != BLDTT_REG_COULOMB && kernel != BLDTT_TEST_POLY) {
     set_error("unknown kernel %d", kernel);
     return BLDTT_EINVAL;
   }

@@ -38,6 +38,11 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const double* __restr
         } else if (KERN == BLDTT_YUKAWA) {
           double r = sqrt(r2);
           g = exp(-kappa * r) / r;
+        } else if (KERN == BLDTT_OSCILLATORY) {
+          double r = sqrt(r2);
+          g = sin(kappa * r) / r;
+        } else if (KERN == BLDTT_REG_COULOMB) {
+          g = rsqrt(r2 + kappa * kappa);
         } else {
           g = 1.0 + dx - 2.0 * dy + 3.0 * dz + dx * dy - dy * dz + dx * dx * dz * dz - 0.5 * dy * dy;
         }
@@ -56,6 +61,10 @@ int direct_sum(const double* targets, int64_t M, const double* sources, int64_t 
     k_direct<BLDTT_COULOMB><<<blocks, kDirectThreads, 0, s>>>(targets, M, sources, N, charges, kappa, phi);
   else if (kernel == BLDTT_YUKAWA)
     k_direct<BLDTT_YUKAWA><<<blocks, kDirectThreads, 0, s>>>(targets, M, sources, N, charges, kappa, phi);
+  else if (kernel == BLDTT_OSCILLATORY)
+    k_direct<BLDTT_OSCILLATORY><<<blocks, kDirectThreads, 0, s>>>(targets, M, sources, N, charges, kappa, phi);
+  else if (kernel == BLDTT_REG_COULOMB)
+    k_direct<BLDTT_REG_COULOMB><<<blocks, kDirectThreads, 0, s>>>(targets, M, sources, N, charges, kappa, phi);
   else
     k_direct<BLDTT_TEST_POLY><<<blocks, kDirectThreads, 0, s>>>(targets, M, sources, N, charges, kappa, phi);
   int64_t dummy = 0;

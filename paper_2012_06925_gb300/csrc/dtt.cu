@@ -24,7 +24,7 @@ static TreeView view(const Tree& T) {
 enum PairAction : int8_t { kActPP = 0, kActPC = 1, kActCP = 2, kActCC = 3, kActSplitT = 4, kActSplitS = 5 };
 
 __global__ void k_dtt_classify(const int2* __restrict__ pairs, int32_t F, TreeView tt, TreeView st,
-                               int64_t np, double theta, int32_t* __restrict__ nkids,
+                               int64_t np, double theta, int variant, int32_t* __restrict__ nkids,
                                int32_t* __restrict__ isentry, int8_t* __restrict__ action) {
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= F) return;
@@ -40,6 +40,7 @@ __global__ void k_dtt_classify(const int2* __restrict__ pairs, int32_t F, TreeVi
   if (sep) {
     bool big_t = cnt_t > np, big_s = cnt_s > np;
     a = big_t ? (big_s ? kActCC : kActCP) : (big_s ? kActPC : kActPP);
+    if (variant == BLDTT_VARIANT_CC_PP_ONLY && a != kActCC) a = kActPP;   // Sec. 4.3 ablation
   } else {
     bool leaf_t = tt.nchild[t] == 0, leaf_s = st.nchild[s] == 0;
     if (leaf_t && leaf_s) a = kActPP;
@@ -133,8 +134,8 @@ int build_lists(bldtt_plan* p, cudaStream_t s) {
     BL_TRY(dalloc_n(&koff, F, s));
     BL_TRY(dalloc_n(&eoff, F, s));
     BL_TRY(dalloc_n(&action, F, s));
-    k_dtt_classify<<<nblk(F, 256), 256, 0, s>>>(front, F, tt, st, p->np, p->theta, nkids, isentry,
-                                                action);
+    k_dtt_classify<<<nblk(F, 256), 256, 0, s>>>(front, F, tt, st, p->np, p->theta, p->variant,
+                                                nkids, isentry, action);
     BL_LAUNCHED(cnt.launches);
     int32_t K = 0, En = 0;
     BL_TRY(scan_exclusive(nkids, koff, F, &K, s, cnt));

@@ -71,7 +71,7 @@ struct InteractView {
   double* phit;
   int* err;
   double kappa;
-  float neg_kappa_log2e;
+  float prm;                   // FP32 kernel parameter (see pair_f32)
 };
 
 struct StageMeta {
@@ -186,23 +186,37 @@ __device__ __forceinline__ T poly_kernel(T dx, T dy, T dz) {
          (T)0.5 * dy * dy;
 }
 
-// q * G in FP32; GUARD makes a pair at r^2 == 0 contribute 0.
+// Kernels that need an explicit r = 0 guard on every pair (finite at r = 0, or
+// the test kernel); they take the scalar path in FP32.
+template <int KERN>
+struct AlwaysGuarded {
+  static constexpr bool value = KERN == BLDTT_OSCILLATORY || KERN == BLDTT_REG_COULOMB ||
+                                KERN == BLDTT_TEST_POLY;
+};
+
+// q * G in FP32; GUARD makes a pair at r^2 == 0 contribute 0.  prm is the
+// kernel parameter in the form the kernel uses (Yukawa: -kappa*log2(e);
+// oscillatory: kappa; regularized Coulomb: kappa^2).
 template <int KERN, bool GUARD>
-__device__ __forceinline__ float pair_f32(float dx, float dy, float dz, float q, float nk) {
+__device__ __forceinline__ float pair_f32(float dx, float dy, float dz, float q, float prm) {
   float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
   if (KERN == BLDTT_TEST_POLY) return r2 > 0.f ? q * poly_kernel<float>(dx, dy, dz) : 0.f;
-  if (GUARD && !(r2 > 0.f)) return 0.f;
+  if ((GUARD || AlwaysGuarded<KERN>::value) && !(r2 > 0.f)) return 0.f;
+  if (KERN == BLDTT_REG_COULOMB) return q * rsqrt_approx(r2 + prm);
   float ri = rsqrt_approx(r2);
   if (KERN == BLDTT_COULOMB) return q * ri;
-  return (q * ri) * exp2_approx(r2 * ri * nk);
+  if (KERN == BLDTT_OSCILLATORY) return (q * ri) * sinf(prm * (r2 * ri));
+  return (q * ri) * exp2_approx(r2 * ri * prm);
 }
 template <int KERN, bool GUARD>
 __device__ __forceinline__ double pair_f64(double dx, double dy, double dz, double q, double kappa) {
   double r2 = dx * dx + dy * dy + dz * dz;
   if (KERN == BLDTT_TEST_POLY) return r2 > 0.0 ? q * poly_kernel<double>(dx, dy, dz) : 0.0;
-  if (GUARD && !(r2 > 0.0)) return 0.0;
+  if ((GUARD || AlwaysGuarded<KERN>::value) && !(r2 > 0.0)) return 0.0;
+  if (KERN == BLDTT_REG_COULOMB) return q * rsqrt(r2 + kappa * kappa);
   double ri = rsqrt(r2);
   if (KERN == BLDTT_COULOMB) return q * ri;
+  if (KERN == BLDTT_OSCILLATORY) return q * ri * sin(kappa * (r2 * ri));
   return q * ri * exp(-kappa * (r2 * ri));
 }
 
@@ -491,28 +505,28 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_interact(InteractView 
         for (int k = 0; k < K; ++k) x2[k][d] = f2_add(f2_sub(xh2[k][d], c2), xl2[k][d]);
       }
       float a[K];
-      if (KERN == BLDTT_TEST_POLY) {
+      if (AlwaysGuarded<KERN>::value) {
         chunk_f32_guarded<KERN, K>(reinterpret_cast<const float*>(sbuf[s]), count, x2, a,
-                                   v.neg_kappa_log2e);
+                                   v.prm);
       } else {
         if (K > 1 && !warp_full) {
           // the warp's last target row lies beyond a partial tile: evaluate the others only
           float a1[K > 1 ? K - 1 : 1];
           const f2_t(&x2s)[K > 1 ? K - 1 : 1][3] = *reinterpret_cast<const f2_t(*)[K > 1 ? K - 1 : 1][3]>(&x2);
           chunk_f32<KERN, (K > 1 ? K - 1 : 1)>(reinterpret_cast<const ulonglong2*>(sbuf[s]),
-                                               (count + 1) / 2, x2s, a1, v.neg_kappa_log2e);
+                                               (count + 1) / 2, x2s, a1, v.prm);
 #pragma unroll
           for (int k = 0; k < K; ++k) a[k] = k < K - 1 ? a1[k < K - 1 ? k : 0] : 0.f;
         } else {
           chunk_f32<KERN, K>(reinterpret_cast<const ulonglong2*>(sbuf[s]), (count + 1) / 2, x2, a,
-                             v.neg_kappa_log2e);
+                             v.prm);
         }
         bool bad = false;
 #pragma unroll
         for (int k = 0; k < K; ++k) bad = bad || not_finite(a[k]);
         if (__any_sync(0xffffffffu, bad))
           chunk_f32_guarded<KERN, K>(reinterpret_cast<const float*>(sbuf[s]), count, x2, a,
-                                     v.neg_kappa_log2e);
+                                     v.prm);
       }
 #pragma unroll
       for (int k = 0; k < K; ++k) acc[k] += (double)a[k];
@@ -520,7 +534,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_interact(InteractView 
       const double4* sb = reinterpret_cast<const double4*>(sbuf[s]);
       double a[K];
       chunk_f64<KERN, false, K>(sb, count, X, a, v.kappa);
-      if (KERN != BLDTT_TEST_POLY) {
+      if (!AlwaysGuarded<KERN>::value) {
         bool bad = false;
 #pragma unroll
         for (int k = 0; k < K; ++k) bad = bad || not_finite(a[k]);
@@ -544,11 +558,18 @@ constexpr int kNumLayouts = 3;
 
 template <bool F32, int KERN>
 static const void* kernel_for(int layout) {
-  switch (layout) {
-    case 1: return reinterpret_cast<const void*>(&k_interact<F32, KERN, 2, 4, 6>);
-    case 2: return reinterpret_cast<const void*>(&k_interact<F32, KERN, 4, 2, 8>);
-    default: return reinterpret_cast<const void*>(&k_interact<F32, KERN, 4, 2, 6>);
+  if (KERN == BLDTT_COULOMB) {   // the tuned path: every layout is instantiated
+    switch (layout) {
+      case 1: return reinterpret_cast<const void*>(&k_interact<F32, KERN, 2, 4, 6>);
+      case 2: return reinterpret_cast<const void*>(&k_interact<F32, KERN, 4, 2, 8>);
+      default: break;
+    }
   }
+  return reinterpret_cast<const void*>(&k_interact<F32, KERN, 4, 2, 6>);
+}
+
+static int effective_layout(const bldtt_plan* p) {
+  return p->kernel == BLDTT_COULOMB ? p->interact_layout : 0;
 }
 
 static const void* select_kernel(const bldtt_plan* p, int layout) {
@@ -556,12 +577,15 @@ static const void* select_kernel(const bldtt_plan* p, int layout) {
   switch (p->kernel) {
     case BLDTT_COULOMB: return f32 ? kernel_for<true, BLDTT_COULOMB>(layout) : kernel_for<false, BLDTT_COULOMB>(layout);
     case BLDTT_YUKAWA: return f32 ? kernel_for<true, BLDTT_YUKAWA>(layout) : kernel_for<false, BLDTT_YUKAWA>(layout);
+    case BLDTT_OSCILLATORY: return f32 ? kernel_for<true, BLDTT_OSCILLATORY>(layout) : kernel_for<false, BLDTT_OSCILLATORY>(layout);
+    case BLDTT_REG_COULOMB: return f32 ? kernel_for<true, BLDTT_REG_COULOMB>(layout) : kernel_for<false, BLDTT_REG_COULOMB>(layout);
     default: return f32 ? kernel_for<true, BLDTT_TEST_POLY>(layout) : kernel_for<false, BLDTT_TEST_POLY>(layout);
   }
 }
 
 int interaction_grid(bldtt_plan* p, int* grid) {
   int dev = 0, sms = 0, per_sm = 0;
+  p->interact_layout = effective_layout(p);
   const int threads = (kLayouts[p->interact_layout].ncw + 1) * 32;
   BL_CUDA(cudaGetDevice(&dev));
   BL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -604,7 +628,9 @@ int run_interactions(bldtt_plan* p, cudaStream_t s) {
   v.phit = p->phit;
   v.err = p->dev_err;
   v.kappa = p->kappa;
-  v.neg_kappa_log2e = (float)(-p->kappa * 1.4426950408889634);
+  v.prm = p->kernel == BLDTT_YUKAWA       ? (float)(-p->kappa * 1.4426950408889634)
+          : p->kernel == BLDTT_REG_COULOMB ? (float)(p->kappa * p->kappa)
+                                           : (float)p->kappa;
   BL_CUDA(cudaMemsetAsync(p->item_counter, 0, sizeof(int32_t), s));
   void* args[] = {&v};
   BL_CUDA(cudaLaunchKernel(select_kernel(p, p->interact_layout), dim3(p->interact_grid),

@@ -114,6 +114,7 @@ struct bldtt_plan {
   double theta = 0.0;
   int N0 = 0, M0 = 0;
   int precision = 0;
+  int variant = 0;                    // enum bldtt_variant
   int device = 0;
   cudaStream_t stream = nullptr;      // stream of the last call (for synchronisation)
 

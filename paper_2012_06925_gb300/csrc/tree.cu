@@ -9,6 +9,7 @@
 // box of its particles.  All geometric decisions are made in FP64 with
 // explicitly rounded operations (no FMA contraction) so that they are the
 // decisions a plain FP64 evaluation of the same expressions makes.
+#include <algorithm>
 #include <utility>
 
 #include "internal.cuh"
@@ -289,9 +290,10 @@ __global__ void k_tree_scatter(int32_t ls, const int32_t* __restrict__ chunk_clu
 }
 
 // Shrink every new cluster to the bounding box of its particles (Sec. 2.3):
-// each cluster is cut into kBoxSlices slices reduced by separate CTAs, then
-// one warp per cluster combines the slices.  Min/max are exact, so the result
-// does not depend on the split.
+// each cluster is cut into `slices` slices (up to kBoxSlices, chosen per level
+// from the average cluster size) reduced by separate CTAs, then one warp per
+// cluster combines the slices.  Min/max are exact, so the result does not
+// depend on the split.
 constexpr int kBoxSlices = 32;
 
 __global__ void k_tree_child_bbox(int32_t first, const int32_t* __restrict__ begin,
@@ -300,7 +302,7 @@ __global__ void k_tree_child_bbox(int32_t first, const int32_t* __restrict__ beg
                                   double* __restrict__ part) {
   const int c = first + blockIdx.x;
   const int32_t b = begin[c], cnt = end[c] - b;
-  const int32_t len = (cnt + kBoxSlices - 1) / kBoxSlices;
+  const int32_t len = (cnt + gridDim.y - 1) / gridDim.y;
   const int32_t s0 = b + blockIdx.y * len, s1 = min(s0 + len, b + cnt);
   double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   for (int32_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
@@ -327,17 +329,17 @@ __global__ void k_tree_child_bbox(int32_t first, const int32_t* __restrict__ beg
     double r = sm[0][threadIdx.x];
     for (int w = 1; w < kTreeThreads / 32; ++w)
       r = threadIdx.x < 3 ? fmin(r, sm[w][threadIdx.x]) : fmax(r, sm[w][threadIdx.x]);
-    part[((int64_t)blockIdx.x * kBoxSlices + blockIdx.y) * 6 + threadIdx.x] = r;
+    part[((int64_t)blockIdx.x * gridDim.y + blockIdx.y) * 6 + threadIdx.x] = r;
   }
 }
 
-__global__ void k_tree_child_bbox_combine(int32_t first, int32_t nc, const double* __restrict__ part,
-                                          double* __restrict__ box) {
+__global__ void k_tree_child_bbox_combine(int32_t first, int32_t nc, int slices,
+                                          const double* __restrict__ part, double* __restrict__ box) {
   const int j = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (j >= nc) return;
   for (int k = 0; k < 6; ++k) {
-    double r = part[((int64_t)j * kBoxSlices + lane) * 6 + k];
+    double r = lane < slices ? part[((int64_t)j * slices + lane) * 6 + k] : (k < 3 ? INFINITY : -INFINITY);
     for (int off = 16; off; off >>= 1) {
       double o = __shfl_down_sync(0xffffffffu, r, off);
       r = k < 3 ? fmin(r, o) : fmax(r, o);
@@ -480,12 +482,15 @@ int build_tree(Tree& T, const double* coords, int32_t n, int32_t max_leaf, int d
     { double* t = T.y; T.y = y2; y2 = t; }
     { double* t = T.z; T.z = z2; z2 = t; }
     { int32_t* t = T.perm; T.perm = perm2; perm2 = t; }
+    // slices per new cluster: about 16K particles each, at most kBoxSlices
+    int64_t per = (int64_t)n / nc;
+    int slices = (int)std::min<int64_t>(kBoxSlices, std::max<int64_t>(1, per / 16384));
     double* part = nullptr;
-    BL_TRY(dalloc_n(&part, (size_t)nc * kBoxSlices * 6, s));
-    k_tree_child_bbox<<<dim3(nc, kBoxSlices), kTreeThreads, 0, s>>>(le, T.begin, T.end, T.x, T.y,
-                                                                    T.z, part);
+    BL_TRY(dalloc_n(&part, (size_t)nc * slices * 6, s));
+    k_tree_child_bbox<<<dim3(nc, slices), kTreeThreads, 0, s>>>(le, T.begin, T.end, T.x, T.y, T.z,
+                                                                part);
     BL_LAUNCHED(cnt.launches);
-    k_tree_child_bbox_combine<<<nblk(nc, 4), 128, 0, s>>>(le, nc, part, T.box);
+    k_tree_child_bbox_combine<<<nblk(nc, 4), 128, 0, s>>>(le, nc, slices, part, T.box);
     BL_LAUNCHED(cnt.launches);
     dfree(part, s);
     T.level_start.push_back(le + nc);

@@ -63,6 +63,8 @@ def normal_charges(n: int, rng: np.random.Generator) -> np.ndarray:
 # Kernel identifiers (same numbering as the C ABI).
 COULOMB = 0
 YUKAWA = 1
+OSCILLATORY = 2
+REG_COULOMB = 3
 TEST_POLY = 99
 
 

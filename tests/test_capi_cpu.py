@@ -82,3 +82,16 @@ def test_setup_rejects_null_pointers(lib):
 def test_direct_sum_rejects_bad_arguments(lib):
     assert lib.bldtt_direct_sum(None, 1, DUMMY, 1, DUMMY, 0, 0.0, DUMMY, None) == 1
     assert lib.bldtt_direct_sum(DUMMY, 1, DUMMY, 1, DUMMY, 7, 0.0, DUMMY, None) == 1
+
+
+def test_setup_ex_rejects_bad_variant_and_params(lib):
+    h = ctypes.c_void_p()
+    prm = B.Params(0, 0.0, 4, 0.7, 10, 10, 1, 7)          # unknown variant
+    assert lib.bldtt_setup_ex(ctypes.byref(h), DUMMY, 100, DUMMY, 100, DUMMY, ctypes.byref(prm),
+                              None) == 1
+    assert lib.bldtt_setup_ex(ctypes.byref(h), DUMMY, 100, DUMMY, 100, DUMMY, None, None) == 1
+    for kernel in (2, 3):                                  # parameter of the Sec. 4.6 kernels
+        prm = B.Params(kernel, -0.5, 4, 0.7, 10, 10, 1, 0)
+        assert lib.bldtt_setup_ex(ctypes.byref(h), DUMMY, 100, DUMMY, 100, DUMMY,
+                                  ctypes.byref(prm), None) == 1
+    assert not h

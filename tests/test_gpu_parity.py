@@ -29,6 +29,14 @@ CASES = [
      dict(kernel=B.COULOMB, n=2, theta=0.6, N0=10, M0=7)),
     ("gaussian_n6", dict(kind="gaussian", n_targets=3000, n_sources=2500, seed=4),
      dict(kernel=B.YUKAWA, kappa=1.7, n=6, theta=0.9, N0=400, M0=300)),
+    ("oscillatory_pi", dict(kind="uniform", n_targets=4000, seed=15),
+     dict(kernel=B.OSCILLATORY, kappa=float(np.pi), n=4, theta=0.7, N0=60, M0=60)),
+    ("regularized_coulomb", dict(kind="sphere", n_targets=3500, n_sources=4000, seed=16,
+                                 sources_kind="uniform"),
+     dict(kernel=B.REG_COULOMB, kappa=0.005, n=3, theta=0.8, N0=40, M0=40)),
+    ("cc_pp_only_variant", dict(kind="uniform", n_targets=5000, n_sources=4500, seed=17,
+                                sources_kind="plummer"),
+     dict(kernel=B.COULOMB, n=2, theta=0.7, N0=20, M0=20, variant=B.VARIANT_CC_PP_ONLY)),
 ]
 
 
@@ -42,6 +50,8 @@ def problem(pkw):
 def test_trees_lists_and_potentials_match_oracle(name, pkw, mkw):
     tgt, src, q = problem(pkw)
     ref = O.bldtt(tgt, src, q, **mkw)
+    if mkw.get("variant") == B.VARIANT_CC_PP_ONLY:
+        assert len(ref.lists[O.PC]) == 0 and len(ref.lists[O.CP]) == 0 and len(ref.lists[O.CC]) > 0
     phi, plan = run_gpu(tgt, src, q, precision=B.FP64, **mkw)
     with plan:
         gt, gs = plan.export_tree(0), plan.export_tree(1)

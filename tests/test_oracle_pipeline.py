@@ -142,3 +142,45 @@ def test_paper_error_at_1e5():
     ref = O.direct_sum(tgt[:, idx], src, q)
     err = O.relative_l2_error(ref, got)
     assert row["bldtt_error"] / 6 <= err <= row["bldtt_error"] * 6
+
+
+# ---- the other kernels of Sec. 4.6 and the CC+PP-only variant of Sec. 4.3 ----
+
+def test_other_kernels_closed_forms():
+    g = O.kernel_values(O.OSCILLATORY, np.pi, np.array([0.5, 0.25, 0.0]), np.zeros(3), np.zeros(3))
+    assert abs(g[0] - 2.0) <= 1e-15 and abs(g[1] - np.sin(np.pi / 4) * 4) <= 1e-14 and g[2] == 0.0
+    g = O.kernel_values(O.REG_COULOMB, 0.005, np.array([0.3, 0.0]), np.array([0.4, 0.0]), np.zeros(2))
+    assert abs(g[0] - 1.0 / np.sqrt(0.25 + 0.005 ** 2)) <= 1e-15 and g[1] == 0.0
+
+
+@pytest.mark.parametrize("kernel,kappa", [(O.OSCILLATORY, np.pi), (O.REG_COULOMB, 0.005)])
+def test_other_kernels_theta_zero_and_convergence(kernel, kappa):
+    tgt, src, q = W.make_problem("uniform", 2500, seed=14)
+    ref = O.direct_sum(tgt, src, q, kernel, kappa)
+    res = O.bldtt(tgt, src, q, kernel=kernel, kappa=kappa, n=3, theta=0.0, N0=60, M0=60)
+    assert O.relative_l2_error(ref, res.phi) <= 1e-14
+    errs = [O.relative_l2_error(ref, O.bldtt(tgt, src, q, kernel=kernel, kappa=kappa, n=n,
+                                            theta=0.8, N0=30, M0=30).phi) for n in (2, 4, 6)]
+    assert errs[0] > errs[1] > errs[2]
+
+
+def test_cc_pp_only_variant():
+    """Sec. 4.3 ablation: no PC/CP entries, still every pair covered once, the
+    degree-2 kernel still reproduced exactly, and the extra PP work shows up."""
+    tgt, src, q = W.make_problem("uniform", 2500, 2200, seed=6, sources_kind="plummer")
+    full = O.bldtt(tgt, src, q, kernel=O.TEST_POLY, n=2, theta=0.7, N0=15, M0=15)
+    abl = O.bldtt(tgt, src, q, kernel=O.TEST_POLY, n=2, theta=0.7, N0=15, M0=15,
+                  variant=O.CC_PP_ONLY)
+    assert len(full.lists[O.PC]) > 0 and len(full.lists[O.CP]) > 0
+    assert len(abl.lists[O.PC]) == 0 and len(abl.lists[O.CP]) == 0
+    assert len(abl.lists[O.CC]) == len(full.lists[O.CC])
+    assert abl.counts[0] > full.counts[0]
+    ref = O.direct_sum(tgt, src, q, O.TEST_POLY)
+    assert O.relative_l2_error(ref, abl.phi) <= 1e-12
+    m = tgt.shape[1]
+    n = src.shape[1]
+    cover = np.zeros((m, n), dtype=np.int32)
+    for typ in range(4):
+        for t, s in abl.lists[typ]:
+            cover[abl.ttree.begin[t]:abl.ttree.end[t], abl.stree.begin[s]:abl.stree.end[s]] += 1
+    assert cover.min() == 1 and cover.max() == 1
