@@ -156,6 +156,35 @@ int bldtt_setup_ex(bldtt_plan** plan,
                    const bldtt_params_t* params, void* cuda_stream);
 
 /*
+ * bldtt_setup_batch - set up nprob independent problems as one plan, so that
+ * a single bldtt_compute (or one replay of bldtt_compute_graph) runs all of
+ * them: the trees of all problems are built level by level together (a
+ * forest with one root per problem), the traversal starts from every
+ * problem's pair of roots, and the interaction work of all problems is
+ * drained by one persistent launch per kernel type present in the batch
+ * (work items are grouped by the kernel of their problem).  Problem i owns targets [target_offsets[i],
+ * target_offsets[i+1]) and sources [source_offsets[i], source_offsets[i+1])
+ * of the concatenated SoA arrays (targets 3*M, sources 3*N, charges N, with
+ * M = target_offsets[nprob], N = source_offsets[nprob]); it interacts only
+ * with itself, with kernel kernels[i] and parameter kappas[i].  phi of
+ * bldtt_compute is the concatenation of the problems' potentials.
+ *
+ *  nprob                     >= 1 problems.
+ *  target_/source_offsets    host, nprob + 1 int64, starting at 0, strictly
+ *                            increasing (every problem has >= 1 target and
+ *                            >= 1 source).
+ *  kernels, kappas           host, nprob entries (enum bldtt_kernel, parameter).
+ *  params                    n, theta, N0, M0, precision, variant shared by all
+ *                            problems (its kernel and kappa are ignored).
+ * Ownership, synchronisation and errors as bldtt_setup.
+ */
+int bldtt_setup_batch(bldtt_plan** plan, int nprob,
+                      const double* targets, const int64_t* target_offsets,
+                      const double* sources, const int64_t* source_offsets,
+                      const double* charges, const int* kernels, const double* kappas,
+                      const bldtt_params_t* params, void* cuda_stream);
+
+/*
  * bldtt_set_charges - replace the source charges of a plan (device, N
  * float64, input order).  Trees and interaction lists depend only on the
  * positions and parameters and are reused.  Errors: EINVAL (NULL arguments,
@@ -174,6 +203,30 @@ int bldtt_set_charges(bldtt_plan* plan, const double* charges, void* cuda_stream
  * the next call that synchronises, e.g. bldtt_stats or bldtt_check_error).
  */
 int bldtt_compute(bldtt_plan* plan, double* phi, void* cuda_stream);
+
+/*
+ * bldtt_compute_graph - bldtt_compute through a CUDA graph.  The first call
+ * (and any call with a different phi pointer) captures the whole compute
+ * phase on cuda_stream into a graph and instantiates it; every call then
+ * launches that graph (one launch for all the compute-phase kernels).  The
+ * stream must be a created stream (not NULL or a default stream).  The plan
+ * keeps the graph until it is destroyed, re-captured or re-tuned.
+ * Errors: EINVAL, ECUDA.
+ */
+int bldtt_compute_graph(bldtt_plan* plan, double* phi, void* cuda_stream);
+
+/*
+ * bldtt_autotune - pick the fastest consumer layout of the interaction kernel
+ * for each kernel type of the plan: runs bldtt_compute once (phi, device M
+ * float64, receives its potentials), then times each kernel type's
+ * persistent launch three times per layout instantiated for that kernel
+ * (Coulomb: 4 warps x 2 targets at 6 or 8 CTAs/SM, 2 warps x 4 targets;
+ * other kernels: 4 warps x 2 targets) with CUDA events and keeps the fastest
+ * in the plan.  Results do not depend on the layout (bit for bit).  *chosen
+ * (may be NULL) receives the layout picked for the lowest kernel id of the
+ * plan.  Synchronous.  Errors: EINVAL, ECUDA, ETIMEOUT.
+ */
+int bldtt_autotune(bldtt_plan* plan, double* phi, void* cuda_stream, int* chosen);
 
 /* Synchronise the plan's last stream and report a device-side error flag
  * (ETIMEOUT from a bounded wait, EINTERNAL from a bounds check). */

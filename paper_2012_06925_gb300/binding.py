@@ -22,7 +22,8 @@ FP64, FP32_BULK = 0, 1
 PP, PC, CP, CC = 0, 1, 2, 3
 
 EXPORTED = (
-    "bldtt_setup", "bldtt_setup_ex", "bldtt_set_charges", "bldtt_compute", "bldtt_check_error", "bldtt_stats",
+    "bldtt_setup", "bldtt_setup_ex", "bldtt_setup_batch", "bldtt_set_charges",
+    "bldtt_compute_graph", "bldtt_autotune", "bldtt_compute", "bldtt_check_error", "bldtt_stats",
     "bldtt_destroy", "bldtt_status_string", "bldtt_last_error", "bldtt_tree_size",
     "bldtt_export_tree", "bldtt_export_lists", "bldtt_export_proxy_charges",
     "bldtt_export_proxy_potentials", "bldtt_direct_sum", "bldtt_solve_host",
@@ -85,6 +86,10 @@ def load_library(path: str = LIB_PATH):
         "bldtt_setup": (i32, [ctypes.POINTER(vp), vp, i64, vp, i64, vp, i32, dbl, i32, dbl, i32,
                                i32, i32, vp]),
         "bldtt_setup_ex": (i32, [ctypes.POINTER(vp), vp, i64, vp, i64, vp, ctypes.POINTER(Params), vp]),
+        "bldtt_setup_batch": (i32, [ctypes.POINTER(vp), i32, vp, P_i64, vp, P_i64, vp,
+                                    ctypes.POINTER(ctypes.c_int), P_dbl, ctypes.POINTER(Params), vp]),
+        "bldtt_compute_graph": (i32, [vp, vp, vp]),
+        "bldtt_autotune": (i32, [vp, vp, vp, ctypes.POINTER(ctypes.c_int)]),
         "bldtt_set_charges": (i32, [vp, vp, vp]),
         "bldtt_compute": (i32, [vp, vp, vp]),
         "bldtt_check_error": (i32, [vp]),
@@ -170,6 +175,50 @@ class Plan:
         if not self._h:
             raise RuntimeError("plan already destroyed")
         return self._h
+
+    @classmethod
+    def batch(cls, targets, target_offsets, sources, source_offsets, charges, kernels, kappas,
+              n=6, theta=0.7, N0=500, M0=500, precision=FP32_BULK, variant=VARIANT_FULL,
+              stream=None):
+        """A plan over independent problems (bldtt_setup_batch).  targets/sources
+        are CUDA float64 (3, total) concatenations; offsets, kernels and kappas
+        are per-problem host sequences."""
+        lib = load_library()
+        self = cls.__new__(cls)
+        self.M = int(targets.shape[1])
+        self.N = int(sources.shape[1])
+        self.n = int(n)
+        self.P = self.n + 1
+        self.np = self.P ** 3
+        self._h = ctypes.c_void_p()
+        nprob = len(kernels)
+        to = np.ascontiguousarray(target_offsets, dtype=np.int64)
+        so = np.ascontiguousarray(source_offsets, dtype=np.int64)
+        ks = np.ascontiguousarray(kernels, dtype=np.int32)
+        kp = np.ascontiguousarray(kappas, dtype=np.float64)
+        prm = Params(0, 0.0, self.n, float(theta), int(N0), int(M0), int(precision), int(variant))
+        _check(lib.bldtt_setup_batch(ctypes.byref(self._h), nprob, _dptr(targets),
+                                     _np_ptr(to, ctypes.c_int64), _dptr(sources),
+                                     _np_ptr(so, ctypes.c_int64), _dptr(charges, self.N),
+                                     ks.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                     _np_ptr(kp, ctypes.c_double), ctypes.byref(prm),
+                                     _stream_ptr(stream)))
+        return self
+
+    def compute_graph(self, phi, stream):
+        """Compute through a captured CUDA graph (stream: a created torch stream)."""
+        _check(load_library().bldtt_compute_graph(self._handle(), _dptr(phi, self.M),
+                                                   _stream_ptr(stream)))
+        return phi
+
+    def autotune(self, phi=None, stream=None) -> int:
+        import torch
+        if phi is None:
+            phi = torch.empty(self.M, dtype=torch.float64, device="cuda")
+        chosen = ctypes.c_int(-1)
+        _check(load_library().bldtt_autotune(self._handle(), _dptr(phi, self.M), _stream_ptr(stream),
+                                             ctypes.byref(chosen)))
+        return chosen.value
 
     def compute(self, phi=None, stream=None):
         import torch

@@ -1,5 +1,6 @@
 // C ABI of the library (declared, with argument conventions, in include/bldtt.h).
 #include <cmath>
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -11,6 +12,10 @@ namespace bldtt {
 const char* last_error();
 int configure_pass_kernels();
 }  // namespace bldtt
+
+namespace {
+int compute_body(bldtt_plan* p, double* phi, cudaStream_t s);
+}
 
 using namespace bldtt;
 
@@ -77,10 +82,16 @@ void release(bldtt_plan* p) {
   dfree_ptr(p->items, s);
   dfree_ptr(p->item_counter, s);
   dfree_ptr(p->chunk_frame, s);
+  dfree_ptr(p->pool_res, s);
+  dfree_ptr(p->item_box, s);
   dfree_ptr(p->qhat, s);
   dfree_ptr(p->phit, s);
   dfree_ptr(p->phi_near, s);
   dfree_ptr(p->dev_err, s);
+  dfree_ptr(p->prob_kernel, s);
+  dfree_ptr(p->prob_kappa, s);
+  dfree_ptr(p->prob_prm, s);
+  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
   cudaStreamSynchronize(s);
   for (auto& e : p->ev)
     if (e) cudaEventDestroy(e);
@@ -88,19 +99,43 @@ void release(bldtt_plan* p) {
   delete p;
 }
 
+// FP32 form of each kernel's parameter, as the interaction kernel uses it.
+float fp32_parameter(int kernel, double kappa) {
+  if (kernel == BLDTT_YUKAWA) return (float)(-kappa * 1.4426950408889634);   // -kappa log2(e)
+  if (kernel == BLDTT_REG_COULOMB) return (float)(kappa * kappa);
+  return (float)kappa;
+}
+
 int setup_impl(bldtt_plan* p, const double* targets, const double* sources, const double* charges) {
   cudaStream_t s = p->stream;
   BL_CUDA(cudaGetDevice(&p->device));
   BL_TRY(configure_pass_kernels());
   for (auto& e : p->ev) BL_CUDA(cudaEventCreate(&e));
+  {
+    const int P = p->nprob;
+    std::vector<float> prm(P);
+    for (int i = 0; i < P; ++i) prm[i] = fp32_parameter(p->prob_kernel_h[i], p->prob_kappa_h[i]);
+    BL_TRY(dalloc_n(&p->prob_kernel, P, s));
+    BL_TRY(dalloc_n(&p->prob_kappa, P, s));
+    BL_TRY(dalloc_n(&p->prob_prm, P, s));
+    BL_CUDA(cudaMemcpyAsync(p->prob_kernel, p->prob_kernel_h.data(), P * sizeof(int),
+                            cudaMemcpyHostToDevice, s));
+    BL_CUDA(cudaMemcpyAsync(p->prob_kappa, p->prob_kappa_h.data(), P * sizeof(double),
+                            cudaMemcpyHostToDevice, s));
+    BL_CUDA(cudaMemcpyAsync(p->prob_prm, prm.data(), P * sizeof(float), cudaMemcpyHostToDevice, s));
+    BL_CUDA(cudaStreamSynchronize(s));   // host staging vectors go out of scope
+  }
   BL_TRY(dalloc_n(&p->dev_err, 1, s));
   BL_CUDA(cudaMemsetAsync(p->dev_err, 0, sizeof(int), s));
   int* bad = nullptr;
   BL_TRY(dalloc_n(&bad, 1, s));
   BL_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
   BL_CUDA(cudaEventRecord(p->ev[0], s));
-  BL_TRY(build_tree(p->tt, targets, (int32_t)p->M, p->M0, p->n, bad, s, p->setup_counter));
-  BL_TRY(build_tree(p->st, sources, (int32_t)p->N, p->N0, p->n, bad, s, p->setup_counter));
+  BL_TRY(build_tree(p->tt, targets, (int32_t)p->M, p->t_off, p->M0, p->n, bad, s,
+                    p->setup_counter));
+  BL_TRY(build_tree(p->st, sources, (int32_t)p->N, p->s_off, p->N0, p->n, bad, s,
+                    p->setup_counter));
+  BL_TRY(morton_order_leaves(p->tt, s, p->setup_counter));
   BL_TRY(morton_order_leaves(p->st, s, p->setup_counter));
   BL_TRY(dalloc_n(&p->q_tree, p->N, s));
   BL_TRY(permute_charges(p, charges, s));
@@ -121,14 +156,21 @@ int setup_impl(bldtt_plan* p, const double* targets, const double* sources, cons
   BL_TRY(dalloc_n(&p->qhat, (size_t)p->st.nclusters * p->np, s));
   BL_TRY(dalloc_n(&p->phit, (size_t)p->tt.nclusters * p->np, s));
   BL_TRY(dalloc_n(&p->phi_near, (size_t)p->M, s));
-  BL_TRY(dalloc_n(&p->item_counter, 1, s));
+  BL_TRY(dalloc_n(&p->item_counter, p->segments.size() > 0 ? p->segments.size() : 1, s));
   BL_TRY(build_chunk_frames(p, s));
   p->interact_layout = 0;
   if (const char* lay = std::getenv("BLDTT_INTERACT_LAYOUT")) {
     int l = std::atoi(lay);
     p->interact_layout = (l >= 0 && l < 3) ? l : 0;
   }
-  BL_TRY(interaction_grid(p, &p->interact_grid));
+  for (auto& seg : p->segments) {      // the requested layout where it is instantiated
+    int cand[3];
+    const int nc = layouts_available(seg.kernel, cand);
+    seg.layout = 0;
+    for (int i = 0; i < nc; ++i)
+      if (cand[i] == p->interact_layout) seg.layout = p->interact_layout;
+  }
+  BL_TRY(interaction_grids(p));
   BL_CUDA(cudaEventRecord(p->ev[2], s));
   BL_CUDA(cudaStreamSynchronize(s));
   p->ms_tree = elapsed(p->ev[0], p->ev[1]);
@@ -173,10 +215,12 @@ const char* bldtt_status_string(int status) {
 
 const char* bldtt_last_error(void) { return bldtt::last_error(); }
 
-static int setup_common(bldtt_plan** plan, const double* targets, int64_t M, const double* sources,
-                        int64_t N, const double* charges, int kernel, double kappa, int n,
-                        double theta, int N0, int M0, int precision, int variant,
-                        void* cuda_stream) {
+// Common set-up of a batch of nprob problems (nprob = 1 for bldtt_setup).
+// t_off / s_off: host offsets (nprob + 1) of each problem's targets / sources.
+static int setup_common(bldtt_plan** plan, const double* targets, const int64_t* t_off,
+                        const double* sources, const int64_t* s_off, const double* charges,
+                        int nprob, const int* kernels, const double* kappas, int n, double theta,
+                        int N0, int M0, int precision, int variant, void* cuda_stream) {
   if (!plan) {
     set_error("plan out-pointer is NULL");
     return BLDTT_EINVAL;
@@ -186,7 +230,24 @@ static int setup_common(bldtt_plan** plan, const double* targets, int64_t M, con
     set_error("targets, sources and charges must be non-NULL device pointers");
     return BLDTT_EINVAL;
   }
-  BL_TRY(validate(M, N, kernel, kappa, n, theta, N0, M0, precision));
+  if (nprob < 1 || !t_off || !s_off || !kernels || !kappas) {
+    set_error("a batch needs at least one problem, offsets, kernels and kappas");
+    return BLDTT_EINVAL;
+  }
+  if (t_off[0] != 0 || s_off[0] != 0) {
+    set_error("problem offsets must start at 0");
+    return BLDTT_EINVAL;
+  }
+  for (int i = 0; i < nprob; ++i) {
+    if (t_off[i + 1] <= t_off[i] || s_off[i + 1] <= s_off[i]) {
+      set_error("problem %d has no targets or no sources (offsets must increase)", i);
+      return BLDTT_EINVAL;
+    }
+    BL_TRY(validate(t_off[i + 1] - t_off[i], s_off[i + 1] - s_off[i], kernels[i], kappas[i], n,
+                    theta, N0, M0, precision));
+  }
+  const int64_t M = t_off[nprob], N = s_off[nprob];
+  BL_TRY(validate(M, N, kernels[0], kappas[0], n, theta, N0, M0, precision));
   if (variant != BLDTT_VARIANT_FULL && variant != BLDTT_VARIANT_CC_PP_ONLY) {
     set_error("unknown traversal variant %d", variant);
     return BLDTT_EINVAL;
@@ -198,9 +259,21 @@ static int setup_common(bldtt_plan** plan, const double* targets, int64_t M, con
   }
   p->M = M;
   p->N = N;
-  p->kernel = kernel;
-  p->kappa = (kernel == BLDTT_YUKAWA || kernel == BLDTT_OSCILLATORY || kernel == BLDTT_REG_COULOMB)
-                 ? kappa : 0.0;
+  p->nprob = nprob;
+  p->t_off.assign(t_off, t_off + nprob + 1);
+  p->s_off.assign(s_off, s_off + nprob + 1);
+  for (int i = 0; i < nprob; ++i) {
+    const int k = kernels[i];
+    const bool has_kappa = k == BLDTT_YUKAWA || k == BLDTT_OSCILLATORY || k == BLDTT_REG_COULOMB;
+    p->prob_kernel_h.push_back(k);
+    p->prob_kappa_h.push_back(has_kappa ? kappas[i] : 0.0);
+  }
+  p->kernels_present = p->prob_kernel_h;
+  std::sort(p->kernels_present.begin(), p->kernels_present.end());
+  p->kernels_present.erase(std::unique(p->kernels_present.begin(), p->kernels_present.end()),
+                           p->kernels_present.end());
+  p->kernel = kernels[0];
+  p->kappa = p->prob_kappa_h[0];
   p->variant = variant;
   p->n = n;
   p->P = n + 1;
@@ -222,8 +295,13 @@ static int setup_common(bldtt_plan** plan, const double* targets, int64_t M, con
 int bldtt_setup(bldtt_plan** plan, const double* targets, int64_t M, const double* sources,
                 int64_t N, const double* charges, int kernel, double kappa, int n, double theta,
                 int N0, int M0, int precision, void* cuda_stream) {
-  return setup_common(plan, targets, M, sources, N, charges, kernel, kappa, n, theta, N0, M0,
-                      precision, BLDTT_VARIANT_FULL, cuda_stream);
+  const int64_t t_off[2] = {0, M}, s_off[2] = {0, N};
+  if (M < 1 || N < 1) {
+    if (plan) *plan = nullptr;
+    BL_TRY(validate(M, N, kernel, kappa, n, theta, N0, M0, precision));
+  }
+  return setup_common(plan, targets, t_off, sources, s_off, charges, 1, &kernel, &kappa, n, theta,
+                      N0, M0, precision, BLDTT_VARIANT_FULL, cuda_stream);
 }
 
 int bldtt_setup_ex(bldtt_plan** plan, const double* targets, int64_t M, const double* sources,
@@ -234,8 +312,29 @@ int bldtt_setup_ex(bldtt_plan** plan, const double* targets, int64_t M, const do
     set_error("params pointer is NULL");
     return BLDTT_EINVAL;
   }
-  return setup_common(plan, targets, M, sources, N, charges, prm->kernel, prm->kappa, prm->n,
-                      prm->theta, prm->N0, prm->M0, prm->precision, prm->variant, cuda_stream);
+  const int64_t t_off[2] = {0, M}, s_off[2] = {0, N};
+  if (M < 1 || N < 1) {
+    if (plan) *plan = nullptr;
+    BL_TRY(validate(M, N, prm->kernel, prm->kappa, prm->n, prm->theta, prm->N0, prm->M0,
+                    prm->precision));
+  }
+  return setup_common(plan, targets, t_off, sources, s_off, charges, 1, &prm->kernel, &prm->kappa,
+                      prm->n, prm->theta, prm->N0, prm->M0, prm->precision, prm->variant,
+                      cuda_stream);
+}
+
+int bldtt_setup_batch(bldtt_plan** plan, int nprob, const double* targets, const int64_t* target_offsets,
+                      const double* sources, const int64_t* source_offsets, const double* charges,
+                      const int* kernels, const double* kappas, const bldtt_params_t* prm,
+                      void* cuda_stream) {
+  if (!prm) {
+    if (plan) *plan = nullptr;
+    set_error("params pointer is NULL");
+    return BLDTT_EINVAL;
+  }
+  return setup_common(plan, targets, target_offsets, sources, source_offsets, charges, nprob,
+                      kernels, kappas, prm->n, prm->theta, prm->N0, prm->M0, prm->precision,
+                      prm->variant, cuda_stream);
 }
 
 int bldtt_set_charges(bldtt_plan* p, const double* charges, void* cuda_stream) {
@@ -269,6 +368,110 @@ int bldtt_compute(bldtt_plan* p, double* phi, void* cuda_stream) {
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   p->stream = s;
   p->compute_counter.launches = 0;
+  return compute_body(p, phi, s);
+}
+
+int bldtt_compute_graph(bldtt_plan* p, double* phi, void* cuda_stream) {
+  if (!p || !phi) {
+    set_error("plan and phi must be non-NULL");
+    return BLDTT_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  if (s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread) {
+    set_error("bldtt_compute_graph needs a created (non-default) stream to capture on");
+    return BLDTT_EINVAL;
+  }
+  p->stream = s;
+  if (!p->graph_exec || p->graph_phi != phi) {
+    if (p->graph_exec) {
+      cudaGraphExecDestroy(p->graph_exec);
+      p->graph_exec = nullptr;
+    }
+    BL_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    p->compute_counter.launches = 0;
+    int st = compute_body(p, phi, s);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (st != BLDTT_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) {
+      set_error("stream capture of the compute phase failed: %s", cudaGetErrorString(e));
+      return BLDTT_ECUDA;
+    }
+    e = cudaGraphInstantiate(&p->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      p->graph_exec = nullptr;
+      set_error("graph instantiation failed: %s", cudaGetErrorString(e));
+      return BLDTT_ECUDA;
+    }
+    p->graph_phi = phi;
+  }
+  BL_CUDA(cudaGraphLaunch(p->graph_exec, s));
+  return BLDTT_OK;
+}
+
+int bldtt_autotune(bldtt_plan* p, double* phi, void* cuda_stream, int* chosen) {
+  if (!p || !phi) {
+    set_error("plan and phi must be non-NULL");
+    return BLDTT_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  p->stream = s;
+  // One full compute stages the pool; then every segment's launch is timed
+  // alone for each layout (a launch only overwrites its own items' outputs).
+  p->compute_counter.launches = 0;
+  BL_TRY(compute_body(p, phi, s));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  BL_CUDA(cudaEventCreate(&e0));
+  BL_CUDA(cudaEventCreate(&e1));
+  int rc = BLDTT_OK;
+  for (size_t g = 0; g < p->segments.size() && rc == BLDTT_OK; ++g) {
+    auto& seg = p->segments[g];
+    int cand[3];
+    const int ncand = layouts_available(seg.kernel, cand);
+    float best = -1.f;
+    int best_layout = seg.layout;
+    for (int i = 0; i < ncand && rc == BLDTT_OK; ++i) {
+      seg.layout = cand[i];
+      if ((rc = interaction_grids(p)) != BLDTT_OK) break;
+      float t = 0.f;
+      for (int rep = 0; rep < 3 && rc == BLDTT_OK; ++rep) {   // first run warms up
+        if (cudaEventRecord(e0, s) != cudaSuccess || (rc = run_segment(p, (int)g, s)) != BLDTT_OK ||
+            cudaEventRecord(e1, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+          if (rc == BLDTT_OK) rc = BLDTT_ECUDA;
+          break;
+        }
+        if ((rc = device_error(p)) != BLDTT_OK) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep == 1 || (rep > 1 && ms < t)) t = ms;
+      }
+      if (rc == BLDTT_OK && (best < 0.f || t < best)) {
+        best = t;
+        best_layout = cand[i];
+      }
+    }
+    seg.layout = best_layout;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  BL_TRY(rc);
+  BL_TRY(interaction_grids(p));
+  if (p->graph_exec) {                    // a captured graph used the old layouts
+    cudaGraphExecDestroy(p->graph_exec);
+    p->graph_exec = nullptr;
+  }
+  if (chosen) *chosen = p->segments.empty() ? 0 : p->segments[0].layout;
+  return BLDTT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+int compute_body(bldtt_plan* p, double* phi, cudaStream_t s) {
   BL_CUDA(cudaEventRecord(p->ev[0], s));
   BL_CUDA(cudaMemsetAsync(p->phit, 0, (size_t)p->tt.nclusters * p->np * sizeof(double), s));
   BL_CUDA(cudaMemsetAsync(p->phi_near, 0, (size_t)p->M * sizeof(double), s));
@@ -282,6 +485,9 @@ int bldtt_compute(bldtt_plan* p, double* phi, void* cuda_stream) {
   p->have_compute_events = true;
   return BLDTT_OK;
 }
+}  // namespace
+
+extern "C" {
 
 int bldtt_check_error(bldtt_plan* p) {
   if (!p) return BLDTT_EINVAL;
@@ -310,8 +516,8 @@ int bldtt_stats(bldtt_plan* p, bldtt_stats_t* out) {
   }
   out->executed_evaluations = p->executed_evaluations;
   out->work_items = p->nitems;
-  out->interact_grid = p->interact_grid;
-  out->interact_threads = p->interact_threads;
+  out->interact_grid = p->segments.empty() ? 0 : p->segments[0].grid;
+  out->interact_threads = p->segments.empty() ? 0 : p->segments[0].threads;
   out->ms_tree = p->ms_tree;
   out->ms_lists = p->ms_lists;
   if (p->have_compute_events) {

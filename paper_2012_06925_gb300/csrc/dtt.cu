@@ -8,6 +8,8 @@
 // rest are replaced by the pairs of the split side's children (Alg. 2,
 // lines 11-17).  Compaction uses prefix sums, so the entry order, and hence
 // every later summation order, is deterministic.
+#include <vector>
+
 #include "internal.cuh"
 
 namespace bldtt {
@@ -122,9 +124,20 @@ int build_lists(bldtt_plan* p, cudaStream_t s) {
   BL_TRY(dalloc_n(&ent_t, ecap, s));
   BL_TRY(dalloc_n(&ent_s, ecap, s));
   BL_TRY(dalloc_n(&ent_key, ecap, s));
-  int2 root = make_int2(0, 0);
-  BL_CUDA(cudaMemcpyAsync(front, &root, sizeof(int2), cudaMemcpyHostToDevice, s));
-  int32_t F = 1;
+  // One root pair per problem (Alg. 2 starts from the two roots of each problem).
+  const int32_t P = p->tt.nroots;
+  {
+    std::vector<int2> roots(P);
+    for (int32_t r = 0; r < P; ++r) roots[r] = make_int2(r, r);
+    if ((size_t)P > fcap) {
+      size_t c = fcap;
+      BL_TRY(dgrow(&front, &c, (size_t)P, 0, s));
+      fcap = c;
+    }
+    BL_CUDA(cudaMemcpyAsync(front, roots.data(), P * sizeof(int2), cudaMemcpyHostToDevice, s));
+    BL_CUDA(cudaStreamSynchronize(s));   // the host vector goes out of scope
+  }
+  int32_t F = P;
   int64_t E = 0;
   while (F > 0) {
     int32_t *nkids = nullptr, *isentry = nullptr, *koff = nullptr, *eoff = nullptr;
@@ -299,17 +312,29 @@ __global__ void k_item_count(int32_t nct, ListView L, const int32_t* __restrict_
   if (ex) atomicAdd(executed, ex);
 }
 
+// Sort key of an item: the segment (kernel group) of its problem in the high
+// bits, then decreasing cost.
+struct SegmentMap {
+  int n;
+  int kernel[8];
+};
+
 __global__ void k_item_fill(int32_t nct, const int32_t* __restrict__ off,
                             const int64_t* __restrict__ cost_part, const int64_t* __restrict__ cost_prox,
                             const int32_t* __restrict__ begin, const int32_t* __restrict__ end,
-                            int32_t np, int4* __restrict__ items, uint32_t* __restrict__ keys,
-                            int32_t* __restrict__ vals) {
+                            const int32_t* __restrict__ problem, const int* __restrict__ prob_kernel,
+                            SegmentMap segmap, int32_t np, int4* __restrict__ items,
+                            uint32_t* __restrict__ keys, int32_t* __restrict__ vals) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nct) return;
   int32_t o = off[c];
   const uint32_t kKeyMax = (1u << 24) - 1u;
+  uint32_t seg = 0;
+  const int kern = prob_kernel[problem[c]];
+  for (int i = 0; i < segmap.n; ++i)
+    if (segmap.kernel[i] == kern) seg = (uint32_t)i;
   if (cost_part[c] > 0) {
-    uint32_t k = kKeyMax - (uint32_t)min((int64_t)kKeyMax, cost_part[c]);
+    uint32_t k = (seg << 24) | (kKeyMax - (uint32_t)min((int64_t)kKeyMax, cost_part[c]));
     for (int32_t r = begin[c]; r < end[c]; r += kTile) {
       items[o] = make_int4(c, r, min(kTile, end[c] - r), kItemParticles);
       keys[o] = k;
@@ -318,7 +343,7 @@ __global__ void k_item_fill(int32_t nct, const int32_t* __restrict__ off,
     }
   }
   if (cost_prox[c] > 0) {
-    uint32_t k = kKeyMax - (uint32_t)min((int64_t)kKeyMax, cost_prox[c]);
+    uint32_t k = (seg << 24) | (kKeyMax - (uint32_t)min((int64_t)kKeyMax, cost_prox[c]));
     for (int32_t r = 0; r < np; r += kTile) {
       items[o] = make_int4(c, r, min(kTile, np - r), kItemProxies);
       keys[o] = k;
@@ -328,10 +353,59 @@ __global__ void k_item_fill(int32_t nct, const int32_t* __restrict__ off,
   }
 }
 
+// First item of every segment (keys sorted): first[seg] = i where the segment starts.
+__global__ void k_segment_starts(const uint32_t* __restrict__ keys, int32_t n, int32_t* __restrict__ first) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t sg = keys[i] >> 24;
+  if (i == 0 || (keys[i - 1] >> 24) != sg) first[sg] = i;
+}
+
 __global__ void k_gather_items(const int4* __restrict__ src, const int32_t* __restrict__ idx,
                                int4* __restrict__ dst, int64_t n) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) dst[i] = src[idx[i]];
+}
+
+// Bounding box of every 32-row group of every work item (the targets one warp
+// evaluates together in any consumer layout), rounded outward to floats; an
+// empty group gets an empty box.  One warp per group.
+__global__ void k_item_boxes(int32_t nitems, const int4* __restrict__ items, const double* __restrict__ x,
+                             const double* __restrict__ y, const double* __restrict__ z,
+                             const double* __restrict__ nodes, int P, float4* __restrict__ box) {
+  const int64_t w = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (w >= (int64_t)nitems * kItemGroups) return;
+  const int4 it = items[w / kItemGroups];
+  const int r = (int)(w % kItemGroups) * 32 + lane;
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  if (r < it.z) {
+    double v[3];
+    if (it.w == kItemParticles) {
+      const int64_t i = (int64_t)it.y + r;
+      v[0] = x[i];
+      v[1] = y[i];
+      v[2] = z[i];
+    } else {
+      const int l = it.y + r;
+      const double* nd = nodes + (int64_t)it.x * 3 * P;
+      v[0] = nd[l / (P * P)];
+      v[1] = nd[P + (l / P) % P];
+      v[2] = nd[2 * P + l % P];
+    }
+    for (int d = 0; d < 3; ++d) lo[d] = hi[d] = v[d];
+  }
+  for (int d = 0; d < 3; ++d)
+    for (int o = 16; o; o >>= 1) {
+      lo[d] = fmin(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+      hi[d] = fmax(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+    }
+  if (lane == 0) {
+    box[2 * w] = make_float4(__double2float_rd(lo[0]), __double2float_rd(lo[1]),
+                             __double2float_rd(lo[2]), 0.f);
+    box[2 * w + 1] = make_float4(__double2float_ru(hi[0]), __double2float_ru(hi[1]),
+                                 __double2float_ru(hi[2]), 0.f);
+  }
 }
 
 int build_work_items(bldtt_plan* p, cudaStream_t s) {
@@ -384,19 +458,53 @@ int build_work_items(bldtt_plan* p, cudaStream_t s) {
   BL_TRY(dalloc_n(&keys, ni, s));
   BL_TRY(dalloc_n(&vals, ni, s));
   BL_TRY(dalloc_n(&p->items, ni, s));
-  k_item_fill<<<nblk(nct, 128), 128, 0, s>>>(nct, off, cost_part, cost_prox, tt.begin, tt.end, p->np,
-                                             items, keys, vals);
+  SegmentMap segmap{};
+  segmap.n = (int)p->kernels_present.size();
+  for (int i = 0; i < segmap.n; ++i) segmap.kernel[i] = p->kernels_present[i];
+  k_item_fill<<<nblk(nct, 128), 128, 0, s>>>(nct, off, cost_part, cost_prox, tt.begin, tt.end,
+                                             tt.problem, p->prob_kernel, segmap, p->np, items, keys,
+                                             vals);
   BL_LAUNCHED(cnt.launches);
-  // Longest items first (stable), so the persistent kernel's tail is short.
-  BL_TRY(radix_sort_pairs(keys, vals, ni, 24, s, cnt));
+  // Grouped by kernel, longest items first within a group (stable), so that
+  // each persistent launch's tail is short.
+  int seg_bits = 0;
+  while ((1 << seg_bits) < segmap.n) ++seg_bits;
+  BL_TRY(radix_sort_pairs(keys, vals, ni, 24 + seg_bits, s, cnt));
+  int32_t* seg_first = nullptr;
+  BL_TRY(dalloc_n(&seg_first, 8, s));
+  BL_CUDA(cudaMemsetAsync(seg_first, 0xff, 8 * sizeof(int32_t), s));
+  if (ni > 0) {
+    k_segment_starts<<<nblk(ni, 256), 256, 0, s>>>(keys, ni, seg_first);
+    BL_LAUNCHED(cnt.launches);
+  }
+  int32_t h_first[8];
+  BL_CUDA(cudaMemcpyAsync(h_first, seg_first, sizeof(h_first), cudaMemcpyDeviceToHost, s));
   if (ni > 0) {
     k_gather_items<<<nblk(ni, 256), 256, 0, s>>>(items, vals, p->items, ni);
+    BL_LAUNCHED(cnt.launches);
+  }
+  if (p->precision == BLDTT_FP32_BULK && ni > 0) {
+    BL_TRY(dalloc_n(&p->item_box, (size_t)ni * kItemGroups * 2, s));
+    k_item_boxes<<<nblk((int64_t)ni * kItemGroups, 8), 256, 0, s>>>(ni, p->items, tt.x, tt.y, tt.z,
+                                                                    tt.nodes, p->P, p->item_box);
     BL_LAUNCHED(cnt.launches);
   }
   unsigned long long h_exec = 0;
   BL_CUDA(cudaMemcpyAsync(&h_exec, executed, sizeof(h_exec), cudaMemcpyDeviceToHost, s));
   BL_CUDA(cudaStreamSynchronize(s));
   p->executed_evaluations = (double)h_exec;
+  dfree(seg_first, s);
+  p->segments.clear();
+  for (int i = 0; i < segmap.n; ++i) {
+    if (h_first[i] < 0) continue;                    // no items for this kernel
+    int32_t end = ni;
+    for (int j = i + 1; j < segmap.n; ++j)
+      if (h_first[j] >= 0) {
+        end = h_first[j];
+        break;
+      }
+    p->segments.push_back({segmap.kernel[i], h_first[i], end - h_first[i], 0, 0, 0});
+  }
   dfree(items, s); dfree(keys, s); dfree(vals, s); dfree(executed, s);
   dfree(nitems, s); dfree(off, s); dfree(cost_part, s); dfree(cost_prox, s);
   return BLDTT_OK;

@@ -57,7 +57,9 @@ struct InteractView {
   const int32_t* s_leaf_first;
   const int32_t* s_leaf_last;
   const int32_t* pad_prefix;
-  const float4* chunk_frame;   // [chunks]: frame centre x, y, z (FP32) and the real count (int bits)
+  const float4* chunk_frame;   // [chunks][2]: frame centre + real count (int bits), extents + tau
+  const float* pool_res;       // FP32: frame residuals of the pool's particles (pair records)
+  const float4* item_box;      // FP32: [items][kItemGroups][2] target group boxes (lo, hi)
   int32_t np_pad;
   int64_t proxy_base;
   const void* pool;
@@ -70,14 +72,19 @@ struct InteractView {
   double* phi_near;
   double* phit;
   int* err;
-  double kappa;
-  float prm;                   // FP32 kernel parameter (see pair_f32)
+  // per-problem kernel parameters (read once per work item)
+  const int32_t* t_problem;    // target cluster -> problem
+  const float* prob_prm;       // FP32 kernel parameter (see pair_f32)
+  const double* prob_kappa;
 };
 
 struct StageMeta {
   int item;
   int count;                    // real sources in the staged chunk
+  int chunk;                    // pool chunk index
+  unsigned near;                // bit g: target group g may be near the chunk (residuals staged)
   unsigned long long c2[3];     // frame centre, each component duplicated (f32x2)
+  float4 ext;                   // half-extents and near distance tau (-inf: proxies)
 };
 
 // ---- PTX helpers: mbarrier, bulk copy, timer -------------------------------
@@ -221,19 +228,61 @@ __device__ __forceinline__ double pair_f64(double dx, double dy, double dz, doub
 }
 
 // ---- producer: walks an item's segments ------------------------------------
-template <typename Vec>
+template <typename Vec, int RES>
 struct Producer {
   const InteractView& v;
   Vec (*buf)[kChunk];
+  float4 (*rbuf)[RES];
   StageMeta* meta;
   uint64_t* full;
   uint64_t* empty;
   uint32_t it = 0;
   int cur_item = -1;
+  int cur_groups = 0;
+  float* ibox;                  // [6] bounding box of the current item's targets (shared memory)
 
-  __device__ Producer(const InteractView& v_, Vec (*b)[kChunk], StageMeta* m, uint64_t* f,
-                      uint64_t* e)
-      : v(v_), buf(b), meta(m), full(f), empty(e) {}
+  __device__ Producer(const InteractView& v_, Vec (*b)[kChunk], float4 (*r)[RES], StageMeta* m,
+                      uint64_t* f, uint64_t* e, float* box)
+      : v(v_), buf(b), rbuf(r), meta(m), full(f), empty(e), ibox(box) {}
+
+  __device__ __noinline__ void load_item_box() {
+    const float4* gb = v.item_box + (int64_t)cur_item * (2 * kItemGroups);
+    float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    for (int g = 0; g < cur_groups; ++g) {
+      const float4 lo = gb[2 * g], hi = gb[2 * g + 1];
+      b[0] = fminf(b[0], lo.x);
+      b[1] = fminf(b[1], lo.y);
+      b[2] = fminf(b[2], lo.z);
+      b[3] = fmaxf(b[3], hi.x);
+      b[4] = fmaxf(b[4], hi.y);
+      b[5] = fmaxf(b[5], hi.z);
+    }
+    for (int d = 0; d < 6; ++d) ibox[d] = b[d];
+  }
+
+  // Target groups of the current item whose box comes within tau of the
+  // particle chunk's box (c +- e): a superset of the targets the consumers'
+  // own test finds near.  The item's box is tested first.
+  __device__ __forceinline__ unsigned near_groups(const float4& f, const float4& ext) const {
+    if (!(ext.w >= 0.f)) return 0u;       // proxy chunk
+    const float gap = fmaxf(fmaxf(fmaxf(ibox[0] - (f.x + ext.x), (f.x - ext.x) - ibox[3]),
+                                  fmaxf(ibox[1] - (f.y + ext.y), (f.y - ext.y) - ibox[4])),
+                            fmaxf(ibox[2] - (f.z + ext.z), (f.z - ext.z) - ibox[5]));
+    return gap < ext.w ? near_groups_of_item(f, ext) : 0u;
+  }
+  __device__ __noinline__ unsigned near_groups_of_item(const float4 f, const float4 ext) const {
+    const float clo[3] = {f.x - ext.x, f.y - ext.y, f.z - ext.z};
+    const float chi[3] = {f.x + ext.x, f.y + ext.y, f.z + ext.z};
+    const float4* gb = v.item_box + (int64_t)cur_item * (2 * kItemGroups);
+    unsigned mask = 0;
+    for (int g = 0; g < cur_groups; ++g) {
+      const float4 lo = gb[2 * g], hi = gb[2 * g + 1];
+      const float gap = fmaxf(fmaxf(fmaxf(lo.x - chi[0], clo[0] - hi.x), fmaxf(lo.y - chi[1], clo[1] - hi.y)),
+                              fmaxf(lo.z - chi[2], clo[2] - hi.z));
+      if (gap < ext.w) mask |= 1u << g;
+    }
+    return mask;
+  }
 
   __device__ bool acquire(int& s) {
     s = (int)(it % kStages);
@@ -246,23 +295,29 @@ struct Producer {
       int s;
       if (!acquire(s)) return false;
       const int64_t q = (off + k) / kChunk;
-      const float4 f = v.chunk_frame[q];
+      const float4 f = v.chunk_frame[kChunkInfo * q];
       const int count = __float_as_int(f.w);
       StageMeta& m = meta[s];
       m.item = cur_item;
       m.count = count;
+      m.chunk = (int)q;
+      m.near = 0;
       uint32_t bytes;
       if (std::is_same<Vec, float4>::value) {
         m.c2[0] = f2_pack(f.x, f.x);
         m.c2[1] = f2_pack(f.y, f.y);
         m.c2[2] = f2_pack(f.z, f.z);
+        m.ext = v.chunk_frame[kChunkInfo * q + 1];
+        m.near = near_groups(f, m.ext);
         bytes = (uint32_t)(((count + 1) / 2) * 32);          // whole pair records
       } else {
         bytes = (uint32_t)(count * sizeof(Vec));
       }
       const char* src = reinterpret_cast<const char*>(v.pool) + (off + k) * (int64_t)sizeof(Vec);
-      mbar_arrive_tx(&full[s], bytes);
+      mbar_arrive_tx(&full[s], m.near ? 2 * bytes : bytes);
       bulk_copy_g2s(buf[s], src, bytes, &full[s]);
+      if (RES == kChunk && m.near)     // the chunk's frame residuals, same record layout
+        bulk_copy_g2s(rbuf[s], v.pool_res + q * (int64_t)(kChunk * 4), bytes, &full[s]);
       ++it;
     }
     return true;
@@ -292,6 +347,8 @@ struct Producer {
       if (idx >= v.nitems) break;
       int4 item = v.items[idx];
       cur_item = idx;
+      cur_groups = (item.z + 31) / 32;
+      if (std::is_same<Vec, float4>::value) load_item_box();
       if (item.w == kItemParticles) {
         for (int32_t a = item.x; a >= 0 && ok; a = v.t_parent[a]) ok = lists(BLDTT_PP, BLDTT_PC, a);
       } else {
@@ -318,18 +375,33 @@ struct Producer {
 // Packed evaluation of target k against the source pair (s0, s1):
 // acc += (q0 G(x - s0), q1 G(x - s1)).
 template <int KERN>
-__device__ __forceinline__ f2_t pair2_f32(f2_t tx, f2_t ty, f2_t tz, const ulonglong2& a,
-                                          const ulonglong2& b, f2_t acc, f2_t nk2) {
-  const f2_t dx = f2_sub(tx, a.x), dy = f2_sub(ty, a.y), dz = f2_sub(tz, b.x);
+__device__ __forceinline__ f2_t pair2_eval(f2_t dx, f2_t dy, f2_t dz, f2_t q2, f2_t acc, f2_t nk2) {
   const f2_t r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
   float r0, r1;
   f2_unpack(r2, r0, r1);
   const f2_t ri = f2_pack(rsqrt_approx(r0), rsqrt_approx(r1));
-  if (KERN == BLDTT_COULOMB) return f2_fma(b.y, ri, acc);
+  if (KERN == BLDTT_COULOMB) return f2_fma(q2, ri, acc);
   // Yukawa: q ri exp2(-kappa log2(e) r), r = r2 ri
   float e0, e1;
   f2_unpack(f2_mul(f2_mul(r2, ri), nk2), e0, e1);
-  return f2_fma(f2_mul(b.y, ri), f2_pack(exp2_approx(e0), exp2_approx(e1)), acc);
+  return f2_fma(f2_mul(q2, ri), f2_pack(exp2_approx(e0), exp2_approx(e1)), acc);
+}
+template <int KERN>
+__device__ __forceinline__ f2_t pair2_f32(f2_t tx, f2_t ty, f2_t tz, const ulonglong2& a,
+                                          const ulonglong2& b, f2_t acc, f2_t nk2) {
+  return pair2_eval<KERN>(f2_sub(tx, a.x), f2_sub(ty, a.y), f2_sub(tz, b.x), b.y, acc, nk2);
+}
+// Careful variant: d = fma(m, x_r - y_r, x'' - y'') with m = 1 for a target
+// near the chunk (frame residuals added) and m = 0 otherwise (exactly the
+// packed difference x'' - y'').
+template <int KERN>
+__device__ __forceinline__ f2_t pair2_careful(f2_t tx, f2_t ty, f2_t tz, f2_t rx, f2_t ry, f2_t rz,
+                                              f2_t m2, const ulonglong2& a, const ulonglong2& b,
+                                              const ulonglong2& ra, const ulonglong2& rb, f2_t acc,
+                                              f2_t nk2) {
+  return pair2_eval<KERN>(f2_fma(m2, f2_sub(rx, ra.x), f2_sub(tx, a.x)),
+                          f2_fma(m2, f2_sub(ry, ra.y), f2_sub(ty, a.y)),
+                          f2_fma(m2, f2_sub(rz, rb.x), f2_sub(tz, b.x)), b.y, acc, nk2);
 }
 
 // Sum over the staged chunk of q G for K targets; two partial sums per target.
@@ -362,26 +434,122 @@ __device__ __forceinline__ void chunk_f32(const ulonglong2* __restrict__ sb, int
   }
 }
 
-// Scalar re-evaluation with the r = 0 guard (rare: only chunks that produced a
-// non-finite partial sum), and the test kernel.
+// A consumer thread's targets, split v = hi + lo in FP32 (each duplicated
+// f32x2), kept in shared memory rather than registers: entry (k, d) of the
+// thread is h[(3k + d) * stride].
+struct TargetSplit {
+  const f2_t* h;
+  const f2_t* l;
+  int stride;
+  __device__ __forceinline__ f2_t hi(int k, int d) const { return h[(3 * k + d) * stride]; }
+  __device__ __forceinline__ f2_t lo(int k, int d) const { return l[(3 * k + d) * stride]; }
+};
+
+// Frame residual (frame_resid) of target slot k in the chunk's frame c2.
+__device__ __forceinline__ void target_residual(const TargetSplit& ts, const f2_t* c2, int k,
+                                                float (&xr)[3]) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    float c, h, l, hi;
+    f2_unpack(c2[d], c, hi);
+    f2_unpack(ts.hi(k, d), h, hi);
+    f2_unpack(ts.lo(k, d), l, hi);
+    xr[d] = frame_resid(h, l, c);
+  }
+}
+
+// Careful packed sum over the staged chunk (sr: its frame residual records).
 template <int KERN, int K>
-__device__ __forceinline__ void chunk_f32_guarded(const float* __restrict__ sf, int count,
-                                                  const f2_t (&x2)[K][3], float (&a)[K], float nk) {
-  float xs[K][3];
+__device__ __forceinline__ void chunk_f32_careful(const ulonglong2* __restrict__ sb,
+                                                  const ulonglong2* __restrict__ sr, int npairs,
+                                                  const f2_t (&x2)[K][3], const TargetSplit& ts,
+                                                  const f2_t* c2, unsigned near, float (&a)[K],
+                                                  float nk) {
+  const f2_t nk2 = f2_pack(nk, nk);
+  f2_t acc[K], m2[K], r2x[K][3];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    float hi;
-    f2_unpack(x2[k][0], xs[k][0], hi);
-    f2_unpack(x2[k][1], xs[k][1], hi);
-    f2_unpack(x2[k][2], xs[k][2], hi);
-    a[k] = 0.f;
+    const float m = ((near >> k) & 1u) ? 1.f : 0.f;
+    m2[k] = f2_pack(m, m);
+    float xr[3];
+    target_residual(ts, c2, k, xr);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) r2x[k][d] = f2_pack(xr[d], xr[d]);
+    acc[k] = 0ull;
   }
-  for (int j = 0; j < count; ++j) {
-    const float* r = sf + (j >> 1) * 8 + (j & 1);   // pair record: x0 x1 y0 y1 z0 z1 q0 q1
-    const float sx = r[0], sy = r[2], sz = r[4], q = r[6];
+#pragma unroll 2
+  for (int jp = 0; jp < npairs; ++jp) {
+    const ulonglong2 A = sb[2 * jp], Bq = sb[2 * jp + 1], RA = sr[2 * jp], RB = sr[2 * jp + 1];
 #pragma unroll
     for (int k = 0; k < K; ++k)
-      a[k] += pair_f32<KERN, true>(xs[k][0] - sx, xs[k][1] - sy, xs[k][2] - sz, q, nk);
+      acc[k] = pair2_careful<KERN>(x2[k][0], x2[k][1], x2[k][2], r2x[k][0], r2x[k][1], r2x[k][2],
+                                   m2[k], A, Bq, RA, RB, acc[k], nk2);
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    float lo, hi;
+    f2_unpack(acc[k], lo, hi);
+    a[k] = lo + hi;
+  }
+}
+
+// One pair in the fast path's scalar arithmetic (the packed path computes
+// exactly this per lane), with the r = 0 guard: acc + q G(d).
+template <int KERN>
+__device__ __forceinline__ float pair_acc_f32(float dx, float dy, float dz, float q, float prm,
+                                              float acc) {
+  const float r2 = fmaf(dz, dz, fmaf(dy, dy, __fmul_rn(dx, dx)));
+  if (!(r2 > 0.f)) return acc;
+  if (KERN == BLDTT_COULOMB) return fmaf(q, rsqrt_approx(r2), acc);
+  if (KERN == BLDTT_YUKAWA) {
+    const float ri = rsqrt_approx(r2);
+    return fmaf(__fmul_rn(q, ri), exp2_approx(__fmul_rn(__fmul_rn(r2, ri), prm)), acc);
+  }
+  return __fadd_rn(acc, pair_f32<KERN, true>(dx, dy, dz, q, prm));
+}
+
+// Scalar evaluation of a staged chunk: the same two partial sums (even and
+// odd entries) and the same arithmetic as the packed path, with the r = 0
+// guard.  Targets whose bit is set in `near` use the corrected difference
+//   d = fl(fl(x'' - y'') + fl(x_r - y_r))
+// of the frame coordinates x'', y'' and frame residuals x_r, y_r, which is
+// within a few u |d| of the exact x - y however small |d| is.  Every other
+// target gets bit for bit what the packed path gives it (when that is
+// finite), so a target's result does not depend on its warp.
+template <int KERN, int K>
+__device__ __forceinline__ void chunk_f32_slow(const float* __restrict__ sf, const float* __restrict__ res,
+                                               int count, const float (&xs)[K][3],
+                                               const TargetSplit& ts, const f2_t* c2, unsigned near,
+                                               float prm, float (&a)[K]) {
+  // one target slot at a time: few live registers on this rare path
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const bool nr = (near >> k) & 1u;
+    float xr[3] = {0.f, 0.f, 0.f};
+    if (nr) target_residual(ts, c2, k, xr);
+    float acc0 = 0.f, acc1 = 0.f;
+    for (int jp = 0; jp < (count + 1) / 2; ++jp) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = 2 * jp + h;
+        if (j < count) {
+          const float* r = sf + jp * 8 + h;   // pair record: x0 x1 y0 y1 z0 z1 q0 q1
+          float dx = __fsub_rn(xs[k][0], r[0]), dy = __fsub_rn(xs[k][1], r[2]),
+                dz = __fsub_rn(xs[k][2], r[4]);
+          if (nr) {
+            const float* e = res + jp * 8 + h;
+            dx = __fadd_rn(dx, __fsub_rn(xr[0], e[0]));
+            dy = __fadd_rn(dy, __fsub_rn(xr[1], e[2]));
+            dz = __fadd_rn(dz, __fsub_rn(xr[2], e[4]));
+          }
+          if (h == 0)
+            acc0 = pair_acc_f32<KERN>(dx, dy, dz, r[6], prm, acc0);
+          else
+            acc1 = pair_acc_f32<KERN>(dx, dy, dz, r[6], prm, acc1);
+        }
+      }
+    }
+    a[k] = acc0 + acc1;
   }
 }
 
@@ -432,12 +600,128 @@ __device__ __forceinline__ void store_output(const InteractView& v, const int4& 
   }
 }
 
+// Out-of-line entries to the rare paths of the packed kernels, so that their
+// registers do not burden the packed loop: they rebuild the targets' frame
+// coordinates from the shared-memory split (the same rounding as the packed
+// path) and return the K partial sums.
+template <int K>
+struct PartialSums {
+  float v[K];
+};
+template <int K>
+__device__ __forceinline__ void frame_targets(const TargetSplit& ts, const f2_t* c2, f2_t (&x2)[K][3]) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const f2_t c = c2[d];
+#pragma unroll
+    for (int k = 0; k < K; ++k) x2[k][d] = f2_add(f2_sub(ts.hi(k, d), c), ts.lo(k, d));
+  }
+}
+template <int KERN, int K>
+__device__ __noinline__ PartialSums<K> slow_sums(const float* sf, const float* res, int count,
+                                                 const TargetSplit ts, const f2_t* c2, unsigned near,
+                                                 float prm) {
+  f2_t x2[K][3];
+  frame_targets<K>(ts, c2, x2);
+  float xs[K][3];
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      float hi;
+      f2_unpack(x2[k][d], xs[k][d], hi);
+    }
+  PartialSums<K> out;
+  chunk_f32_slow<KERN, K>(sf, res, count, xs, ts, c2, near, prm, out.v);
+  return out;
+}
+// One staged chunk in FP32 for K targets (partial sums in a[]).  ts holds
+// the targets' FP32 splits and c2 the chunk's frame centre (duplicated
+// f32x2), x2 the targets' frame coordinates, ext the chunk's half-extents and
+// near distance tau, res its staged frame residuals, and bit k of `slot` says
+// that the producer found target slot k's group near the chunk.  A target
+// with max_d (|x''_d| - e_d) < tau is near: the warp then takes the careful
+// packed path, which adds the frame residuals for near targets only.
+// Otherwise the plain packed path runs.  A chunk whose packed sum is not
+// finite (some r = 0) is redone in the scalar path with the r = 0 guard.
+template <int KERN, int K>
+__device__ __forceinline__ void eval_chunk_f32(const void* buf, const float4* rbuf, int count,
+                                               const f2_t (&x2)[K][3], const TargetSplit& ts,
+                                               const f2_t* c2, const float4* ext_p, unsigned slot, bool warp_full,
+                                               float prm, float (&a)[K]) {
+  const float* sf = reinterpret_cast<const float*>(buf);
+  const float* res = reinterpret_cast<const float*>(rbuf);
+  float xs[K][3];
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      float hi;
+      f2_unpack(x2[k][d], xs[k][d], hi);
+    }
+  unsigned near = 0;
+  bool any_near = false;
+  if (slot) {                                   // warp-uniform
+    const float4 ext = *ext_p;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float m = fmaxf(fmaxf(fabsf(xs[k][0]) - ext.x, fabsf(xs[k][1]) - ext.y),
+                            fabsf(xs[k][2]) - ext.z);
+      if (((slot >> k) & 1u) && m < ext.w) near |= 1u << k;
+    }
+    any_near = __any_sync(0xffffffffu, near != 0);
+  }
+  if (AlwaysGuarded<KERN>::value) {
+    chunk_f32_slow<KERN, K>(sf, res, count, xs, ts, c2, near, prm, a);
+    return;
+  }
+  const ulonglong2* sb = reinterpret_cast<const ulonglong2*>(buf);
+  if (any_near) {
+    chunk_f32_careful<KERN, K>(sb, reinterpret_cast<const ulonglong2*>(rbuf), (count + 1) / 2, x2, ts,
+                               c2, near, a, prm);
+  } else if (K > 1 && !warp_full) {
+    // the warp's last target row lies beyond a partial tile: evaluate the others only
+    constexpr int K1 = K > 1 ? K - 1 : 1;
+    float a1[K1];
+    const f2_t(&x2s)[K1][3] = *reinterpret_cast<const f2_t(*)[K1][3]>(&x2);
+    chunk_f32<KERN, K1>(sb, (count + 1) / 2, x2s, a1, prm);
+#pragma unroll
+    for (int k = 0; k < K; ++k) a[k] = k < K1 ? a1[k < K1 ? k : 0] : 0.f;
+  } else {
+    chunk_f32<KERN, K>(sb, (count + 1) / 2, x2, a, prm);
+  }
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < K; ++k) bad = bad || not_finite(a[k]);
+  if (__any_sync(0xffffffffu, bad)) {
+    const PartialSums<K> r = slow_sums<KERN, K>(sf, res, count, ts, c2, near, prm);
+#pragma unroll
+    for (int k = 0; k < K; ++k) a[k] = r.v[k];
+  }
+}
+
+// One staged chunk in FP64 for K targets.
+template <int KERN, int K>
+__device__ __forceinline__ void eval_chunk_f64(const void* buf, int count, const double (&X)[K][3],
+                                               double kappa, double (&a)[K]) {
+  const double4* sb = reinterpret_cast<const double4*>(buf);
+  chunk_f64<KERN, false, K>(sb, count, X, a, kappa);
+  if (!AlwaysGuarded<KERN>::value) {
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) bad = bad || not_finite(a[k]);
+    if (__any_sync(0xffffffffu, bad)) chunk_f64<KERN, true, K>(sb, count, X, a, kappa);
+  }
+}
+
 template <bool F32, int KERN, int NCW, int K, int MINB>
 __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_interact(InteractView v) {
   static_assert(NCW * 32 * K == kTile, "a CTA covers exactly one work-item tile");
   constexpr int kConsumers = NCW * 32;
   using Vec = typename std::conditional<F32, float4, double4>::type;
   __shared__ __align__(128) Vec sbuf[kStages][kChunk];
+  constexpr int kRes = F32 ? kChunk : 1;     // frame residual records (FP32 only)
+  __shared__ __align__(128) float4 sres[kStages][kRes];
   __shared__ __align__(16) StageMeta smeta[kStages];
   __shared__ __align__(8) uint64_t full[kStages];
   __shared__ __align__(8) uint64_t empty[kStages];
@@ -453,7 +737,8 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_interact(InteractView 
 
   if (warp == NCW) {
     if (lane == 0) {
-      Producer<Vec> prod(v, sbuf, smeta, full, empty);
+      __shared__ float s_ibox[6];
+      Producer<Vec, kRes> prod(v, sbuf, sres, smeta, full, empty, s_ibox);
       prod.run();
     }
     return;
@@ -463,9 +748,14 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_interact(InteractView 
   int cur = -1;
   int4 item = make_int4(0, 0, 0, 0);
   double X[K][3];               // FP64 targets (FP64 path)
-  f2_t xh2[K][3], xl2[K][3];    // FP32 split of the targets, each duplicated (FP32 path)
+  // FP32 split of this thread's targets (FP32 path), in shared memory
+  constexpr int kSplit = F32 ? K * 3 * kConsumers : 1;
+  __shared__ __align__(16) f2_t s_th[kSplit], s_tl[kSplit];
+  const TargetSplit ts{s_th + ct, s_tl + ct, kConsumers};
   double acc[K];
   bool warp_full = true;
+  float prm = 0.f;              // its FP32 parameter
+  double kappa = 0.0;           // its FP64 parameter
   for (uint32_t it = 0;; ++it) {
     const int s = (int)(it % kStages);
     if (!mbar_wait(&full[s], (it / kStages) & 1u, v.err)) return;
@@ -478,6 +768,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_interact(InteractView 
       if (mi < 0) return;
       cur = mi;
       item = v.items[mi];
+      const int pid = v.t_problem[item.x];
+      prm = v.prob_prm[pid];
+      kappa = v.prob_kappa[pid];
       // does any row of this warp's last target slot hold a real target?
       warp_full = (K - 1) * kConsumers + (warp * 32) < item.z;
 #pragma unroll
@@ -489,8 +782,8 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_interact(InteractView 
           for (int d = 0; d < 3; ++d) {
             const float h = (float)X[k][d];
             const float l = (float)(X[k][d] - (double)h);
-            xh2[k][d] = f2_pack(h, h);
-            xl2[k][d] = f2_pack(l, l);
+            s_th[(3 * k + d) * kConsumers + ct] = f2_pack(h, h);
+            s_tl[(3 * k + d) * kConsumers + ct] = f2_pack(l, l);
           }
         }
       }
@@ -498,48 +791,27 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_interact(InteractView 
     const int count = smeta[s].count;
     if (F32) {
       f2_t x2[K][3];
+      const f2_t* c2 = smeta[s].c2;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        const f2_t c2 = smeta[s].c2[d];
+        const f2_t c = c2[d];
 #pragma unroll
-        for (int k = 0; k < K; ++k) x2[k][d] = f2_add(f2_sub(xh2[k][d], c2), xl2[k][d]);
+        for (int k = 0; k < K; ++k) x2[k][d] = f2_add(f2_sub(ts.hi(k, d), c), ts.lo(k, d));
+      }
+      const float4* ext = &smeta[s].ext;
+      const unsigned gm = smeta[s].near;
+      unsigned slot = 0;
+      if (gm) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) slot |= ((gm >> (k * NCW + warp)) & 1u) << k;
       }
       float a[K];
-      if (AlwaysGuarded<KERN>::value) {
-        chunk_f32_guarded<KERN, K>(reinterpret_cast<const float*>(sbuf[s]), count, x2, a,
-                                   v.prm);
-      } else {
-        if (K > 1 && !warp_full) {
-          // the warp's last target row lies beyond a partial tile: evaluate the others only
-          float a1[K > 1 ? K - 1 : 1];
-          const f2_t(&x2s)[K > 1 ? K - 1 : 1][3] = *reinterpret_cast<const f2_t(*)[K > 1 ? K - 1 : 1][3]>(&x2);
-          chunk_f32<KERN, (K > 1 ? K - 1 : 1)>(reinterpret_cast<const ulonglong2*>(sbuf[s]),
-                                               (count + 1) / 2, x2s, a1, v.prm);
-#pragma unroll
-          for (int k = 0; k < K; ++k) a[k] = k < K - 1 ? a1[k < K - 1 ? k : 0] : 0.f;
-        } else {
-          chunk_f32<KERN, K>(reinterpret_cast<const ulonglong2*>(sbuf[s]), (count + 1) / 2, x2, a,
-                             v.prm);
-        }
-        bool bad = false;
-#pragma unroll
-        for (int k = 0; k < K; ++k) bad = bad || not_finite(a[k]);
-        if (__any_sync(0xffffffffu, bad))
-          chunk_f32_guarded<KERN, K>(reinterpret_cast<const float*>(sbuf[s]), count, x2, a,
-                                     v.prm);
-      }
+      eval_chunk_f32<KERN, K>(sbuf[s], sres[s], count, x2, ts, c2, ext, slot, warp_full, prm, a);
 #pragma unroll
       for (int k = 0; k < K; ++k) acc[k] += (double)a[k];
     } else {
-      const double4* sb = reinterpret_cast<const double4*>(sbuf[s]);
       double a[K];
-      chunk_f64<KERN, false, K>(sb, count, X, a, v.kappa);
-      if (!AlwaysGuarded<KERN>::value) {
-        bool bad = false;
-#pragma unroll
-        for (int k = 0; k < K; ++k) bad = bad || not_finite(a[k]);
-        if (__any_sync(0xffffffffu, bad)) chunk_f64<KERN, true, K>(sb, count, X, a, v.kappa);
-      }
+      eval_chunk_f64<KERN, K>(sbuf[s], count, X, kappa, a);
 #pragma unroll
       for (int k = 0; k < K; ++k) acc[k] += a[k];
     }
@@ -554,27 +826,27 @@ struct Layout {
   int ncw, k, minb;
 };
 static const Layout kLayouts[] = {{4, 2, 6}, {2, 4, 6}, {4, 2, 8}};
-constexpr int kNumLayouts = 3;
 
 template <bool F32, int KERN>
 static const void* kernel_for(int layout) {
-  if (KERN == BLDTT_COULOMB) {   // the tuned path: every layout is instantiated
-    switch (layout) {
-      case 1: return reinterpret_cast<const void*>(&k_interact<F32, KERN, 2, 4, 6>);
-      case 2: return reinterpret_cast<const void*>(&k_interact<F32, KERN, 4, 2, 8>);
-      default: break;
-    }
+  if constexpr (KERN == BLDTT_COULOMB) {
+    if (layout == 1) return reinterpret_cast<const void*>(&k_interact<F32, KERN, 2, 4, 6>);
+    if (layout == 2) return reinterpret_cast<const void*>(&k_interact<F32, KERN, 4, 2, 8>);
   }
   return reinterpret_cast<const void*>(&k_interact<F32, KERN, 4, 2, 6>);
 }
 
-static int effective_layout(const bldtt_plan* p) {
-  return p->kernel == BLDTT_COULOMB ? p->interact_layout : 0;
+// Layouts instantiated for a kernel (the autotuner tries these).
+int layouts_available(int kernel, int* out) {
+  out[0] = 0;
+  if (kernel != BLDTT_COULOMB) return 1;
+  out[1] = 1;
+  out[2] = 2;
+  return 3;
 }
 
-static const void* select_kernel(const bldtt_plan* p, int layout) {
-  bool f32 = p->precision == BLDTT_FP32_BULK;
-  switch (p->kernel) {
+static const void* select_kernel(int kernel, bool f32, int layout) {
+  switch (kernel) {
     case BLDTT_COULOMB: return f32 ? kernel_for<true, BLDTT_COULOMB>(layout) : kernel_for<false, BLDTT_COULOMB>(layout);
     case BLDTT_YUKAWA: return f32 ? kernel_for<true, BLDTT_YUKAWA>(layout) : kernel_for<false, BLDTT_YUKAWA>(layout);
     case BLDTT_OSCILLATORY: return f32 ? kernel_for<true, BLDTT_OSCILLATORY>(layout) : kernel_for<false, BLDTT_OSCILLATORY>(layout);
@@ -583,24 +855,27 @@ static const void* select_kernel(const bldtt_plan* p, int layout) {
   }
 }
 
-int interaction_grid(bldtt_plan* p, int* grid) {
-  int dev = 0, sms = 0, per_sm = 0;
-  p->interact_layout = effective_layout(p);
-  const int threads = (kLayouts[p->interact_layout].ncw + 1) * 32;
+// Persistent grid of every segment: all CTAs that fit on the device at once
+// (never more than the segment's items).
+int interaction_grids(bldtt_plan* p) {
+  int dev = 0, sms = 0;
   BL_CUDA(cudaGetDevice(&dev));
   BL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_kernel(p, p->interact_layout),
-                                                        threads, 0));
-  if (per_sm < 1) per_sm = 1;
-  int g = sms * per_sm;
-  if (p->nitems > 0 && g > p->nitems) g = p->nitems;
-  *grid = g < 1 ? 1 : g;
-  p->interact_threads = threads;
+  const bool f32 = p->precision == BLDTT_FP32_BULK;
+  for (auto& seg : p->segments) {
+    int per_sm = 0;
+    seg.threads = (kLayouts[seg.layout].ncw + 1) * 32;
+    BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, select_kernel(seg.kernel, f32, seg.layout), seg.threads, 0));
+    if (per_sm < 1) per_sm = 1;
+    const int g = sms * per_sm;
+    seg.grid = g > seg.count ? seg.count : g;
+    if (seg.grid < 1) seg.grid = 1;
+  }
   return BLDTT_OK;
 }
 
-int run_interactions(bldtt_plan* p, cudaStream_t s) {
-  if (p->nitems == 0) return BLDTT_OK;
+static InteractView make_view(const bldtt_plan* p) {
   const Tree& tt = p->tt;
   const Tree& st = p->st;
   InteractView v;
@@ -615,6 +890,8 @@ int run_interactions(bldtt_plan* p, cudaStream_t s) {
   v.s_leaf_last = st.leaf_last;
   v.pad_prefix = p->pad_prefix;
   v.chunk_frame = p->chunk_frame;
+  v.pool_res = p->pool_res;
+  v.item_box = p->item_box;
   v.np_pad = p->np_pad;
   v.proxy_base = p->pool_particles;
   v.pool = p->pool;
@@ -627,15 +904,41 @@ int run_interactions(bldtt_plan* p, cudaStream_t s) {
   v.phi_near = p->phi_near;
   v.phit = p->phit;
   v.err = p->dev_err;
-  v.kappa = p->kappa;
-  v.prm = p->kernel == BLDTT_YUKAWA       ? (float)(-p->kappa * 1.4426950408889634)
-          : p->kernel == BLDTT_REG_COULOMB ? (float)(p->kappa * p->kappa)
-                                           : (float)p->kappa;
-  BL_CUDA(cudaMemsetAsync(p->item_counter, 0, sizeof(int32_t), s));
+  v.t_problem = tt.problem;
+  v.prob_prm = p->prob_prm;
+  v.prob_kappa = p->prob_kappa;
+  return v;
+}
+
+// One segment's persistent launch over items [first, first + count).
+static int launch_segment(const bldtt_plan* p, const InteractView& base, int g, cudaStream_t s) {
+  const auto& seg = p->segments[g];
+  InteractView v = base;
+  v.items = p->items + seg.first;
+  v.nitems = seg.count;
+  v.counter = p->item_counter + g;
+  if (v.item_box) v.item_box = p->item_box + (int64_t)seg.first * (2 * kItemGroups);
   void* args[] = {&v};
-  BL_CUDA(cudaLaunchKernel(select_kernel(p, p->interact_layout), dim3(p->interact_grid),
-                           dim3(p->interact_threads), args, 0, s));
+  BL_CUDA(cudaLaunchKernel(select_kernel(seg.kernel, p->precision == BLDTT_FP32_BULK, seg.layout),
+                           dim3(seg.grid), dim3(seg.threads), args, 0, s));
+  return BLDTT_OK;
+}
+
+int run_segment(bldtt_plan* p, int g, cudaStream_t s) {
+  BL_CUDA(cudaMemsetAsync(p->item_counter + g, 0, sizeof(int32_t), s));
+  BL_TRY(launch_segment(p, make_view(p), g, s));
   BL_LAUNCHED(p->compute_counter.launches);
+  return BLDTT_OK;
+}
+
+int run_interactions(bldtt_plan* p, cudaStream_t s) {
+  if (p->nitems == 0 || p->segments.empty()) return BLDTT_OK;
+  const InteractView v = make_view(p);
+  BL_CUDA(cudaMemsetAsync(p->item_counter, 0, p->segments.size() * sizeof(int32_t), s));
+  for (int g = 0; g < (int)p->segments.size(); ++g) {
+    BL_TRY(launch_segment(p, v, g, s));
+    BL_LAUNCHED(p->compute_counter.launches);
+  }
   return BLDTT_OK;
 }
 

@@ -31,6 +31,32 @@ constexpr int kMaxP = kMaxDegree + 1;
 constexpr int kChunk = 64;                     // sources per staged chunk
 constexpr int kTile = 256;                     // targets per work item of the interaction kernel
 constexpr int kStages = 6;                     // depth of the shared-memory ring
+constexpr int kChunkInfo = 2;                  // float4 per pool chunk description
+constexpr int kItemGroups = kTile / 32;        // 32-row target groups per work item
+
+// ---- FP32 frame coordinates ------------------------------------------------
+// A coordinate v (FP64) is carried in FP32 relative to a frame centre c (a
+// float) by the split v = hi + lo, hi = fl(v), lo = fl(v - hi):
+//   main  = fl(fl(hi - c) + lo)
+//   resid = the exact rounding errors of both additions (TwoSum), summed,
+// so that hi - c + lo = main + resid to within u^2 |v|.  The same expressions
+// serve the source pool and the targets, so that equal FP64 points get equal
+// FP32 parts.
+__device__ __forceinline__ float frame_main(float hi, float lo, float c) {
+  return __fadd_rn(__fsub_rn(hi, c), lo);
+}
+__device__ __forceinline__ float two_sum_err(float a, float b, float s) {
+  const float bb = __fsub_rn(s, a);
+  return __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ float frame_resid(float hi, float lo, float c) {
+  const float d = __fsub_rn(hi, c);
+  return __fadd_rn(two_sum_err(hi, -c, d), two_sum_err(d, lo, __fadd_rn(d, lo)));
+}
+__device__ __forceinline__ void split_f64(double v, float& hi, float& lo) {
+  hi = __double2float_rn(v);
+  lo = __double2float_rn(__dsub_rn(v, (double)hi));
+}
 
 enum ItemKind { kItemParticles = 0, kItemProxies = 1 };
 
@@ -90,6 +116,8 @@ struct Tree {
   int32_t* perm = nullptr;            // tree position -> input index
   int32_t *begin = nullptr, *end = nullptr, *parent = nullptr;
   int32_t *first_child = nullptr, *nchild = nullptr, *level = nullptr;
+  int32_t* problem = nullptr;         // [C] problem (root) the cluster belongs to
+  int32_t nroots = 1;                 // problems: clusters 0..nroots-1 are the roots
   double* box = nullptr;              // [C][6]: lo x,y,z, hi x,y,z
   double* center = nullptr;           // [C][3]
   double* radius = nullptr;           // [C]
@@ -116,6 +144,17 @@ struct bldtt_plan {
   int precision = 0;
   int variant = 0;                    // enum bldtt_variant
   int device = 0;
+
+  // Problems of a batch (one for bldtt_setup): particle offsets of each
+  // problem's targets and sources, and each problem's kernel and parameter.
+  int32_t nprob = 1;
+  std::vector<int32_t> t_off, s_off;  // host, nprob + 1 entries
+  std::vector<int> prob_kernel_h;     // host copies
+  std::vector<double> prob_kappa_h;
+  int* prob_kernel = nullptr;         // device [nprob]
+  double* prob_kappa = nullptr;       // device [nprob]
+  float* prob_prm = nullptr;          // device [nprob] FP32 form of the parameter
+  std::vector<int> kernels_present;   // distinct kernel ids of the batch, ascending
   cudaStream_t stream = nullptr;      // stream of the last call (for synchronisation)
 
   bldtt::Tree tt, st;                 // target and source trees
@@ -138,12 +177,20 @@ struct bldtt_plan {
   // Work items of the interaction kernel, sorted by decreasing cost.
   int4* items = nullptr;              // {cluster, row_begin, row_count, kind}
   int32_t nitems = 0;
-  int32_t* item_counter = nullptr;
+  int32_t* item_counter = nullptr;    // one per segment
   double executed_evaluations = 0.0;
-  int interact_grid = 0;
-  int interact_threads = 0;
-  int interact_layout = 0;            // consumer layout: 0 = 4 warps x 2 targets, 1 = 2 warps x 4
-  float4* chunk_frame = nullptr;      // [pool chunks]: FP32 frame centre, real entries (int bits)
+  // Items are grouped by the kernel of their problem; each group is one
+  // persistent launch of the interaction kernel specialised for that kernel.
+  struct Segment {
+    int kernel;                       // BLDTT_COULOMB, ...
+    int32_t first, count;             // items [first, first + count)
+    int layout, grid, threads;        // consumer layout and launch shape
+  };
+  std::vector<Segment> segments;
+  int interact_layout = 0;            // requested layout: 0 = 4 warps x 2 targets, 1 = 2 x 4, 2 = 4 x 2 at 8 CTAs/SM
+  float4* chunk_frame = nullptr;      // [pool chunks][kChunkInfo]: frame centre + count, extents + tau
+  float4* item_box = nullptr;         // FP32_BULK: [items][kItemGroups][2] target group boxes (lo, hi)
+  float* pool_res = nullptr;          // FP32_BULK: frame residuals of the pool's particles (pair records)
 
   // Compute-phase arrays.
   double* qhat = nullptr;             // [Cs][np] proxy charges
@@ -156,6 +203,10 @@ struct bldtt_plan {
   float ms_tree = 0.f, ms_lists = 0.f;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   bool have_compute_events = false;
+
+  // Captured compute phase (bldtt_compute_graph).
+  cudaGraphExec_t graph_exec = nullptr;
+  double* graph_phi = nullptr;
 };
 
 namespace bldtt {
@@ -176,8 +227,9 @@ int bbox_reduce(const double* x, const double* y, const double* z, int64_t n, do
 int check_finite(const double* v, int64_t n, int* bad_dev, cudaStream_t s, Counters& c);
 
 // ---- trees (tree.cu) ----
-int build_tree(Tree& T, const double* coords_user, int32_t n, int32_t max_leaf, int degree,
-               int* bad_dev, cudaStream_t s, Counters& c);
+// roots: host offsets (nroots + 1 entries) of the problems' particle ranges.
+int build_tree(Tree& T, const double* coords_user, int32_t n, const std::vector<int32_t>& roots,
+               int32_t max_leaf, int degree, int* bad_dev, cudaStream_t s, Counters& c);
 // Reorder the particles inside every leaf along a Morton curve of the leaf's box.
 int morton_order_leaves(Tree& T, cudaStream_t s, Counters& c);
 void free_tree(Tree& T, cudaStream_t s);
@@ -195,7 +247,9 @@ int downward_pass(bldtt_plan* p, double* phi_user, cudaStream_t s);
 int configure_pass_kernels();
 
 // ---- interactions (interact.cu) ----
-int interaction_grid(bldtt_plan* p, int* grid);
+int layouts_available(int kernel, int* out);
+int interaction_grids(bldtt_plan* p);                 // launch shape of every segment
+int run_segment(bldtt_plan* p, int seg, cudaStream_t s);
 int run_interactions(bldtt_plan* p, cudaStream_t s);
 
 // ---- direct sum (direct.cu) ----

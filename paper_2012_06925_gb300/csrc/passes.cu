@@ -229,20 +229,20 @@ int upward_pass(bldtt_plan* p, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Source pool: leaf particles then proxy points, each block padded to kChunk
 // ---------------------------------------------------------------------------
-// FP32_BULK pool entries are relative to the frame centre c (a float) of their
-// chunk of kChunk entries: with the split v = hi + lo (hi = fl(v),
-// lo = fl(v - hi)) the entry is fl(fl(hi - c) + lo); the interaction kernel
-// moves its targets into each chunk's frame with the same expression.  A
-// chunk is stored as 32 pair records {x0,x1, y0,y1, z0,z1, q0,q1}.
+// FP32_BULK pool entries are the frame coordinates (frame_main) of their
+// point relative to the frame centre c (a float) of their chunk of kChunk
+// entries; the interaction kernel moves its targets into each chunk's frame
+// with the same expression.  A chunk is stored as 32 pair records
+// {x0,x1, y0,y1, z0,z1, q0,q1}.
 __device__ __forceinline__ float frame_coord(double v, float c) {
-  float vh = (float)v;
-  float vl = (float)(v - (double)vh);
-  return __fadd_rn(__fsub_rn(vh, c), vl);
+  float hi, lo;
+  split_f64(v, hi, lo);
+  return frame_main(hi, lo, c);
 }
 
 __device__ __forceinline__ void put(float4* pool, const float4* frame, int64_t i, double x, double y,
                                     double z, double q) {
-  const float4 f = frame[i / kChunk];
+  const float4 f = frame[kChunkInfo * (i / kChunk)];
   const int64_t j = i % kChunk;
   float* r = reinterpret_cast<float*>(pool) + ((i / kChunk) * (kChunk / 2) + j / 2) * 8 + (j & 1);
   r[0] = frame_coord(x, f.x);
@@ -307,11 +307,31 @@ int build_pool(bldtt_plan* p, cudaStream_t s) {
   return BLDTT_OK;
 }
 
-// Frame of every pool chunk: a float centre (the rounded centre of the chunk's
-// bounding box for particles; the rounded cluster centre for proxies) and the
-// number of real entries (bit-cast into .w).
-__device__ __forceinline__ void store_frame(float4* frame, int64_t q, const double* c, int count) {
-  frame[q] = make_float4((float)c[0], (float)c[1], (float)c[2], __int_as_float(count));
+// Description of every pool chunk (kChunkInfo float4 per chunk):
+//  [0] frame centre c (floats: the rounded centre of the chunk's bounding box
+//      for particles, the rounded cluster centre for proxies), real entries;
+//  [1] half-extents e of the chunk's entries around c (rounded up) and the
+//      near distance tau = 0.3 |e| (particle chunks; -inf for proxy chunks).
+// A target whose frame coordinates x'' satisfy max_d (|x''_d| - e_d) >= tau is
+// at distance r >= tau from every entry, so the FP32 rounding of the two frame
+// coordinates (at most u |x''| and u |e|, |x''| <= r + |e|) changes r by at
+// most sqrt(3) u (1 + 2|e|/tau) r < 14 u r.  Nearer targets add the frame
+// residuals of both points (the interaction kernel's careful path), which
+// restores a relative error of a few u at any r > 0.  Proxy chunks need no
+// such path: the MAC keeps every target at r > (1 - theta) R from them.
+__device__ __forceinline__ void store_chunk(float4* info, int64_t q, const double* c, const double* e,
+                                            int count, bool particles) {
+  float cf[3], ef[3];
+  double e2 = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    cf[d] = (float)c[d];
+    double ed = e[d] + fabs(c[d] - (double)cf[d]);
+    ef[d] = __double2float_ru(ed);
+    e2 += (double)ef[d] * (double)ef[d];
+  }
+  const float tau = particles ? __double2float_ru(0.3 * sqrt(e2)) : -INFINITY;
+  info[kChunkInfo * q] = make_float4(cf[0], cf[1], cf[2], __int_as_float(count));
+  info[kChunkInfo * q + 1] = make_float4(ef[0], ef[1], ef[2], tau);
 }
 
 __global__ void k_frames_particles(int32_t nleaves, const int32_t* __restrict__ leaf_ids,
@@ -346,27 +366,57 @@ __global__ void k_frames_particles(int32_t nleaves, const int32_t* __restrict__ 
       mx[d] = fmax(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], off));
     }
   if (lane == 0) {
-    double c3[3];
-    for (int d = 0; d < 3; ++d) c3[d] = b < e ? 0.5 * (mn[d] + mx[d]) : 0.0;
-    store_frame(frame, q, c3, (int)(e > b ? e - b : 0));
+    double c3[3], e3[3];
+    for (int d = 0; d < 3; ++d) {
+      c3[d] = b < e ? 0.5 * (mn[d] + mx[d]) : 0.0;
+      e3[d] = b < e ? 0.5 * (mx[d] - mn[d]) : 0.0;
+    }
+    store_chunk(frame, q, c3, e3, (int)(e > b ? e - b : 0), true);
   }
 }
 
 __global__ void k_frames_proxies(int32_t nclusters, int64_t first_chunk, int32_t chunks_per_cluster,
                                  int32_t np, const double* __restrict__ center,
-                                 float4* __restrict__ frame) {
+                                 const double* __restrict__ box, float4* __restrict__ frame) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)nclusters * chunks_per_cluster) return;
   const int64_t c = t / chunks_per_cluster;
   const int k = (int)(t % chunks_per_cluster);
-  store_frame(frame, first_chunk + t, center + c * 3, min(kChunk, np - k * kChunk));
+  double e3[3];
+  for (int d = 0; d < 3; ++d) e3[d] = 0.5 * (box[c * 6 + 3 + d] - box[c * 6 + d]);
+  store_chunk(frame, first_chunk + t, center + c * 3, e3, min(kChunk, np - k * kChunk), false);
+}
+
+// Frame residuals of the pool's particles, in the pool's pair-record layout
+// (x0,x1, y0,y1, z0,z1, unused): read only by the careful path.
+__global__ void k_pool_residuals(const int32_t* __restrict__ leaf_ids, const int32_t* __restrict__ begin,
+                                 const int32_t* __restrict__ end, const int32_t* __restrict__ pad_prefix,
+                                 const float4* __restrict__ frame, const double* __restrict__ x,
+                                 const double* __restrict__ y, const double* __restrict__ z,
+                                 float* __restrict__ res) {
+  const int lf = blockIdx.x;
+  const int c = leaf_ids[lf];
+  const int64_t o = pad_prefix[lf];
+  for (int32_t i = begin[c] + threadIdx.x; i < end[c]; i += blockDim.x) {
+    const int64_t k = o + (i - begin[c]);
+    const float4 f = frame[kChunkInfo * (k / kChunk)];
+    const int64_t j = k % kChunk;
+    float* r = res + ((k / kChunk) * (kChunk / 2) + j / 2) * 8 + (j & 1);
+    const double v[3] = {x[i], y[i], z[i]};
+    const float cf[3] = {f.x, f.y, f.z};
+    for (int d = 0; d < 3; ++d) {
+      float hi, lo;
+      split_f64(v[d], hi, lo);
+      r[2 * d] = frame_resid(hi, lo, cf[d]);
+    }
+  }
 }
 
 int build_chunk_frames(bldtt_plan* p, cudaStream_t s) {
   Counters& cnt = p->setup_counter;
   const Tree& T = p->st;
   const int64_t nchunks = p->pool_len / kChunk;
-  BL_TRY(dalloc_n(&p->chunk_frame, (size_t)nchunks, s));
+  BL_TRY(dalloc_n(&p->chunk_frame, (size_t)nchunks * kChunkInfo, s));
   const int64_t pchunks = p->pool_particles / kChunk;
   if (pchunks > 0) {
     k_frames_particles<<<nblk(pchunks, 4), 128, 0, s>>>(T.nleaves, T.leaf_ids, T.begin, T.end,
@@ -375,9 +425,16 @@ int build_chunk_frames(bldtt_plan* p, cudaStream_t s) {
   }
   const int32_t cpc = p->np_pad / kChunk;
   k_frames_proxies<<<nblk((int64_t)T.nclusters * cpc, 256), 256, 0, s>>>(T.nclusters, pchunks, cpc,
-                                                                          p->np, T.center,
+                                                                          p->np, T.center, T.box,
                                                                           p->chunk_frame);
   BL_LAUNCHED(cnt.launches);
+  if (p->precision == BLDTT_FP32_BULK && pchunks > 0) {
+    BL_TRY(dalloc_n(&p->pool_res, (size_t)p->pool_particles * 4, s));
+    BL_CUDA(cudaMemsetAsync(p->pool_res, 0, (size_t)p->pool_particles * 4 * sizeof(float), s));
+    k_pool_residuals<<<T.nleaves, 256, 0, s>>>(T.leaf_ids, T.begin, T.end, p->pad_prefix,
+                                               p->chunk_frame, T.x, T.y, T.z, p->pool_res);
+    BL_LAUNCHED(cnt.launches);
+  }
   return BLDTT_OK;
 }
 

@@ -9,6 +9,11 @@
 // box of its particles.  All geometric decisions are made in FP64 with
 // explicitly rounded operations (no FMA contraction) so that they are the
 // decisions a plain FP64 evaluation of the same expressions makes.
+//
+// The build works on a forest: level 0 holds one root per problem (a
+// contiguous range of the particle array), and every level is processed for
+// all problems at once, so a batch of independent problems costs one set of
+// launches per level.
 #include <algorithm>
 #include <utility>
 
@@ -38,12 +43,18 @@ __global__ void k_tree_init(const double* __restrict__ coords, int32_t n, double
   perm[i] = (int32_t)i;
 }
 
-__global__ void k_tree_root(int32_t n, int32_t* begin, int32_t* end, int32_t* parent,
-                            int32_t* level) {
-  begin[0] = 0;
-  end[0] = n;
-  parent[0] = -1;
-  level[0] = 0;
+// One root per problem: cluster p holds particles [offsets[p], offsets[p+1]).
+__global__ void k_tree_roots(int32_t nroots, const int32_t* __restrict__ offsets,
+                             int32_t* __restrict__ begin, int32_t* __restrict__ end,
+                             int32_t* __restrict__ parent, int32_t* __restrict__ level,
+                             int32_t* __restrict__ problem) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nroots) return;
+  begin[p] = offsets[p];
+  end[p] = offsets[p + 1];
+  parent[p] = -1;
+  level[p] = 0;
+  problem[p] = p;
 }
 
 // Split decision of each cluster of the level (reading: leaf iff |C| <= M0 or
@@ -220,7 +231,7 @@ __global__ void k_tree_children(int32_t nl, int32_t ls, int32_t le, int32_t lvl,
                                 const int32_t* __restrict__ child_cnt, int32_t* __restrict__ begin,
                                 int32_t* __restrict__ end, int32_t* __restrict__ parent,
                                 int32_t* __restrict__ level, int32_t* __restrict__ first_child,
-                                int32_t* __restrict__ nchild) {
+                                int32_t* __restrict__ nchild, int32_t* __restrict__ problem) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nl || !splitmask[j]) return;
   int c = ls + j;
@@ -235,6 +246,7 @@ __global__ void k_tree_children(int32_t nl, int32_t ls, int32_t le, int32_t lvl,
     end[id] = pos + cnt;
     parent[id] = c;
     level[id] = lvl + 1;
+    problem[id] = problem[c];
     pos += cnt;
   }
   first_child[c] = fc;
@@ -392,7 +404,8 @@ static int grow_clusters(Tree& T, size_t need, size_t keep, cudaStream_t s) {
   if (need <= T.cap && T.begin) return BLDTT_OK;
   size_t ncap = T.cap ? T.cap : 64;
   while (ncap < need) ncap *= 2;
-  int32_t** iarr[6] = {&T.begin, &T.end, &T.parent, &T.first_child, &T.nchild, &T.level};
+  int32_t** iarr[7] = {&T.begin, &T.end, &T.parent, &T.first_child, &T.nchild, &T.level,
+                       &T.problem};
   for (auto a : iarr) {
     size_t c = T.cap;
     BL_TRY(dgrow(a, &c, ncap, keep, s));
@@ -405,8 +418,8 @@ static int grow_clusters(Tree& T, size_t need, size_t keep, cudaStream_t s) {
 
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-int build_tree(Tree& T, const double* coords, int32_t n, int32_t max_leaf, int degree,
-               int* bad_dev, cudaStream_t s, Counters& cnt) {
+int build_tree(Tree& T, const double* coords, int32_t n, const std::vector<int32_t>& roots,
+               int32_t max_leaf, int degree, int* bad_dev, cudaStream_t s, Counters& cnt) {
   T.n = n;
   double *x2 = nullptr, *y2 = nullptr, *z2 = nullptr;
   int32_t* perm2 = nullptr;
@@ -422,12 +435,35 @@ int build_tree(Tree& T, const double* coords, int32_t n, int32_t max_leaf, int d
   BL_TRY(dalloc_n(&code, n, s));
   k_tree_init<<<nblk(n, 256), 256, 0, s>>>(coords, n, T.x, T.y, T.z, T.perm);
   BL_LAUNCHED(cnt.launches);
-  BL_TRY(grow_clusters(T, 1024, 0, s));
-  k_tree_root<<<1, 1, 0, s>>>(n, T.begin, T.end, T.parent, T.level);
-  BL_LAUNCHED(cnt.launches);
-  BL_TRY(bbox_reduce(T.x, T.y, T.z, n, T.box, bad_dev, s, cnt));
+  const int32_t nroots = (int32_t)roots.size() - 1;
+  BL_TRY(grow_clusters(T, std::max<size_t>(1024, 2 * (size_t)nroots), 0, s));
+  {
+    int32_t* d_roots = nullptr;
+    BL_TRY(dalloc_n(&d_roots, roots.size(), s));
+    BL_CUDA(cudaMemcpyAsync(d_roots, roots.data(), roots.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, s));
+    k_tree_roots<<<nblk(nroots, 128), 128, 0, s>>>(nroots, d_roots, T.begin, T.end, T.parent,
+                                                   T.level, T.problem);
+    BL_LAUNCHED(cnt.launches);
+    BL_TRY(check_finite(T.x, n, bad_dev, s, cnt));
+    BL_TRY(check_finite(T.y, n, bad_dev, s, cnt));
+    BL_TRY(check_finite(T.z, n, bad_dev, s, cnt));
+    // root boxes: the minimal bounding box of each problem's particles (Sec. 2.3)
+    int64_t per = (int64_t)n / nroots;
+    int slices = (int)std::min<int64_t>(32, std::max<int64_t>(1, per / 16384));
+    double* part = nullptr;
+    BL_TRY(dalloc_n(&part, (size_t)nroots * slices * 6, s));
+    k_tree_child_bbox<<<dim3(nroots, slices), kTreeThreads, 0, s>>>(0, T.begin, T.end, T.x, T.y,
+                                                                    T.z, part);
+    BL_LAUNCHED(cnt.launches);
+    k_tree_child_bbox_combine<<<nblk(nroots, 4), 128, 0, s>>>(0, nroots, slices, part, T.box);
+    BL_LAUNCHED(cnt.launches);
+    dfree(part, s);
+    dfree(d_roots, s);
+  }
 
-  T.level_start.assign({0, 1});
+  T.level_start.assign({0, nroots});
+  T.nroots = nroots;
   for (int lvl = 0;; ++lvl) {
     int32_t ls = T.level_start[lvl], le = T.level_start[lvl + 1], nl = le - ls;
     uint8_t* splitmask = nullptr;
@@ -469,7 +505,7 @@ int build_tree(Tree& T, const double* coords, int32_t n, int32_t max_leaf, int d
     BL_TRY(grow_clusters(T, (size_t)le + nc, (size_t)le, s));
     k_tree_children<<<nblk(nl, 128), 128, 0, s>>>(nl, ls, le, lvl, splitmask, child_off, child_cnt,
                                                   T.begin, T.end, T.parent, T.level, T.first_child,
-                                                  T.nchild);
+                                                  T.nchild, T.problem);
     BL_LAUNCHED(cnt.launches);
     BL_CUDA(cudaMemcpyAsync(x2, T.x, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
     BL_CUDA(cudaMemcpyAsync(y2, T.y, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
@@ -641,6 +677,7 @@ void free_tree(Tree& T, cudaStream_t s) {
   dfree_ptr(T.x, s); dfree_ptr(T.y, s); dfree_ptr(T.z, s); dfree_ptr(T.perm, s);
   dfree_ptr(T.begin, s); dfree_ptr(T.end, s); dfree_ptr(T.parent, s);
   dfree_ptr(T.first_child, s); dfree_ptr(T.nchild, s); dfree_ptr(T.level, s);
+  dfree_ptr(T.problem, s);
   dfree_ptr(T.box, s); dfree_ptr(T.center, s); dfree_ptr(T.radius, s); dfree_ptr(T.nodes, s);
   dfree_ptr(T.leaf_ids, s); dfree_ptr(T.leaf_first, s); dfree_ptr(T.leaf_last, s);
   T.cap = 0;

@@ -68,8 +68,8 @@ def max_rel(ref, got):
 
 
 def same_leaf_members(gtree: dict, otree: O.Tree) -> bool:
-    """The GPU orders particles inside each source leaf along a Morton curve;
-    the leaf memberships (sets) must still equal the oracle's."""
+    """The GPU orders the particles inside each leaf along a Morton curve; the
+    leaf memberships (sets) must still equal the oracle's."""
     gperm, operm = gtree["perm"], otree.perm
     for c in otree.leaves():
         b, e = otree.begin[c], otree.end[c]

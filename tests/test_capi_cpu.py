@@ -95,3 +95,20 @@ def test_setup_ex_rejects_bad_variant_and_params(lib):
         assert lib.bldtt_setup_ex(ctypes.byref(h), DUMMY, 100, DUMMY, 100, DUMMY,
                                   ctypes.byref(prm), None) == 1
     assert not h
+
+
+def test_setup_batch_rejects_bad_batches(lib):
+    h = ctypes.c_void_p()
+    prm = B.Params(0, 0.0, 4, 0.7, 10, 10, 1, 0)
+    I64 = ctypes.c_int64 * 3
+    ks = (ctypes.c_int * 2)(0, 1)
+    kp = (ctypes.c_double * 2)(0.0, 0.5)
+    def call(nprob, to, so, kernels=ks, kappas=kp):
+        return lib.bldtt_setup_batch(ctypes.byref(h), nprob, DUMMY, to, DUMMY, so, DUMMY,
+                                     kernels, kappas, ctypes.byref(prm), None)
+    assert call(0, I64(0, 5, 9), I64(0, 5, 9)) == 1                    # no problems
+    assert call(2, I64(1, 5, 9), I64(0, 5, 9)) == 1                    # offsets not from 0
+    assert call(2, I64(0, 5, 5), I64(0, 5, 9)) == 1                    # empty problem
+    assert call(2, I64(0, 5, 9), I64(0, 5, 9), kernels=(ctypes.c_int * 2)(0, 7)) == 1
+    assert call(2, I64(0, 5, 9), I64(0, 5, 9), kappas=(ctypes.c_double * 2)(0.0, -1.0)) == 1
+    assert not h
