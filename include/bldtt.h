@@ -185,6 +185,107 @@ int bldtt_setup_batch(bldtt_plan** plan, int nprob,
                       const bldtt_params_t* params, void* cuda_stream);
 
 /*
+ * Learned pair selector (no counterpart in the paper: the paper fixes one
+ * degree n and the MAC r_t + r_s < theta R of Alg. 2).  A network of three
+ * hidden ReLU layers of 64 reads six features of a pair (C_t, C_s) with
+ * R = |c_t - c_s| > 0 and (r_t + r_s)/R < 1:
+ *   plog2(|C_t|)/16, plog2(|C_s|)/16, r_t/R, r_s/R, (r_t + r_s)/R, kappa R/(1 + kappa R)
+ * (plog2(m) = e + (f - 1) for m = f 2^e, 1 <= f < 2; radii are half box
+ * diagonals) and predicts, for each degree degrees[i], the log10 of the
+ * relative l2 error of PC, CP and CC (Eqs. (8), (12), (15)) on the pair:
+ * output 3 i + t, t = 0 PC, 1 CP, 2 CC.  The traversal takes the cheapest
+ * option predicted at or below log10_budget (cost PC |C_t| n_p(d), CP
+ * n_p(d) |C_s|, CC n_p(d)^2), or PP when |C_t||C_s| costs no more; with no
+ * feasible option it descends as Alg. 2 does for a pair that fails the MAC.
+ * Pairs whose features fall outside [feature_lo, feature_hi] are decided by
+ * the MAC of Alg. 2 (params theta) at the highest degree.
+ *
+ * Arithmetic (identical on every device): features in FP64, rounded to
+ * float and to bfloat16 (round to nearest even); bf16 weights; each neuron
+ * z_j = b_j + sum_k w_jk a_k summed in float in increasing k (bf16 products
+ * are exact in float); a_j = bf16(max(z_j, 0)); float biases.
+ *
+ * weights: host float32 master weights, rows = outputs, packed
+ *   W1[64][6] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] W4[3m][64] b4[3m]
+ *   (m = num_degrees; bldtt_selector_param_count gives the length), or NULL:
+ *   then every pair is decided by the MAC at the highest degree.
+ */
+typedef struct bldtt_selector {
+    int num_degrees;                /* 1..8 */
+    int degrees[8];                 /* strictly increasing, 1..16; the highest = params n */
+    const float* weights;           /* host, see above, or NULL */
+    float feature_lo[6], feature_hi[6];
+    float log10_budget;             /* per-pair budget, log10 of the relative error */
+} bldtt_selector_t;
+
+/* Number of float32 master weights of a selector with num_degrees degrees
+ * (-1 if num_degrees is outside 1..8). */
+int64_t bldtt_selector_param_count(int num_degrees);
+
+/*
+ * bldtt_setup_learned - bldtt_setup_ex with the learned selector in place of
+ * the MAC.  The plan carries proxies of every degree of sel (the proxy
+ * charges of a lower degree d come from those of the highest n by the exact
+ * transfer A(x)A(x)A, A[k][k'] = L^(d)_k(s^(n)_k'); proxy potentials of
+ * degree d go back to the degree-n grid by its transpose before Eq. (20)).
+ * Interaction lists are then classes: 0 = PP, 1 + 3 i + t = (PC, CP, CC)[t]
+ * at degree degrees[i] (bldtt_list_classes, bldtt_export_lists).  Arguments,
+ * ownership and errors as bldtt_setup_ex; EINVAL also for a bad selector
+ * (degree count or order, highest degree != params n, empty feature box,
+ * non-finite budget or weight).  The selector is copied; the caller keeps it.
+ */
+int bldtt_setup_learned(bldtt_plan** plan, const double* targets, int64_t M,
+                        const double* sources, int64_t N, const double* charges,
+                        const bldtt_params_t* params, const bldtt_selector_t* sel,
+                        void* cuda_stream);
+
+/* Interaction-list classes of a plan: *num_classes = 1 + 3 * num_degrees,
+ * degrees (capacity 8, may be NULL) receives the plan's degrees. */
+int bldtt_list_classes(bldtt_plan* plan, int* num_classes, int* degrees, int* num_degrees);
+
+/*
+ * Training of the selector network (device buffers throughout, asynchronous
+ * on cuda_stream).  params: the packed float32 master weights; x: [batch][6]
+ * float32 features (rounded to bf16 inside, as in the selector); y, target,
+ * mask: [batch][num_out]; num_out = 3 * num_degrees <= 24.
+ *  bldtt_mlp_forward:   y = network(x) with the selector's arithmetic.
+ *  bldtt_mlp_gradients: loss = sum mask (y - target)^2 / max(1, sum mask)
+ *                       (written to *loss, device, if non-NULL) and its
+ *                       gradient for every master weight (grads, same
+ *                       layout as params), ReLU' = [z > 0], the bf16
+ *                       rounding of weights and activations passed through;
+ *                       sums over the batch in float in increasing order.
+ *  bldtt_mlp_adam:      one Adam step (beta 0.9, 0.999, eps 1e-8; step >= 1
+ *                       counts from 1) on count weights with moments m, v.
+ * Errors: EINVAL (NULL pointers, sizes), ENOMEM, ECUDA.
+ */
+int bldtt_mlp_forward(const float* params, int num_out, const float* x, int64_t batch, float* y,
+                      void* cuda_stream);
+int bldtt_mlp_gradients(const float* params, int num_out, const float* x, const float* target,
+                        const float* mask, int64_t batch, float* grads, float* loss,
+                        void* cuda_stream);
+int bldtt_mlp_adam(float* params, float* m, float* v, const float* grads, int64_t count, int step,
+                   float lr, void* cuda_stream);
+
+/*
+ * Training data from a plan's trees (cluster ids as bldtt_export_tree
+ * numbers them; pairs: device int32 [npairs][2] = (target cluster, source
+ * cluster)).
+ *  bldtt_pair_features: the selector's six FP64 features per pair into
+ *    features (device [npairs][6]); NaN for pairs that cannot be approximated.
+ *  bldtt_pair_errors: in FP64, the relative l2 error of PC, CP and CC at each
+ *    degree against the exact pair sum of Eq. (6) (the plan's kernel and
+ *    charges), on min(samples, |C_t|) targets spread evenly over C_t:
+ *    err (device [npairs][num_degrees][3]).  samples <= 256, degrees in
+ *    1..16 (host array of num_degrees <= 8).
+ * Errors: EINVAL, ECUDA.
+ */
+int bldtt_pair_features(bldtt_plan* plan, int64_t npairs, const int32_t* pairs, double* features,
+                        void* cuda_stream);
+int bldtt_pair_errors(bldtt_plan* plan, int64_t npairs, const int32_t* pairs, int samples,
+                      int num_degrees, const int* degrees, double* err, void* cuda_stream);
+
+/*
  * bldtt_set_charges - replace the source charges of a plan (device, N
  * float64, input order).  Trees and interaction lists depend only on the
  * positions and parameters and are reused.  Errors: EINVAL (NULL arguments,
@@ -265,9 +366,10 @@ int bldtt_export_tree(bldtt_plan* plan, int which, int32_t* perm, int32_t* begin
                       double* lo, double* hi, int32_t* parent, int32_t* level);
 
 /*
- * bldtt_export_lists - copy the entries of one interaction list type
- * (enum bldtt_interaction) as (target cluster, source cluster) pairs, sorted
- * by target cluster.  count is in/out: capacity on entry, entries on return
+ * bldtt_export_lists - copy the entries of one interaction-list class as
+ * (target cluster, source cluster) pairs, sorted by target cluster.  For a
+ * plan of one degree the classes are the types (enum bldtt_interaction);
+ * see bldtt_setup_learned for plans of several degrees.  count is in/out: capacity on entry, entries on return
  * (EINVAL, with the needed count, if the capacity is too small).
  */
 int bldtt_export_lists(bldtt_plan* plan, int type, int32_t* target, int32_t* source,

@@ -27,7 +27,9 @@ EXPORTED = (
     "bldtt_destroy", "bldtt_status_string", "bldtt_last_error", "bldtt_tree_size",
     "bldtt_export_tree", "bldtt_export_lists", "bldtt_export_proxy_charges",
     "bldtt_export_proxy_potentials", "bldtt_direct_sum", "bldtt_solve_host",
-    "bldtt_bounding_box_noalloc",
+    "bldtt_bounding_box_noalloc", "bldtt_selector_param_count", "bldtt_setup_learned",
+    "bldtt_list_classes", "bldtt_mlp_forward", "bldtt_mlp_gradients", "bldtt_mlp_adam",
+    "bldtt_pair_features", "bldtt_pair_errors",
 )
 
 
@@ -35,6 +37,13 @@ class BLDTTError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
         super().__init__(what)
+
+
+class SelectorStruct(ctypes.Structure):
+    _fields_ = [("num_degrees", ctypes.c_int), ("degrees", ctypes.c_int * 8),
+                ("weights", ctypes.POINTER(ctypes.c_float)),
+                ("feature_lo", ctypes.c_float * 6), ("feature_hi", ctypes.c_float * 6),
+                ("log10_budget", ctypes.c_float)]
 
 
 class Params(ctypes.Structure):
@@ -106,6 +115,16 @@ def load_library(path: str = LIB_PATH):
         "bldtt_solve_host": (i32, [P_dbl, i64, P_dbl, i64, P_dbl, i32, dbl, i32, dbl, i32, i32,
                                    i32, P_dbl, ctypes.POINTER(Stats)]),
         "bldtt_bounding_box_noalloc": (i32, [vp, i64, vp, vp, vp]),
+        "bldtt_selector_param_count": (i64, [i32]),
+        "bldtt_setup_learned": (i32, [ctypes.POINTER(vp), vp, i64, vp, i64, vp, ctypes.POINTER(Params),
+                                      ctypes.POINTER(SelectorStruct), vp]),
+        "bldtt_list_classes": (i32, [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int)]),
+        "bldtt_mlp_forward": (i32, [vp, i32, vp, i64, vp, vp]),
+        "bldtt_mlp_gradients": (i32, [vp, i32, vp, vp, vp, i64, vp, vp, vp]),
+        "bldtt_mlp_adam": (i32, [vp, vp, vp, vp, i64, i32, ctypes.c_float, vp]),
+        "bldtt_pair_features": (i32, [vp, i64, vp, vp, vp]),
+        "bldtt_pair_errors": (i32, [vp, i64, vp, i32, i32, ctypes.POINTER(ctypes.c_int), vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -175,6 +194,29 @@ class Plan:
         if not self._h:
             raise RuntimeError("plan already destroyed")
         return self._h
+
+    @classmethod
+    def learned(cls, targets, sources, charges, selector, kernel=COULOMB, kappa=0.0, theta=0.7,
+                N0=2000, M0=2000, precision=FP32_BULK, variant=VARIANT_FULL, stream=None):
+        """A plan whose traversal asks the learned selector (bldtt_setup_learned).
+        selector: a Selector (degrees, float32 master weights or None, feature
+        box, log10 budget)."""
+        lib = load_library()
+        self = cls.__new__(cls)
+        self.M = int(targets.shape[1])
+        self.N = int(sources.shape[1])
+        self.n = int(selector.degrees[-1])
+        self.P = self.n + 1
+        self.np = self.P ** 3
+        self._h = ctypes.c_void_p()
+        prm = Params(int(kernel), float(kappa), self.n, float(theta), int(N0), int(M0),
+                     int(precision), int(variant))
+        st, keep = selector.as_struct()
+        _check(lib.bldtt_setup_learned(ctypes.byref(self._h), _dptr(targets), self.M, _dptr(sources),
+                                       self.N, _dptr(charges, self.N), ctypes.byref(prm),
+                                       ctypes.byref(st), _stream_ptr(stream)))
+        del keep
+        return self
 
     @classmethod
     def batch(cls, targets, target_offsets, sources, source_offsets, charges, kernels, kappas,
@@ -259,11 +301,21 @@ class Plan:
         return dict(perm=perm, begin=begin, end=end, lo=lo.reshape(3, C), hi=hi.reshape(3, C),
                     parent=parent, level=level, levels=nl.value)
 
-    def export_lists(self):
-        """Four (target, source) int32 array pairs: PP, PC, CP, CC."""
+    def list_classes(self):
+        """(number of list classes, degrees of the plan)."""
+        nc, nd = ctypes.c_int(), ctypes.c_int()
+        deg = (ctypes.c_int * 8)()
+        _check(load_library().bldtt_list_classes(self._handle(), ctypes.byref(nc), deg,
+                                                 ctypes.byref(nd)))
+        return nc.value, [deg[i] for i in range(nd.value)]
+
+    def export_lists(self, classes=None):
+        """(target, source) int32 array pairs per list class: PP, PC, CP, CC for a
+        plan of one degree; 0 = PP, 1 + 3 i + (PC, CP, CC) at degree i otherwise."""
         lib = load_library()
         out = []
-        for typ in range(4):
+        nclass = self.list_classes()[0] if classes is None else classes
+        for typ in range(nclass):
             cnt = ctypes.c_int64(0)
             st = lib.bldtt_export_lists(self._handle(), typ, None, None, ctypes.byref(cnt))
             if st != 0 and cnt.value == 0:
@@ -307,6 +359,105 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class Selector:
+    """Learned pair selector of bldtt_setup_learned: degrees, float32 master
+    weights (packed as bldtt_selector_param_count describes) or None for the
+    MAC everywhere, the feature box and the per-pair log10 budget."""
+
+    def __init__(self, degrees, weights=None, lo=None, hi=None, log10_budget=-6.0):
+        self.degrees = [int(d) for d in degrees]
+        self.weights = None if weights is None else np.ascontiguousarray(weights, dtype=np.float32)
+        self.lo = np.full(6, -np.inf, np.float32) if lo is None else np.asarray(lo, np.float32)
+        self.hi = np.full(6, np.inf, np.float32) if hi is None else np.asarray(hi, np.float32)
+        self.log10_budget = float(log10_budget)
+        if self.weights is not None and self.weights.size != param_count(len(self.degrees)):
+            raise ValueError("selector weights have the wrong length")
+
+    def as_struct(self):
+        st = SelectorStruct()
+        st.num_degrees = len(self.degrees)
+        for i, d in enumerate(self.degrees):
+            st.degrees[i] = d
+        keep = None
+        if self.weights is not None:
+            keep = self.weights
+            st.weights = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        for i in range(6):
+            st.feature_lo[i] = float(max(self.lo[i], -3.0e38))
+            st.feature_hi[i] = float(min(self.hi[i], 3.0e38))
+        st.log10_budget = self.log10_budget
+        return st, keep
+
+
+def param_count(num_degrees: int) -> int:
+    return int(load_library().bldtt_selector_param_count(int(num_degrees)))
+
+
+def _fptr(t, n_expected=None, dtype_name="float32"):
+    import torch
+    dt = {"float32": torch.float32, "float64": torch.float64, "int32": torch.int32}[dtype_name]
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
+        raise TypeError(f"expected a contiguous CUDA {dtype_name} tensor")
+    if n_expected is not None and t.numel() != n_expected:
+        raise ValueError(f"expected {n_expected} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def mlp_forward(params, num_out, x, y=None, stream=None):
+    """Selector network outputs for x (CUDA float32 [batch, 6])."""
+    import torch
+    B = int(x.shape[0])
+    if y is None:
+        y = torch.empty(B, num_out, dtype=torch.float32, device="cuda")
+    _check(load_library().bldtt_mlp_forward(_fptr(params), int(num_out), _fptr(x, B * 6), B,
+                                            _fptr(y, B * num_out), _stream_ptr(stream)))
+    return y
+
+
+def mlp_gradients(params, num_out, x, target, mask, grads=None, loss=None, stream=None):
+    """Loss and gradient of the masked squared error (bldtt_mlp_gradients)."""
+    import torch
+    B = int(x.shape[0])
+    if grads is None:
+        grads = torch.empty_like(params)
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    _check(load_library().bldtt_mlp_gradients(_fptr(params), int(num_out), _fptr(x, B * 6),
+                                              _fptr(target, B * num_out), _fptr(mask, B * num_out), B,
+                                              _fptr(grads, params.numel()), _fptr(loss, 1),
+                                              _stream_ptr(stream)))
+    return grads, loss
+
+
+def mlp_adam(params, m, v, grads, step, lr, stream=None):
+    n = params.numel()
+    _check(load_library().bldtt_mlp_adam(_fptr(params, n), _fptr(m, n), _fptr(v, n), _fptr(grads, n),
+                                         n, int(step), float(lr), _stream_ptr(stream)))
+
+
+def pair_features(plan, pairs, stream=None):
+    """FP64 selector features of (target, source) cluster pairs (CUDA int32 [n, 2])."""
+    import torch
+    n = int(pairs.shape[0])
+    out = torch.empty(n, 6, dtype=torch.float64, device="cuda")
+    _check(load_library().bldtt_pair_features(plan._handle(), n, _fptr(pairs, 2 * n, "int32"),
+                                              _fptr(out, 6 * n, "float64"), _stream_ptr(stream)))
+    return out
+
+
+def pair_errors(plan, pairs, degrees, samples=64, stream=None):
+    """FP64 relative errors [n, len(degrees), 3] of PC, CP, CC per pair and degree."""
+    import torch
+    n = int(pairs.shape[0])
+    deg = np.ascontiguousarray(degrees, dtype=np.int32)
+    out = torch.empty(n, len(deg), 3, dtype=torch.float64, device="cuda")
+    _check(load_library().bldtt_pair_errors(plan._handle(), n, _fptr(pairs, 2 * n, "int32"),
+                                            int(samples), len(deg),
+                                            deg.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                            _fptr(out, out.numel(), "float64"), _stream_ptr(stream)))
+    return out
 
 
 def direct_sum(targets, sources, charges, kernel=COULOMB, kappa=0.0, phi=None, stream=None):

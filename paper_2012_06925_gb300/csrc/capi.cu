@@ -91,6 +91,16 @@ void release(bldtt_plan* p) {
   dfree_ptr(p->prob_kernel, s);
   dfree_ptr(p->prob_kappa, s);
   dfree_ptr(p->prob_prm, s);
+  for (int i = 0; i + 1 < p->deg.n; ++i) {   // the highest degree aliases the tree/plan arrays
+    dfree_ptr(p->nodes_t[i], s);
+    dfree_ptr(p->nodes_s[i], s);
+    dfree_ptr(p->qhat_d[i], s);
+    dfree_ptr(p->phit_d[i], s);
+    dfree_ptr(p->xfer[i], s);
+  }
+  dfree(p->sel_w, s);
+  p->sel_w = nullptr;
+  dfree_ptr(p->sel_b, s);
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
   cudaStreamSynchronize(s);
   for (auto& e : p->ev)
@@ -149,12 +159,15 @@ int setup_impl(bldtt_plan* p, const double* targets, const double* sources, cons
     set_error("a target, source or charge value is not finite");
     return BLDTT_EINVAL;
   }
+  BL_TRY(setup_degrees(p, s));
   BL_TRY(build_lists(p, s));
   BL_TRY(build_work_items(p, s));
   const size_t esz = p->precision == BLDTT_FP32_BULK ? sizeof(float4) : sizeof(double4);
   BL_TRY(dalloc(&p->pool, (size_t)p->pool_len * esz, s));
   BL_TRY(dalloc_n(&p->qhat, (size_t)p->st.nclusters * p->np, s));
   BL_TRY(dalloc_n(&p->phit, (size_t)p->tt.nclusters * p->np, s));
+  p->qhat_d[p->deg.n - 1] = p->qhat;
+  p->phit_d[p->deg.n - 1] = p->phit;
   BL_TRY(dalloc_n(&p->phi_near, (size_t)p->M, s));
   BL_TRY(dalloc_n(&p->item_counter, p->segments.size() > 0 ? p->segments.size() : 1, s));
   BL_TRY(build_chunk_frames(p, s));
@@ -215,12 +228,51 @@ const char* bldtt_status_string(int status) {
 
 const char* bldtt_last_error(void) { return bldtt::last_error(); }
 
+// Selector weights: float master weights (W1 b1 W2 b2 W3 b3 W4 b4, rows =
+// outputs) -> bf16 weights (round to nearest even) and float biases.
+static uint16_t host_bf16(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  u = (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+  return (uint16_t)u;
+}
+static int upload_selector(bldtt_plan* p, const float* weights) {
+  const int nout = p->sel_nout;
+  const int in[4] = {kFeatures, kHidden, kHidden, kHidden};
+  const int out[4] = {kHidden, kHidden, kHidden, nout};
+  std::vector<uint16_t> w;
+  std::vector<float> b;
+  size_t o = 0;
+  for (int l = 0; l < 4; ++l) {
+    for (int i = 0; i < in[l] * out[l]; ++i) {
+      if (!std::isfinite(weights[o + i])) {
+        set_error("selector weight %zu is not finite", o + i);
+        return BLDTT_EINVAL;
+      }
+      w.push_back(host_bf16(weights[o + i]));
+    }
+    o += (size_t)in[l] * out[l];
+    for (int i = 0; i < out[l]; ++i) b.push_back(weights[o + i]);
+    o += out[l];
+  }
+  cudaStream_t s = p->stream;
+  uint16_t* dw = nullptr;
+  BL_TRY(dalloc_n(&dw, w.size(), s));
+  p->sel_w = dw;
+  BL_TRY(dalloc_n(&p->sel_b, b.size(), s));
+  BL_CUDA(cudaMemcpyAsync(p->sel_w, w.data(), w.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, s));
+  BL_CUDA(cudaMemcpyAsync(p->sel_b, b.data(), b.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+  BL_CUDA(cudaStreamSynchronize(s));
+  return BLDTT_OK;
+}
+
 // Common set-up of a batch of nprob problems (nprob = 1 for bldtt_setup).
 // t_off / s_off: host offsets (nprob + 1) of each problem's targets / sources.
 static int setup_common(bldtt_plan** plan, const double* targets, const int64_t* t_off,
                         const double* sources, const int64_t* s_off, const double* charges,
                         int nprob, const int* kernels, const double* kappas, int n, double theta,
-                        int N0, int M0, int precision, int variant, void* cuda_stream) {
+                        int N0, int M0, int precision, int variant, const bldtt_selector_t* sel,
+                        void* cuda_stream) {
   if (!plan) {
     set_error("plan out-pointer is NULL");
     return BLDTT_EINVAL;
@@ -248,6 +300,32 @@ static int setup_common(bldtt_plan** plan, const double* targets, const int64_t*
   }
   const int64_t M = t_off[nprob], N = s_off[nprob];
   BL_TRY(validate(M, N, kernels[0], kappas[0], n, theta, N0, M0, precision));
+  if (sel) {
+    if (sel->num_degrees < 1 || sel->num_degrees > kMaxDegrees) {
+      set_error("selector: %d degrees (1..%d allowed)", sel->num_degrees, kMaxDegrees);
+      return BLDTT_EINVAL;
+    }
+    for (int i = 0; i < sel->num_degrees; ++i)
+      if (sel->degrees[i] < 1 || sel->degrees[i] > kMaxDegree ||
+          (i > 0 && sel->degrees[i] <= sel->degrees[i - 1])) {
+        set_error("selector: degrees must increase strictly within [1, %d]", kMaxDegree);
+        return BLDTT_EINVAL;
+      }
+    if (sel->degrees[sel->num_degrees - 1] != n) {
+      set_error("selector: the highest degree (%d) must equal params n (%d)",
+                sel->degrees[sel->num_degrees - 1], n);
+      return BLDTT_EINVAL;
+    }
+    for (int d = 0; d < 6; ++d)
+      if (!(sel->feature_lo[d] <= sel->feature_hi[d])) {
+        set_error("selector: feature box %d is empty or not finite", d);
+        return BLDTT_EINVAL;
+      }
+    if (!std::isfinite(sel->log10_budget)) {
+      set_error("selector: log10_budget is not finite");
+      return BLDTT_EINVAL;
+    }
+  }
   if (variant != BLDTT_VARIANT_FULL && variant != BLDTT_VARIANT_CC_PP_ONLY) {
     set_error("unknown traversal variant %d", variant);
     return BLDTT_EINVAL;
@@ -283,7 +361,27 @@ static int setup_common(bldtt_plan** plan, const double* targets, const int64_t*
   p->M0 = M0;
   p->precision = precision;
   p->stream = static_cast<cudaStream_t>(cuda_stream);
-  int st = setup_impl(p, targets, sources, charges);
+  p->deg.n = sel ? sel->num_degrees : 1;
+  for (int i = 0; i < p->deg.n; ++i) {
+    const int d = sel ? sel->degrees[i] : n;
+    p->deg.d[i] = d;
+    p->deg.np[i] = (d + 1) * (d + 1) * (d + 1);
+    p->deg.np_pad[i] = (p->deg.np[i] + kChunk - 1) / kChunk * kChunk;
+  }
+  p->nclass = 1 + 3 * p->deg.n;
+  int st = BLDTT_OK;
+  if (sel) {
+    p->learned = true;
+    p->selector_net = sel->weights != nullptr;
+    p->sel_nout = 3 * p->deg.n;
+    for (int d = 0; d < 6; ++d) {
+      p->sel_lo[d] = sel->feature_lo[d];
+      p->sel_hi[d] = sel->feature_hi[d];
+    }
+    p->sel_log_eps = sel->log10_budget;
+    if (p->selector_net) st = upload_selector(p, sel->weights);
+  }
+  if (st == BLDTT_OK) st = setup_impl(p, targets, sources, charges);
   if (st != BLDTT_OK) {
     release(p);
     return st;
@@ -301,7 +399,7 @@ int bldtt_setup(bldtt_plan** plan, const double* targets, int64_t M, const doubl
     BL_TRY(validate(M, N, kernel, kappa, n, theta, N0, M0, precision));
   }
   return setup_common(plan, targets, t_off, sources, s_off, charges, 1, &kernel, &kappa, n, theta,
-                      N0, M0, precision, BLDTT_VARIANT_FULL, cuda_stream);
+                      N0, M0, precision, BLDTT_VARIANT_FULL, nullptr, cuda_stream);
 }
 
 int bldtt_setup_ex(bldtt_plan** plan, const double* targets, int64_t M, const double* sources,
@@ -319,7 +417,7 @@ int bldtt_setup_ex(bldtt_plan** plan, const double* targets, int64_t M, const do
                     prm->precision));
   }
   return setup_common(plan, targets, t_off, sources, s_off, charges, 1, &prm->kernel, &prm->kappa,
-                      prm->n, prm->theta, prm->N0, prm->M0, prm->precision, prm->variant,
+                      prm->n, prm->theta, prm->N0, prm->M0, prm->precision, prm->variant, nullptr,
                       cuda_stream);
 }
 
@@ -334,7 +432,38 @@ int bldtt_setup_batch(bldtt_plan** plan, int nprob, const double* targets, const
   }
   return setup_common(plan, targets, target_offsets, sources, source_offsets, charges, nprob,
                       kernels, kappas, prm->n, prm->theta, prm->N0, prm->M0, prm->precision,
-                      prm->variant, cuda_stream);
+                      prm->variant, nullptr, cuda_stream);
+}
+
+int bldtt_setup_learned(bldtt_plan** plan, const double* targets, int64_t M, const double* sources,
+                        int64_t N, const double* charges, const bldtt_params_t* prm,
+                        const bldtt_selector_t* sel, void* cuda_stream) {
+  if (!prm || !sel) {
+    if (plan) *plan = nullptr;
+    set_error("params and selector pointers must be non-NULL");
+    return BLDTT_EINVAL;
+  }
+  const int64_t t_off[2] = {0, M}, s_off[2] = {0, N};
+  if (M < 1 || N < 1) {
+    if (plan) *plan = nullptr;
+    BL_TRY(validate(M, N, prm->kernel, prm->kappa, prm->n, prm->theta, prm->N0, prm->M0,
+                    prm->precision));
+  }
+  return setup_common(plan, targets, t_off, sources, s_off, charges, 1, &prm->kernel, &prm->kappa,
+                      prm->n, prm->theta, prm->N0, prm->M0, prm->precision, prm->variant, sel,
+                      cuda_stream);
+}
+
+int bldtt_list_classes(bldtt_plan* p, int* num_classes, int* degrees, int* num_degrees) {
+  if (!p) {
+    set_error("plan is NULL");
+    return BLDTT_EINVAL;
+  }
+  if (num_classes) *num_classes = p->nclass;
+  if (num_degrees) *num_degrees = p->deg.n;
+  if (degrees)
+    for (int i = 0; i < p->deg.n; ++i) degrees[i] = p->deg.d[i];
+  return BLDTT_OK;
 }
 
 int bldtt_set_charges(bldtt_plan* p, const double* charges, void* cuda_stream) {
@@ -473,7 +602,8 @@ int bldtt_autotune(bldtt_plan* p, double* phi, void* cuda_stream, int* chosen) {
 namespace {
 int compute_body(bldtt_plan* p, double* phi, cudaStream_t s) {
   BL_CUDA(cudaEventRecord(p->ev[0], s));
-  BL_CUDA(cudaMemsetAsync(p->phit, 0, (size_t)p->tt.nclusters * p->np * sizeof(double), s));
+  for (int i = 0; i < p->deg.n; ++i)
+    BL_CUDA(cudaMemsetAsync(p->phit_d[i], 0, (size_t)p->tt.nclusters * p->deg.np[i] * sizeof(double), s));
   BL_CUDA(cudaMemsetAsync(p->phi_near, 0, (size_t)p->M * sizeof(double), s));
   BL_TRY(upward_pass(p, s));
   BL_TRY(build_pool(p, s));
@@ -568,11 +698,11 @@ int bldtt_export_tree(bldtt_plan* p, int which, int32_t* perm, int32_t* begin, i
 }
 
 int bldtt_export_lists(bldtt_plan* p, int type, int32_t* target, int32_t* source, int64_t* count) {
-  if (!p || type < 0 || type > 3 || !count) {
-    set_error("bad plan, list type or count pointer");
+  if (!p || type < 0 || type >= p->nclass || !count) {
+    set_error("bad plan, list class or count pointer");
     return BLDTT_EINVAL;
   }
-  int64_t need = p->list_count[type];
+  int64_t need = p->class_count[type];
   if (*count < need) {
     *count = need;
     set_error("list capacity %lld below the %lld entries", (long long)*count, (long long)need);

@@ -23,29 +23,40 @@ static TreeView view(const Tree& T) {
   return TreeView{T.begin, T.end, T.nchild, T.first_child, T.center, T.radius};
 }
 
-enum PairAction : int8_t { kActPP = 0, kActPC = 1, kActCP = 2, kActCC = 3, kActSplitT = 4, kActSplitS = 5 };
+// Action of a frontier pair: an entry of list class 0..kMaxClasses-1, or a split.
+constexpr int8_t kActSplitT = 100, kActSplitS = 101;
 
+// choice (may be NULL): the learned selector's decision per pair; NULL or
+// kChoiceFallback applies Alg. 2's MAC at the highest degree (index imax).
 __global__ void k_dtt_classify(const int2* __restrict__ pairs, int32_t F, TreeView tt, TreeView st,
-                               int64_t np, double theta, int variant, int32_t* __restrict__ nkids,
+                               int64_t np, int imax, double theta, int variant,
+                               const int16_t* __restrict__ choice, int32_t* __restrict__ nkids,
                                int32_t* __restrict__ isentry, int8_t* __restrict__ action) {
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= F) return;
   int t = pairs[i].x, s = pairs[i].y;
-  const double* ct = tt.center + (int64_t)t * 3;
-  const double* cs = st.center + (int64_t)s * 3;
-  double dx = __dsub_rn(ct[0], cs[0]), dy = __dsub_rn(ct[1], cs[1]), dz = __dsub_rn(ct[2], cs[2]);
-  double R = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
-  bool sep = __dadd_rn(tt.radius[t], st.radius[s]) < __dmul_rn(theta, R);
   int64_t cnt_t = tt.end[t] - tt.begin[t], cnt_s = st.end[s] - st.begin[s];
-  int8_t a;
+  const int16_t ch = choice ? choice[i] : kChoiceFallback;
+  int8_t a = -1;
   int32_t kids = 0;
-  if (sep) {
-    bool big_t = cnt_t > np, big_s = cnt_s > np;
-    a = big_t ? (big_s ? kActCC : kActCP) : (big_s ? kActPC : kActPP);
-    if (variant == BLDTT_VARIANT_CC_PP_ONLY && a != kActCC) a = kActPP;   // Sec. 4.3 ablation
-  } else {
+  if (ch >= 0) {
+    a = (int8_t)ch;
+  } else if (ch == kChoiceFallback) {
+    const double* ct = tt.center + (int64_t)t * 3;
+    const double* cs = st.center + (int64_t)s * 3;
+    double dx = __dsub_rn(ct[0], cs[0]), dy = __dsub_rn(ct[1], cs[1]), dz = __dsub_rn(ct[2], cs[2]);
+    double R = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+    bool sep = __dadd_rn(tt.radius[t], st.radius[s]) < __dmul_rn(theta, R);
+    if (sep) {
+      bool big_t = cnt_t > np, big_s = cnt_s > np;
+      int type = big_t ? (big_s ? BLDTT_CC : BLDTT_CP) : (big_s ? BLDTT_PC : BLDTT_PP);
+      if (variant == BLDTT_VARIANT_CC_PP_ONLY && type != BLDTT_CC) type = BLDTT_PP;   // Sec. 4.3 ablation
+      a = (int8_t)class_of(type, imax);
+    }
+  }
+  if (a < 0) {
     bool leaf_t = tt.nchild[t] == 0, leaf_s = st.nchild[s] == 0;
-    if (leaf_t && leaf_s) a = kActPP;
+    if (leaf_t && leaf_s) a = 0;   // PP
     else if (leaf_s) a = kActSplitT;
     else if (leaf_t) a = kActSplitS;
     else a = cnt_s < cnt_t ? kActSplitT : kActSplitS;
@@ -96,17 +107,19 @@ __global__ void k_key_hist(const uint32_t* __restrict__ keys, int64_t n, int32_t
   if (i < n) atomicAdd(&cnt[keys[i]], 1);
 }
 
-// Kernel evaluations per type (Eqs. (6), (8), (12), (15)); integer sums, exact.
+// Kernel evaluations per list class (Eqs. (6), (8), (12), (15)); integer sums, exact.
 __global__ void k_count_evals(const int32_t* __restrict__ et, const int32_t* __restrict__ es,
                               const uint32_t* __restrict__ key, int64_t n, int32_t nct,
-                              TreeView tt, TreeView st, int64_t np,
+                              TreeView tt, TreeView st, DegreeSet deg,
                               unsigned long long* __restrict__ out) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  int type = (int)(key[i] / (uint32_t)nct);
+  const int c = (int)(key[i] / (uint32_t)nct);
+  const int type = class_type(c);
+  const int64_t np = deg.np[class_degree(c)];
   int64_t ct = tt.end[et[i]] - tt.begin[et[i]], cs = st.end[es[i]] - st.begin[es[i]];
-  int64_t v = type == 0 ? ct * cs : type == 1 ? ct * np : type == 2 ? np * cs : np * np;
-  atomicAdd(&out[type], (unsigned long long)v);
+  int64_t v = type == BLDTT_PP ? ct * cs : type == BLDTT_PC ? ct * np : type == BLDTT_CP ? np * cs : np * np;
+  atomicAdd(&out[c], (unsigned long long)v);
 }
 
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -139,17 +152,24 @@ int build_lists(bldtt_plan* p, cudaStream_t s) {
   }
   int32_t F = P;
   int64_t E = 0;
+  const int imax = p->deg.n - 1;
   while (F > 0) {
     int32_t *nkids = nullptr, *isentry = nullptr, *koff = nullptr, *eoff = nullptr;
     int8_t* action = nullptr;
+    int16_t* choice = nullptr;
     BL_TRY(dalloc_n(&nkids, F, s));
     BL_TRY(dalloc_n(&isentry, F, s));
     BL_TRY(dalloc_n(&koff, F, s));
     BL_TRY(dalloc_n(&eoff, F, s));
     BL_TRY(dalloc_n(&action, F, s));
-    k_dtt_classify<<<nblk(F, 256), 256, 0, s>>>(front, F, tt, st, p->np, p->theta, p->variant,
-                                                nkids, isentry, action);
+    if (p->learned) {
+      BL_TRY(dalloc_n(&choice, F, s));
+      BL_TRY(select_pairs(p, front, F, choice, s));
+    }
+    k_dtt_classify<<<nblk(F, 256), 256, 0, s>>>(front, F, tt, st, p->deg.np[imax], imax, p->theta,
+                                                p->variant, choice, nkids, isentry, action);
     BL_LAUNCHED(cnt.launches);
+    if (choice) dfree(choice, s);
     int32_t K = 0, En = 0;
     BL_TRY(scan_exclusive(nkids, koff, F, &K, s, cnt));
     BL_TRY(scan_exclusive(isentry, eoff, F, &En, s, cnt));
@@ -181,8 +201,9 @@ int build_lists(bldtt_plan* p, cudaStream_t s) {
 
   // Sort entries by (type, target cluster); the traversal order breaks ties.
   p->nentries = E;
+  const int nclass = p->nclass;
   int key_bits = 1;
-  while ((1ull << key_bits) < 4ull * (unsigned long long)nct) ++key_bits;
+  while ((1ull << key_bits) < (unsigned long long)nclass * (unsigned long long)nct) ++key_bits;
   int32_t* order = nullptr;
   BL_TRY(dalloc_n(&order, E, s));
   if (E > 0) {
@@ -198,7 +219,7 @@ int build_lists(bldtt_plan* p, cudaStream_t s) {
     k_gather_i32<<<nblk(E, 256), 256, 0, s>>>(ent_t, order, p->list_tgt, E);
     BL_LAUNCHED(cnt.launches);
   }
-  int64_t nkeys = 4 * (int64_t)nct;
+  int64_t nkeys = (int64_t)nclass * nct;
   int32_t* hist = nullptr;
   BL_TRY(dalloc_n(&hist, nkeys, s));
   BL_TRY(dalloc_n(&p->list_ptr, nkeys + 1, s));
@@ -212,23 +233,31 @@ int build_lists(bldtt_plan* p, cudaStream_t s) {
   BL_CUDA(cudaMemcpyAsync(p->list_ptr + nkeys, &total, sizeof(int32_t), cudaMemcpyHostToDevice, s));
 
   unsigned long long* evals = nullptr;
-  BL_TRY(dalloc_n(&evals, 4, s));
-  BL_CUDA(cudaMemsetAsync(evals, 0, 4 * sizeof(unsigned long long), s));
+  BL_TRY(dalloc_n(&evals, kMaxClasses, s));
+  BL_CUDA(cudaMemsetAsync(evals, 0, kMaxClasses * sizeof(unsigned long long), s));
   if (E > 0) {
     k_count_evals<<<nblk(E, 256), 256, 0, s>>>(p->list_tgt, p->list_src, ent_key, E, nct, tt, st,
-                                               p->np, evals);
+                                               p->deg, evals);
     BL_LAUNCHED(cnt.launches);
   }
-  unsigned long long h_evals[4];
-  int32_t h_ptr[5];
-  for (int k = 0; k < 5; ++k)
+  unsigned long long h_evals[kMaxClasses];
+  int32_t h_ptr[kMaxClasses + 1];
+  for (int k = 0; k <= nclass; ++k)
     BL_CUDA(cudaMemcpyAsync(&h_ptr[k], p->list_ptr + (int64_t)k * nct, sizeof(int32_t),
                             cudaMemcpyDeviceToHost, s));
   BL_CUDA(cudaMemcpyAsync(h_evals, evals, sizeof(h_evals), cudaMemcpyDeviceToHost, s));
   BL_CUDA(cudaStreamSynchronize(s));
+  p->class_count.assign(nclass, 0);
+  p->class_evals.assign(nclass, 0.0);
   for (int k = 0; k < 4; ++k) {
-    p->list_count[k] = h_ptr[k + 1] - h_ptr[k];
-    p->interactions[k] = (double)h_evals[k];
+    p->list_count[k] = 0;
+    p->interactions[k] = 0.0;
+  }
+  for (int c = 0; c < nclass; ++c) {
+    p->class_count[c] = h_ptr[c + 1] - h_ptr[c];
+    p->class_evals[c] = (double)h_evals[c];
+    p->list_count[class_type(c)] += p->class_count[c];
+    p->interactions[class_type(c)] += p->class_evals[c];
   }
   if (total != E) {
     set_error("interaction list CSR holds %d entries, traversal produced %lld", total, (long long)E);
@@ -257,58 +286,63 @@ struct ListView {
   const int32_t *ptr, *src;
   int32_t nct;
   const int32_t *s_leaf_first, *s_leaf_last, *pad_prefix;
-  int32_t np_pad;
+  DegreeSet deg;
 };
 
-// Real sources (no padding) a target cluster's own lists of two types contribute.
-__device__ __forceinline__ int64_t list_sources(const ListView& L, const int32_t* s_begin,
-                                                const int32_t* s_end, int32_t np, int type_particles,
-                                                int type_proxies, int32_t c) {
-  int64_t n = 0;
-  int64_t k0 = (int64_t)type_particles * L.nct + c;
-  for (int32_t e = L.ptr[k0]; e < L.ptr[k0 + 1]; ++e) n += s_end[L.src[e]] - s_begin[L.src[e]];
-  int64_t k1 = (int64_t)type_proxies * L.nct + c;
-  n += (int64_t)(L.ptr[k1 + 1] - L.ptr[k1]) * np;
-  return n;
-}
-
-// Chunks a target cluster's own lists of two types contribute.
-__device__ __forceinline__ int64_t list_chunks(const ListView& L, int type_particles, int type_proxies,
-                                               int32_t c) {
-  int64_t ch = 0;
-  int64_t k0 = (int64_t)type_particles * L.nct + c;
-  for (int32_t e = L.ptr[k0]; e < L.ptr[k0 + 1]; ++e) {
-    int32_t s = L.src[e];
-    ch += (L.pad_prefix[L.s_leaf_last[s]] - L.pad_prefix[L.s_leaf_first[s]]) / kChunk;
+// Real sources (no padding) and pool chunks that the entries of list class
+// `cls` of target cluster c contribute: particles of source clusters
+// (particles = true) or proxies of degree index i.
+__device__ __forceinline__ void class_work(const ListView& L, const int32_t* s_begin, const int32_t* s_end,
+                                           int cls, bool particles, int i, int32_t c, int64_t& sources,
+                                           int64_t& chunks) {
+  const int64_t k = (int64_t)cls * L.nct + c;
+  const int32_t e0 = L.ptr[k], e1 = L.ptr[k + 1];
+  if (particles) {
+    for (int32_t e = e0; e < e1; ++e) {
+      const int32_t s = L.src[e];
+      sources += s_end[s] - s_begin[s];
+      chunks += (L.pad_prefix[L.s_leaf_last[s]] - L.pad_prefix[L.s_leaf_first[s]]) / kChunk;
+    }
+  } else {
+    sources += (int64_t)(e1 - e0) * L.deg.np[i];
+    chunks += (int64_t)(e1 - e0) * (L.deg.np_pad[i] / kChunk);
   }
-  int64_t k1 = (int64_t)type_proxies * L.nct + c;
-  ch += (int64_t)(L.ptr[k1 + 1] - L.ptr[k1]) * (L.np_pad / kChunk);
-  return ch;
 }
 
+// Items of target cluster c: tiles of its particles (a leaf: PP and PC of every
+// degree, on the leaf and on each ancestor), and tiles of its proxy points of
+// degree i (CP and CC of degree i on the cluster itself).  cost_prox is
+// [nct][kMaxDegrees].
 __global__ void k_item_count(int32_t nct, ListView L, const int32_t* __restrict__ parent,
                              const int32_t* __restrict__ nchild, const int32_t* __restrict__ begin,
                              const int32_t* __restrict__ end, const int32_t* __restrict__ s_begin,
-                             const int32_t* __restrict__ s_end, int32_t np,
-                             int32_t* __restrict__ nitems, int64_t* __restrict__ cost_part,
-                             int64_t* __restrict__ cost_prox, unsigned long long* __restrict__ executed) {
+                             const int32_t* __restrict__ s_end, int32_t* __restrict__ nitems,
+                             int64_t* __restrict__ cost_part, int64_t* __restrict__ cost_prox,
+                             unsigned long long* __restrict__ executed) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nct) return;
   int64_t cp = 0, sp = 0;
   if (nchild[c] == 0)   // PP + PC of the leaf and of all its ancestors (Sec. 2.7 chain)
     for (int32_t a = c; a >= 0; a = parent[a]) {
-      cp += list_chunks(L, 0, 1, a);
-      sp += list_sources(L, s_begin, s_end, np, 0, 1, a);
+      class_work(L, s_begin, s_end, 0, true, 0, a, sp, cp);
+      for (int i = 0; i < L.deg.n; ++i)
+        class_work(L, s_begin, s_end, class_of(BLDTT_PC, i), false, i, a, sp, cp);
     }
-  int64_t cq = list_chunks(L, 2, 3, c);   // CP + CC of the cluster itself
-  int64_t sq = list_sources(L, s_begin, s_end, np, 2, 3, c);
-  int32_t tp = cp > 0 ? (end[c] - begin[c] + kTile - 1) / kTile : 0;
-  int32_t tq = cq > 0 ? (np + kTile - 1) / kTile : 0;
-  nitems[c] = tp + tq;
+  const int32_t tp = cp > 0 ? (end[c] - begin[c] + kTile - 1) / kTile : 0;
+  int32_t items = tp;
+  unsigned long long ex = (unsigned long long)tp * kTile * sp;
+  for (int i = 0; i < L.deg.n; ++i) {   // CP + CC of degree i on the cluster itself
+    int64_t cq = 0, sq = 0;
+    class_work(L, s_begin, s_end, class_of(BLDTT_CP, i), true, i, c, sq, cq);
+    class_work(L, s_begin, s_end, class_of(BLDTT_CC, i), false, i, c, sq, cq);
+    const int32_t tq = cq > 0 ? (L.deg.np[i] + kTile - 1) / kTile : 0;
+    items += tq;
+    cost_prox[(int64_t)c * kMaxDegrees + i] = cq;
+    ex += (unsigned long long)tq * kTile * sq;
+  }
+  nitems[c] = items;
   cost_part[c] = cp;
-  cost_prox[c] = cq;
   // evaluations the kernel performs: every target slot of every tile meets every real source
-  unsigned long long ex = (unsigned long long)tp * kTile * sp + (unsigned long long)tq * kTile * sq;
   if (ex) atomicAdd(executed, ex);
 }
 
@@ -323,7 +357,7 @@ __global__ void k_item_fill(int32_t nct, const int32_t* __restrict__ off,
                             const int64_t* __restrict__ cost_part, const int64_t* __restrict__ cost_prox,
                             const int32_t* __restrict__ begin, const int32_t* __restrict__ end,
                             const int32_t* __restrict__ problem, const int* __restrict__ prob_kernel,
-                            SegmentMap segmap, int32_t np, int4* __restrict__ items,
+                            SegmentMap segmap, DegreeSet deg, int4* __restrict__ items,
                             uint32_t* __restrict__ keys, int32_t* __restrict__ vals) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nct) return;
@@ -342,10 +376,13 @@ __global__ void k_item_fill(int32_t nct, const int32_t* __restrict__ off,
       ++o;
     }
   }
-  if (cost_prox[c] > 0) {
-    uint32_t k = (seg << 24) | (kKeyMax - (uint32_t)min((int64_t)kKeyMax, cost_prox[c]));
+  for (int i = 0; i < deg.n; ++i) {
+    const int64_t cq = cost_prox[(int64_t)c * kMaxDegrees + i];
+    if (cq <= 0) continue;
+    const int32_t np = deg.np[i];
+    uint32_t k = (seg << 24) | (kKeyMax - (uint32_t)min((int64_t)kKeyMax, cq));
     for (int32_t r = 0; r < np; r += kTile) {
-      items[o] = make_int4(c, r, min(kTile, np - r), kItemProxies);
+      items[o] = make_int4(c, r, min(kTile, np - r), kItemProxies + i);
       keys[o] = k;
       vals[o] = o;
       ++o;
@@ -370,9 +407,13 @@ __global__ void k_gather_items(const int4* __restrict__ src, const int32_t* __re
 // Bounding box of every 32-row group of every work item (the targets one warp
 // evaluates together in any consumer layout), rounded outward to floats; an
 // empty group gets an empty box.  One warp per group.
+struct NodeSet {
+  const double* nodes[kMaxDegrees];   // [C][3][d+1] per degree index
+};
+
 __global__ void k_item_boxes(int32_t nitems, const int4* __restrict__ items, const double* __restrict__ x,
-                             const double* __restrict__ y, const double* __restrict__ z,
-                             const double* __restrict__ nodes, int P, float4* __restrict__ box) {
+                             const double* __restrict__ y, const double* __restrict__ z, NodeSet ns,
+                             DegreeSet deg, float4* __restrict__ box) {
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (w >= (int64_t)nitems * kItemGroups) return;
@@ -388,7 +429,8 @@ __global__ void k_item_boxes(int32_t nitems, const int4* __restrict__ items, con
       v[2] = z[i];
     } else {
       const int l = it.y + r;
-      const double* nd = nodes + (int64_t)it.x * 3 * P;
+      const int P = deg.d[it.w - kItemProxies] + 1;
+      const double* nd = ns.nodes[it.w - kItemProxies] + (int64_t)it.x * 3 * P;
       v[0] = nd[l / (P * P)];
       v[1] = nd[P + (l / P) % P];
       v[2] = nd[2 * P + l % P];
@@ -429,23 +471,27 @@ int build_work_items(bldtt_plan* p, cudaStream_t s) {
   BL_CUDA(cudaMemcpyAsync(p->pad_prefix + st.nleaves, &total, sizeof(int32_t),
                           cudaMemcpyHostToDevice, s));
   dfree(padded, s);
-  p->np_pad = (p->np + kChunk - 1) / kChunk * kChunk;
   p->pool_particles = total;
-  p->pool_len = (int64_t)total + (int64_t)st.nclusters * p->np_pad;
+  p->pool_len = total;
+  for (int i = 0; i < p->deg.n; ++i) {   // proxy blocks of every source cluster, per degree
+    p->deg.proxy_base[i] = p->pool_len;
+    p->pool_len += (int64_t)st.nclusters * p->deg.np_pad[i];
+  }
+  p->np_pad = p->deg.np_pad[p->deg.n - 1];
 
   const int32_t nct = tt.nclusters;
-  ListView L{p->list_ptr, p->list_src, nct, st.leaf_first, st.leaf_last, p->pad_prefix, p->np_pad};
+  ListView L{p->list_ptr, p->list_src, nct, st.leaf_first, st.leaf_last, p->pad_prefix, p->deg};
   int32_t *nitems = nullptr, *off = nullptr;
   int64_t *cost_part = nullptr, *cost_prox = nullptr;
   BL_TRY(dalloc_n(&nitems, nct, s));
   BL_TRY(dalloc_n(&off, nct, s));
   BL_TRY(dalloc_n(&cost_part, nct, s));
-  BL_TRY(dalloc_n(&cost_prox, nct, s));
+  BL_TRY(dalloc_n(&cost_prox, (size_t)nct * kMaxDegrees, s));
   unsigned long long* executed = nullptr;
   BL_TRY(dalloc_n(&executed, 1, s));
   BL_CUDA(cudaMemsetAsync(executed, 0, sizeof(unsigned long long), s));
   k_item_count<<<nblk(nct, 128), 128, 0, s>>>(nct, L, tt.parent, tt.nchild, tt.begin, tt.end,
-                                              st.begin, st.end, p->np, nitems, cost_part, cost_prox,
+                                              st.begin, st.end, nitems, cost_part, cost_prox,
                                               executed);
   BL_LAUNCHED(cnt.launches);
   int32_t ni = 0;
@@ -462,7 +508,7 @@ int build_work_items(bldtt_plan* p, cudaStream_t s) {
   segmap.n = (int)p->kernels_present.size();
   for (int i = 0; i < segmap.n; ++i) segmap.kernel[i] = p->kernels_present[i];
   k_item_fill<<<nblk(nct, 128), 128, 0, s>>>(nct, off, cost_part, cost_prox, tt.begin, tt.end,
-                                             tt.problem, p->prob_kernel, segmap, p->np, items, keys,
+                                             tt.problem, p->prob_kernel, segmap, p->deg, items, keys,
                                              vals);
   BL_LAUNCHED(cnt.launches);
   // Grouped by kernel, longest items first within a group (stable), so that
@@ -485,8 +531,10 @@ int build_work_items(bldtt_plan* p, cudaStream_t s) {
   }
   if (p->precision == BLDTT_FP32_BULK && ni > 0) {
     BL_TRY(dalloc_n(&p->item_box, (size_t)ni * kItemGroups * 2, s));
-    k_item_boxes<<<nblk((int64_t)ni * kItemGroups, 8), 256, 0, s>>>(ni, p->items, tt.x, tt.y, tt.z,
-                                                                    tt.nodes, p->P, p->item_box);
+    NodeSet ns{};
+    for (int i = 0; i < p->deg.n; ++i) ns.nodes[i] = p->nodes_t[i];
+    k_item_boxes<<<nblk((int64_t)ni * kItemGroups, 8), 256, 0, s>>>(ni, p->items, tt.x, tt.y, tt.z, ns,
+                                                                    p->deg, p->item_box);
     BL_LAUNCHED(cnt.launches);
   }
   unsigned long long h_exec = 0;

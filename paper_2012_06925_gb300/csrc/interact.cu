@@ -60,17 +60,15 @@ struct InteractView {
   const float4* chunk_frame;   // [chunks][2]: frame centre + real count (int bits), extents + tau
   const float* pool_res;       // FP32: frame residuals of the pool's particles (pair records)
   const float4* item_box;      // FP32: [items][kItemGroups][2] target group boxes (lo, hi)
-  int32_t np_pad;
-  int64_t proxy_base;
+  DegreeSet deg;               // degrees, proxies per cluster and pool offsets per degree
   const void* pool;
   // targets and outputs (consumers)
   const double* tx;
   const double* ty;
   const double* tz;
-  const double* t_nodes;
-  int32_t P, np;
+  const double* t_nodes[kMaxDegrees];   // target proxy nodes per degree index
   double* phi_near;
-  double* phit;
+  double* phit[kMaxDegrees];            // target proxy potentials per degree index
   int* err;
   // per-problem kernel parameters (read once per work item)
   const int32_t* t_problem;    // target cluster -> problem
@@ -330,13 +328,16 @@ struct Producer {
     return segment(o, v.pad_prefix[v.s_leaf_last[s]] - o);
   }
 
-  __device__ bool lists(int type_particles, int type_proxies, int32_t c) {
-    int64_t k0 = (int64_t)type_particles * v.nct + c;
-    for (int32_t e = v.list_ptr[k0]; e < v.list_ptr[k0 + 1]; ++e)
-      if (!leaves_of(v.list_src[e])) return false;
-    int64_t k1 = (int64_t)type_proxies * v.nct + c;
-    for (int32_t e = v.list_ptr[k1]; e < v.list_ptr[k1 + 1]; ++e)
-      if (!segment(v.proxy_base + (int64_t)v.list_src[e] * v.np_pad, v.np_pad)) return false;
+  // Entries of list class cls of target cluster c: particles of the source
+  // clusters, or their proxy blocks of degree index i (i >= 0).
+  __device__ bool entries(int cls, int i, int32_t c) {
+    const int64_t k = (int64_t)cls * v.nct + c;
+    for (int32_t e = v.list_ptr[k]; e < v.list_ptr[k + 1]; ++e) {
+      const int32_t src = v.list_src[e];
+      const bool ok = i < 0 ? leaves_of(src)
+                            : segment(v.deg.proxy_base[i] + (int64_t)src * v.deg.np_pad[i], v.deg.np_pad[i]);
+      if (!ok) return false;
+    }
     return true;
   }
 
@@ -349,10 +350,14 @@ struct Producer {
       cur_item = idx;
       cur_groups = (item.z + 31) / 32;
       if (std::is_same<Vec, float4>::value) load_item_box();
-      if (item.w == kItemParticles) {
-        for (int32_t a = item.x; a >= 0 && ok; a = v.t_parent[a]) ok = lists(BLDTT_PP, BLDTT_PC, a);
-      } else {
-        ok = lists(BLDTT_CP, BLDTT_CC, item.x);
+      if (item.w == kItemParticles) {   // PP and PC of every degree, leaf and ancestors
+        for (int32_t a = item.x; a >= 0 && ok; a = v.t_parent[a]) {
+          ok = entries(0, -1, a);
+          for (int i = 0; i < v.deg.n && ok; ++i) ok = entries(class_of(BLDTT_PC, i), i, a);
+        }
+      } else {                          // CP and CC of one degree on the cluster itself
+        const int i = item.w - kItemProxies;
+        ok = entries(class_of(BLDTT_CP, i), -1, item.x) && entries(class_of(BLDTT_CC, i), i, item.x);
       }
       if (!ok) break;
     }
@@ -580,10 +585,11 @@ __device__ __forceinline__ void target_coords(const InteractView& v, const int4&
     Y = v.ty[i];
     Z = v.tz[i];
   } else {
-    const int P = v.P;
+    const int i = item.w - kItemProxies;
+    const int P = v.deg.d[i] + 1;
     int l = item.y + r;
     int l1 = l / (P * P), l2 = (l / P) % P, l3 = l % P;
-    const double* nd = v.t_nodes + (int64_t)item.x * 3 * P;
+    const double* nd = v.t_nodes[i] + (int64_t)item.x * 3 * P;
     X = nd[l1];
     Y = nd[P + l2];
     Z = nd[2 * P + l3];
@@ -596,7 +602,7 @@ __device__ __forceinline__ void store_output(const InteractView& v, const int4& 
     if (item.w == kItemParticles)
       v.phi_near[(int64_t)item.y + r] = value;
     else
-      v.phit[(int64_t)item.x * v.np + item.y + r] = value;
+      v.phit[item.w - kItemProxies][(int64_t)item.x * v.deg.np[item.w - kItemProxies] + item.y + r] = value;
   }
 }
 
@@ -892,17 +898,16 @@ static InteractView make_view(const bldtt_plan* p) {
   v.chunk_frame = p->chunk_frame;
   v.pool_res = p->pool_res;
   v.item_box = p->item_box;
-  v.np_pad = p->np_pad;
-  v.proxy_base = p->pool_particles;
+  v.deg = p->deg;
   v.pool = p->pool;
   v.tx = tt.x;
   v.ty = tt.y;
   v.tz = tt.z;
-  v.t_nodes = tt.nodes;
-  v.P = p->P;
-  v.np = p->np;
+  for (int i = 0; i < kMaxDegrees; ++i) {
+    v.t_nodes[i] = i < p->deg.n ? p->nodes_t[i] : nullptr;
+    v.phit[i] = i < p->deg.n ? p->phit_d[i] : nullptr;
+  }
   v.phi_near = p->phi_near;
-  v.phit = p->phit;
   v.err = p->dev_err;
   v.t_problem = tt.problem;
   v.prob_prm = p->prob_prm;

@@ -33,6 +33,32 @@ constexpr int kTile = 256;                     // targets per work item of the i
 constexpr int kStages = 6;                     // depth of the shared-memory ring
 constexpr int kChunkInfo = 2;                  // float4 per pool chunk description
 constexpr int kItemGroups = kTile / 32;        // 32-row target groups per work item
+constexpr int kMaxDegrees = 8;                 // interpolation degrees of one plan
+constexpr int kMaxClasses = 1 + 3 * kMaxDegrees;
+constexpr int kHidden = 64;                    // selector network width
+constexpr int kFeatures = 6;                   // selector network inputs
+
+// Degree set of a plan (one degree, n, unless a learned selector picks a
+// degree per pair).  Interaction-list classes: 0 = PP, 1 + 3 i + t with
+// t = 0 PC, 1 CP, 2 CC at degree d[i]; with one degree the classes are
+// PP, PC, CP, CC = 0, 1, 2, 3.
+struct DegreeSet {
+  int n = 1;
+  int d[kMaxDegrees] = {};
+  int np[kMaxDegrees] = {};
+  int np_pad[kMaxDegrees] = {};
+  int64_t proxy_base[kMaxDegrees] = {};   // source-pool offset of degree i's proxy blocks
+};
+// Chebyshev point of the 2nd kind s_k = cos(pi k / n) on [-1, 1], symmetrised
+// (s_{n-k} = -s_k, s_{n/2} = 0) as the proxy points of Sec. 2.2.
+__device__ __forceinline__ double cheb_point(int k, int n) {
+  if (2 * k == n) return 0.0;
+  if (2 * k < n) return cos(__ddiv_rn(__dmul_rn(M_PI, (double)k), (double)n));
+  return -cos(__ddiv_rn(__dmul_rn(M_PI, (double)(n - k)), (double)n));
+}
+__host__ __device__ inline int class_type(int c) { return c == 0 ? BLDTT_PP : 1 + (c - 1) % 3; }
+__host__ __device__ inline int class_degree(int c) { return c == 0 ? 0 : (c - 1) / 3; }
+__host__ __device__ inline int class_of(int type, int i) { return type == BLDTT_PP ? 0 : 1 + 3 * i + (type - 1); }
 
 // ---- FP32 frame coordinates ------------------------------------------------
 // A coordinate v (FP64) is carried in FP32 relative to a frame centre c (a
@@ -58,6 +84,8 @@ __device__ __forceinline__ void split_f64(double v, float& hi, float& lo) {
   lo = __double2float_rn(__dsub_rn(v, (double)hi));
 }
 
+// Work-item kinds: particle targets, or the proxy points of degree index
+// (kind - kItemProxies) of a target cluster.
 enum ItemKind { kItemParticles = 0, kItemProxies = 1 };
 
 // Error flag codes written by kernels into plan->dev_err.
@@ -121,7 +149,7 @@ struct Tree {
   double* box = nullptr;              // [C][6]: lo x,y,z, hi x,y,z
   double* center = nullptr;           // [C][3]
   double* radius = nullptr;           // [C]
-  double* nodes = nullptr;            // [C][3][P]
+  double* nodes = nullptr;            // [C][3][P], P = n + 1 of the plan's highest degree
   int32_t* leaf_ids = nullptr;        // leaf order (by begin) -> cluster
   int32_t *leaf_first = nullptr, *leaf_last = nullptr;   // per cluster: leaf-order range
   std::vector<int32_t> level_start;   // host: level l holds clusters [ls[l], ls[l+1])
@@ -158,6 +186,26 @@ struct bldtt_plan {
   cudaStream_t stream = nullptr;      // stream of the last call (for synchronisation)
 
   bldtt::Tree tt, st;                 // target and source trees
+  // Degrees (bldtt::DegreeSet); n above is the highest.  Per degree index i
+  // below the highest: proxy nodes of both trees [C][3][d+1], the proxy
+  // charges and potentials [C][np], and the (d+1) x (n+1) matrix
+  // A[k][k'] = L^(d)_k(s^(n)_k') of Chebyshev points on [-1, 1].
+  bldtt::DegreeSet deg;
+  int nclass = 4;
+  double* nodes_t[bldtt::kMaxDegrees] = {};
+  double* nodes_s[bldtt::kMaxDegrees] = {};
+  double* qhat_d[bldtt::kMaxDegrees] = {};
+  double* phit_d[bldtt::kMaxDegrees] = {};
+  double* xfer[bldtt::kMaxDegrees] = {};
+  // Learned selector (bldtt_setup_learned): bf16 weights W1..W4, float
+  // biases, the training box of the features and the per-pair budget.
+  bool learned = false;
+  bool selector_net = false;          // false: the MAC fallback decides every pair
+  void* sel_w = nullptr;              // __nv_bfloat16 [64*6 + 64*64*2 + nout*64]
+  float* sel_b = nullptr;             // [64*3 + nout]
+  int sel_nout = 0;
+  float sel_lo[bldtt::kFeatures] = {}, sel_hi[bldtt::kFeatures] = {};
+  float sel_log_eps = 0.f;
   double* q_tree = nullptr;           // [N] charges, source tree order
 
   // Interaction lists: CSR over key = type * nct + t.
@@ -165,8 +213,10 @@ struct bldtt_plan {
   int32_t* list_src = nullptr;        // [E]
   int32_t* list_tgt = nullptr;        // [E]
   int64_t nentries = 0;
-  int64_t list_count[4] = {0, 0, 0, 0};
+  int64_t list_count[4] = {0, 0, 0, 0};        // entries per type (all degrees)
   double interactions[4] = {0, 0, 0, 0};
+  std::vector<int64_t> class_count;             // entries per class
+  std::vector<double> class_evals;              // kernel evaluations per class
 
   // Source pool.
   int np_pad = 0;                     // proxies per cluster rounded up to kChunk
@@ -242,6 +292,8 @@ int build_work_items(bldtt_plan* p, cudaStream_t s);
 int permute_charges(bldtt_plan* p, const double* charges_user, cudaStream_t s);
 int upward_pass(bldtt_plan* p, cudaStream_t s);
 int build_pool(bldtt_plan* p, cudaStream_t s);
+// Proxy nodes and degree-transfer matrices of the degrees below the highest.
+int setup_degrees(bldtt_plan* p, cudaStream_t s);
 int build_chunk_frames(bldtt_plan* p, cudaStream_t s);
 int downward_pass(bldtt_plan* p, double* phi_user, cudaStream_t s);
 int configure_pass_kernels();
@@ -251,6 +303,13 @@ int layouts_available(int kernel, int* out);
 int interaction_grids(bldtt_plan* p);                 // launch shape of every segment
 int run_segment(bldtt_plan* p, int seg, cudaStream_t s);
 int run_interactions(bldtt_plan* p, cudaStream_t s);
+
+// ---- learned selector (learned.cu) ----
+// Class decision of every frontier pair (class >= 0, kChoiceNoApprox, or
+// kChoiceFallback for the MAC of Alg. 2).
+constexpr int16_t kChoiceNoApprox = -2;
+constexpr int16_t kChoiceFallback = -1;
+int select_pairs(bldtt_plan* p, const int2* pairs, int32_t F, int16_t* choice, cudaStream_t s);
 
 // ---- direct sum (direct.cu) ----
 int direct_sum(const double* targets, int64_t M, const double* sources, int64_t N,

@@ -5,7 +5,9 @@
 // guard of the second barycentric form (Sec. 2.1, Eq. (3)); in FP32_BULK mode
 // the contractions that follow (leaf proxy charges and the leaf interpolation
 // to particles) run in FP32 over short runs that are summed in FP64.
+#include <cmath>
 #include <type_traits>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -207,6 +209,57 @@ __global__ void k_up_parent(int32_t ls, const int32_t* __restrict__ nchild,
   }
 }
 
+// Degree change on one proxy grid (same box): with A[k][k'] = L^(d)_k(s^(n)_k')
+// (Chebyshev points on [-1, 1]; the barycentric basis is scale free),
+//   proxy charges of degree d:   qhat^(d)_k  = sum_k' A(x)A(x)A [k][k'] qhat^(n)_k'
+//   proxy potentials to degree n: phi^(n)_k' += sum_k A(x)A(x)A [k][k'] phi^(d)_k
+// Both are exact in exact arithmetic: L^(d)_k is a polynomial of degree
+// d <= n, reproduced by the degree-n interpolation (App. A).
+// y[a][b][c] (+)= sum M[a][a'] M[b][b'] M[c][c'] x[a'][b'][c'], M = Pout x Pin,
+// element (r, k) at M[r * ms_r + k * ms_k].  One block per cluster.
+__global__ void k_mode3(int32_t C, const double* __restrict__ M, int ms_r, int ms_k, int Pin, int Pout,
+                        const double* __restrict__ in, double* __restrict__ out, int accumulate) {
+  extern __shared__ double smem[];
+  const int c = blockIdx.x;
+  if (c >= C) return;
+  double* Ms = smem;                         // [Pout][Pin]
+  double* X = Ms + Pout * Pin;               // [Pin^3]
+  double* T1 = X + Pin * Pin * Pin;          // [Pout][Pin][Pin]
+  double* T2 = T1 + Pout * Pin * Pin;        // [Pout][Pout][Pin]
+  const int nin = Pin * Pin * Pin, nout = Pout * Pout * Pout;
+  for (int t = threadIdx.x; t < Pout * Pin; t += blockDim.x)
+    Ms[t] = M[(t / Pin) * ms_r + (t % Pin) * ms_k];
+  for (int t = threadIdx.x; t < nin; t += blockDim.x) X[t] = in[(int64_t)c * nin + t];
+  __syncthreads();
+  for (int t = threadIdx.x; t < Pout * Pin * Pin; t += blockDim.x) {
+    const int a = t / (Pin * Pin), rest = t % (Pin * Pin);
+    double v = 0.0;
+    for (int k = 0; k < Pin; ++k) v += Ms[a * Pin + k] * X[k * Pin * Pin + rest];
+    T1[t] = v;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < Pout * Pout * Pin; t += blockDim.x) {
+    const int a = t / (Pout * Pin), b = (t / Pin) % Pout, cc = t % Pin;
+    double v = 0.0;
+    for (int k = 0; k < Pin; ++k) v += Ms[b * Pin + k] * T1[(a * Pin + k) * Pin + cc];
+    T2[t] = v;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nout; t += blockDim.x) {
+    const int ab = t / Pout, cc = t % Pout;
+    double v = 0.0;
+    for (int k = 0; k < Pin; ++k) v += Ms[cc * Pin + k] * T2[ab * Pin + k];
+    if (accumulate)
+      out[(int64_t)c * nout + t] += v;
+    else
+      out[(int64_t)c * nout + t] = v;
+  }
+}
+
+static size_t mode3_smem_bytes(int Pin, int Pout) {
+  return sizeof(double) * (size_t)(Pout * Pin + Pin * Pin * Pin + Pout * Pin * Pin + Pout * Pout * Pin);
+}
+
 int upward_pass(bldtt_plan* p, cudaStream_t s) {
   Counters& cnt = p->compute_counter;
   const Tree& T = p->st;
@@ -221,6 +274,14 @@ int upward_pass(bldtt_plan* p, cudaStream_t s) {
   for (int lvl = T.nlevels - 2; lvl >= 0; --lvl) {
     int32_t ls = T.level_start[lvl], nl = T.level_start[lvl + 1] - ls;
     k_up_parent<<<nl, kUpThreads, sm, s>>>(ls, T.nchild, T.first_child, T.nodes, p->n, p->qhat);
+    BL_LAUNCHED(cnt.launches);
+  }
+  // Proxy charges of the lower degrees from those of the highest.
+  const int Pm = p->P;
+  for (int i = 0; i + 1 < p->deg.n; ++i) {
+    const int Pi = p->deg.d[i] + 1;
+    k_mode3<<<T.nclusters, kUpThreads, mode3_smem_bytes(Pm, Pi), s>>>(T.nclusters, p->xfer[i], Pm, 1,
+                                                                      Pm, Pi, p->qhat, p->qhat_d[i], 0);
     BL_LAUNCHED(cnt.launches);
   }
   return BLDTT_OK;
@@ -293,15 +354,25 @@ int build_pool(bldtt_plan* p, cudaStream_t s) {
                                                        p->chunk_frame, T.x, T.y, T.z, p->q_tree,
                                                        (float4*)p->pool);
     BL_LAUNCHED(cnt.launches);
-    k_pool_proxies<float4><<<T.nclusters, 256, 0, s>>>(p->n, p->np_pad, p->pool_particles, T.nodes,
-                                                       p->chunk_frame, p->qhat, (float4*)p->pool);
+    for (int i = 0; i < p->deg.n; ++i) {
+      k_pool_proxies<float4><<<T.nclusters, 256, 0, s>>>(p->deg.d[i], p->deg.np_pad[i],
+                                                         p->deg.proxy_base[i], p->nodes_s[i],
+                                                         p->chunk_frame, p->qhat_d[i],
+                                                         (float4*)p->pool);
+      if (i + 1 < p->deg.n) BL_LAUNCHED(cnt.launches);
+    }
   } else {
     k_pool_particles<double4><<<T.nleaves, 256, 0, s>>>(T.leaf_ids, T.begin, T.end, p->pad_prefix,
                                                         p->chunk_frame, T.x, T.y, T.z, p->q_tree,
                                                         (double4*)p->pool);
     BL_LAUNCHED(cnt.launches);
-    k_pool_proxies<double4><<<T.nclusters, 256, 0, s>>>(p->n, p->np_pad, p->pool_particles, T.nodes,
-                                                        p->chunk_frame, p->qhat, (double4*)p->pool);
+    for (int i = 0; i < p->deg.n; ++i) {
+      k_pool_proxies<double4><<<T.nclusters, 256, 0, s>>>(p->deg.d[i], p->deg.np_pad[i],
+                                                          p->deg.proxy_base[i], p->nodes_s[i],
+                                                          p->chunk_frame, p->qhat_d[i],
+                                                          (double4*)p->pool);
+      if (i + 1 < p->deg.n) BL_LAUNCHED(cnt.launches);
+    }
   }
   BL_LAUNCHED(cnt.launches);
   return BLDTT_OK;
@@ -423,11 +494,13 @@ int build_chunk_frames(bldtt_plan* p, cudaStream_t s) {
                                                         p->pad_prefix, T.x, T.y, T.z, p->chunk_frame);
     BL_LAUNCHED(cnt.launches);
   }
-  const int32_t cpc = p->np_pad / kChunk;
-  k_frames_proxies<<<nblk((int64_t)T.nclusters * cpc, 256), 256, 0, s>>>(T.nclusters, pchunks, cpc,
-                                                                          p->np, T.center, T.box,
-                                                                          p->chunk_frame);
-  BL_LAUNCHED(cnt.launches);
+  for (int i = 0; i < p->deg.n; ++i) {
+    const int32_t cpc = p->deg.np_pad[i] / kChunk;
+    k_frames_proxies<<<nblk((int64_t)T.nclusters * cpc, 256), 256, 0, s>>>(
+        T.nclusters, p->deg.proxy_base[i] / kChunk, cpc, p->deg.np[i], T.center, T.box,
+        p->chunk_frame);
+    BL_LAUNCHED(cnt.launches);
+  }
   if (p->precision == BLDTT_FP32_BULK && pchunks > 0) {
     BL_TRY(dalloc_n(&p->pool_res, (size_t)p->pool_particles * 4, s));
     BL_CUDA(cudaMemsetAsync(p->pool_res, 0, (size_t)p->pool_particles * 4 * sizeof(float), s));
@@ -528,6 +601,13 @@ __global__ void __launch_bounds__(kDownThreads) k_down_leaf(
 int downward_pass(bldtt_plan* p, double* phi_user, cudaStream_t s) {
   Counters& cnt = p->compute_counter;
   const Tree& T = p->tt;
+  // Proxy potentials of the lower degrees onto the highest degree's grid.
+  for (int i = 0; i + 1 < p->deg.n; ++i) {
+    const int Pi = p->deg.d[i] + 1, Pm = p->P;
+    k_mode3<<<T.nclusters, kUpThreads, mode3_smem_bytes(Pi, Pm), s>>>(T.nclusters, p->xfer[i], 1, Pm,
+                                                                      Pi, Pm, p->phit_d[i], p->phit, 1);
+    BL_LAUNCHED(cnt.launches);
+  }
   size_t sm = transfer_smem_bytes(p->P);
   for (int lvl = 1; lvl < T.nlevels; ++lvl) {
     int32_t ls = T.level_start[lvl], nl = T.level_start[lvl + 1] - ls;
@@ -559,6 +639,74 @@ int configure_pass_kernels() {
   BL_CUDA(cudaFuncSetAttribute(k_down_parent, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   BL_CUDA(cudaFuncSetAttribute(k_down_leaf<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   BL_CUDA(cudaFuncSetAttribute(k_down_leaf<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  BL_CUDA(cudaFuncSetAttribute(k_mode3, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  return BLDTT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Degree sets
+// ---------------------------------------------------------------------------
+__global__ void k_nodes_degree(int32_t C, int degree, const double* __restrict__ box,
+                               double* __restrict__ nodes) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  const int P = degree + 1;
+  const double* b = box + (int64_t)c * 6;
+  for (int d = 0; d < 3; ++d) {   // the same expression as the tree's own proxy points
+    const double lo = b[d], hi = b[3 + d];
+    const double cc = __dmul_rn(__dadd_rn(lo, hi), 0.5);
+    const double h = __dmul_rn(__dsub_rn(hi, lo), 0.5);
+    for (int k = 0; k < P; ++k)
+      nodes[((int64_t)c * 3 + d) * P + k] = __dadd_rn(cc, __dmul_rn(h, cheb_point(k, degree)));
+  }
+}
+
+// Host: Chebyshev points of the 2nd kind on [-1, 1] and the barycentric basis
+// with the coincident-point guard (Eqs. (3)-(5)).
+static double host_cheb(int k, int n) {
+  if (2 * k == n) return 0.0;
+  if (2 * k < n) return std::cos(M_PI * (double)k / (double)n);
+  return -std::cos(M_PI * (double)(n - k) / (double)n);
+}
+static void host_basis(double x, int n, double* out) {
+  double sum = 0.0, r[kMaxP];
+  int hit = -1;
+  for (int k = 0; k <= n; ++k) {
+    const double d = x - host_cheb(k, n);
+    if (d == 0.0 && hit < 0) hit = k;
+    double w = (k == 0 || k == n) ? 0.5 : 1.0;
+    if (k & 1) w = -w;
+    r[k] = d == 0.0 ? 0.0 : w / d;
+    sum += r[k];
+  }
+  for (int k = 0; k <= n; ++k) out[k] = hit >= 0 ? (k == hit ? 1.0 : 0.0) : r[k] / sum;
+}
+
+int setup_degrees(bldtt_plan* p, cudaStream_t s) {
+  Counters& cnt = p->setup_counter;
+  const int m = p->deg.n - 1, nmax = p->deg.d[m];
+  p->nodes_t[m] = p->tt.nodes;
+  p->nodes_s[m] = p->st.nodes;
+  for (int i = 0; i < m; ++i) {
+    const int d = p->deg.d[i], P = d + 1;
+    BL_TRY(dalloc_n(&p->nodes_t[i], (size_t)p->tt.nclusters * 3 * P, s));
+    BL_TRY(dalloc_n(&p->nodes_s[i], (size_t)p->st.nclusters * 3 * P, s));
+    k_nodes_degree<<<nblk(p->tt.nclusters, 128), 128, 0, s>>>(p->tt.nclusters, d, p->tt.box, p->nodes_t[i]);
+    BL_LAUNCHED(cnt.launches);
+    k_nodes_degree<<<nblk(p->st.nclusters, 128), 128, 0, s>>>(p->st.nclusters, d, p->st.box, p->nodes_s[i]);
+    BL_LAUNCHED(cnt.launches);
+    std::vector<double> A((size_t)P * (nmax + 1));
+    std::vector<double> col(P);
+    for (int kp = 0; kp <= nmax; ++kp) {   // A[k][k'] = L^(d)_k(s^(nmax)_k')
+      host_basis(host_cheb(kp, nmax), d, col.data());
+      for (int k = 0; k < P; ++k) A[(size_t)k * (nmax + 1) + kp] = col[k];
+    }
+    BL_TRY(dalloc_n(&p->xfer[i], A.size(), s));
+    BL_CUDA(cudaMemcpyAsync(p->xfer[i], A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    BL_TRY(dalloc_n(&p->qhat_d[i], (size_t)p->st.nclusters * p->deg.np[i], s));
+    BL_TRY(dalloc_n(&p->phit_d[i], (size_t)p->tt.nclusters * p->deg.np[i], s));
+    BL_CUDA(cudaStreamSynchronize(s));   // the host matrix goes out of scope
+  }
   return BLDTT_OK;
 }
 

@@ -26,12 +26,6 @@ constexpr int kTreeThreads = 256;
 
 // Chebyshev point of the 2nd kind, s_k = cos(pi k / n), symmetrised so that
 // s_0 = 1, s_n = -1, s_{n-k} = -s_k and s_{n/2} = 0 (Sec. 2.1, Eq. (4)).
-__device__ __forceinline__ double cheb_point(int k, int n) {
-  if (2 * k == n) return 0.0;
-  if (2 * k < n) return cos(__ddiv_rn(__dmul_rn(M_PI, (double)k), (double)n));
-  return -cos(__ddiv_rn(__dmul_rn(M_PI, (double)(n - k)), (double)n));
-}
-
 __global__ void k_tree_init(const double* __restrict__ coords, int32_t n, double* __restrict__ x,
                             double* __restrict__ y, double* __restrict__ z,
                             int32_t* __restrict__ perm) {
