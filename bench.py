@@ -542,12 +542,163 @@ def run_gpu_batched(args):
     return 0
 
 
+def run_gpu_learned(args):
+    """1E8 uniform points, Coulomb, leaves 2000, FP32 bulk: the learned pair
+    selector (degrees 3..8, trained on the GPU on smaller problems with their
+    own seeds, per-pair budget calibrated for 1e-6) against the fixed rule
+    n=8, theta=0.7.  A step is setup + compute; errors are against the FP64
+    direct sum on 1E4 sampled targets.  `value` is the learned path's rate."""
+    import numpy as np
+    import torch
+
+    from paper_2012_06925_gb300 import binding as B
+    from paper_2012_06925_gb300 import build as builder
+    from paper_2012_06925_gb300 import selector as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    builder.build()
+    B.load_library()
+    t_train = time.perf_counter()
+    sel, report = S.train_selector(budget=1e-6, epochs=200, seed=0)
+    t_train = time.perf_counter() - t_train
+
+    cfg, tgt, src, q, kw = workload(args.workload)
+    M = tgt.shape[1]
+    dt = torch.from_numpy(tgt).cuda()
+    dq = torch.from_numpy(q).cuda()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    phi = torch.empty(M, dtype=torch.float64, device="cuda")
+    base = dict(theta=kw["theta"], N0=kw["N0"], M0=kw["M0"], precision=B.FP32_BULK, stream=stream)
+
+    def step(which):
+        if which == "learned":
+            plan = B.Plan.learned(dt, dt, dq, sel, **base)
+        else:
+            plan = B.Plan(dt, dt, dq, kernel=kw["kernel"], kappa=kw["kappa"], n=kw["n"], **base)
+        plan.compute(phi, stream=stream)
+        return plan
+
+    idx = np.random.default_rng(77).choice(M, size=10_000, replace=False)
+    idx.sort()
+    errors = {}
+    for which in ("fixed", "learned"):
+        plan = step(which)
+        plan.check_error()
+        plan.close()
+        errors[which] = S.sampled_error(tgt, q, phi.cpu().numpy(), idx)
+
+    def timed(which):
+        for _ in range(args.warmup):
+            flush.fill_(1.0)
+            step(which).close()
+        torch.cuda.synchronize()
+        times, sts = [], []
+        with ClockSampler(local) as clocks:
+            for i in range(args.steps):
+                flush.fill_(float(i))
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                plan = step(which)
+                e1.record(stream)
+                sts.append(plan.stats())
+                plan.close()
+                times.append(e0.elapsed_time(e1))
+        return sum(times), sts, clocks.summary()
+
+    if dist is not None:
+        dist.barrier()
+    total_ms, sts, csum = timed("learned")
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    fixed_ms, fsts, _ = timed("fixed")
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    st, fst = sts[-1], fsts[-1]
+    value = M * args.steps * world / (total_ms / 1000.0)
+    ms_interact = statistics.mean(s["ms_interact"] for s in sts)
+    flops = 20.0 * sum(st["interactions"])
+    achieved = flops / (ms_interact / 1000.0) / 1e12
+    props = torch.cuda.get_device_properties(local)
+    sm_max = measured_peaks().get("sm_max_mhz", 2070.0)
+    peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+
+    # End to end through the public API: pinned host inputs in, potentials out.
+    ht = torch.from_numpy(tgt).pin_memory()
+    hq = torch.from_numpy(q).pin_memory()
+    hphi = torch.empty(M, dtype=torch.float64).pin_memory()
+    e2e_times = []
+    for i in range(2):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dt2 = ht.cuda(non_blocking=True)
+        dq2 = hq.cuda(non_blocking=True)
+        plan = B.Plan.learned(dt2, dt2, dq2, sel, **base)
+        plan.compute(phi, stream=stream)
+        hphi.copy_(phi, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+        plan.close()
+        del dt2, dq2
+    e2e = {"value": M / min(e2e_times), "unit": UNIT, "h2d_bytes_per_step": int(M * 32),
+           "d2h_bytes_per_step": int(M * 8), "seconds": min(e2e_times)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(config_dict(cfg), workload=(
+            "uniform_n1e8: 1E8 uniform in [-1,1]^3, targets=sources, charges U[-1,1], Coulomb, "
+            "leaves 2000, FP32 bulk; learned selector (degrees 3..8, 6 features, 3x64 hidden, "
+            "bf16) vs fixed n=8 theta=0.7; errors vs FP64 direct on 1E4 sampled targets")),
+        "rel_l2_vs_fp64_direct": errors["learned"], "accuracy_ok": errors["learned"] <= 1e-6,
+        "fixed_rule": {"value": M * args.steps / (fixed_ms / 1000.0), "unit": UNIT,
+                       "ms_per_step": fixed_ms / args.steps,
+                       "rel_l2_vs_fp64_direct": errors["fixed"],
+                       "interactions": sum(fst["interactions"]),
+                       "phases_ms": {k: fst["ms_" + k] for k in ("tree", "lists", "upward", "interact",
+                                                                  "downward", "compute")}},
+        "speedup_vs_fixed_rule": fixed_ms / total_ms,
+        "selector": {"train_seconds": t_train, "pairs": report["pairs"], "loss": report["loss"],
+                     "log10_pair_budget": report["log_eps"], "degrees": list(sel.degrees)},
+        "phases_ms": {k: st["ms_" + k] for k in ("tree", "lists", "upward", "interact", "downward",
+                                                  "compute")},
+        "interactions": {"PP": st["interactions"][0], "PC": st["interactions"][1],
+                         "CP": st["interactions"][2], "CC": st["interactions"][3]},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_interact<FP32,Coulomb> (multi-degree)", "flops_per_launch": flops,
+                     "ms_per_launch": ms_interact},
+        "e2e": e2e, "gpu_launches": sum(s["launches_setup"] + s["launches_compute"] for s in sts),
+        "clocks": csum, "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched_512":
         return run_gpu_batched(args)
+    if args.workload == "uniform_n1e8":
+        return run_gpu_learned(args)
     return run_gpu(args)
 
 

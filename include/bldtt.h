@@ -275,7 +275,9 @@ int bldtt_mlp_adam(float* params, float* m, float* v, const float* grads, int64_
  *    features (device [npairs][6]); NaN for pairs that cannot be approximated.
  *  bldtt_pair_errors: in FP64, the relative l2 error of PC, CP and CC at each
  *    degree against the exact pair sum of Eq. (6) (the plan's kernel and
- *    charges), on min(samples, |C_t|) targets spread evenly over C_t:
+ *    charges), on min(samples, |C_t|) targets spread evenly over C_t (a
+ *    source cluster of more than 4096 particles is represented, in the exact
+ *    sum and the approximations alike, by every ceil(|C_s|/4096)-th one):
  *    err (device [npairs][num_degrees][3]).  samples <= 256, degrees in
  *    1..16 (host array of num_degrees <= 8).
  * Errors: EINVAL, ECUDA.

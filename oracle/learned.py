@@ -351,7 +351,9 @@ def pair_errors(targets, sources, charges, tt, st, t, s, degrees, positions, ker
                 kappa=0.0):
     """Relative l2 error of PC, CP and CC at each degree against the exact
     pair sum (Eq. (6)), on the target tree positions `positions` of C_t.
-    Returns an array (len(degrees), 3)."""
+    Returns an array (len(degrees), 3).  (The GPU labels represent a source
+    cluster of more than 4096 particles by a strided subset; this oracle
+    always uses the whole cluster, so it pins clusters up to that size.)"""
     xs = np.asarray(targets, dtype=np.float64)[:, tt.perm]
     ys = np.asarray(sources, dtype=np.float64)[:, st.perm]
     qs = np.asarray(charges, dtype=np.float64)[st.perm]

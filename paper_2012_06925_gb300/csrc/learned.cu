@@ -396,6 +396,7 @@ __device__ void basis(double x, const double* nodes, int n, double* out, int str
 
 constexpr int kErrThreads = 256;
 constexpr int kErrChunk = 32;
+constexpr int kErrMaxSources = 4096;   // larger source clusters: an evenly strided subset
 
 struct ErrTrees {
   const int32_t *tb, *te, *sb, *se;
@@ -405,7 +406,10 @@ struct ErrTrees {
 
 // One block per (pair, degree): the relative l2 errors of PC, CP and CC at
 // degree d against the exact pair sum (Eq. (6)), on up to S target samples
-// spread evenly over C_t.  err[(pair * ndeg + di) * 3 + type].
+// spread evenly over C_t.  A source cluster of more than kErrMaxSources
+// particles is represented by every stride-th particle (stride =
+// ceil(|C_s| / kErrMaxSources)) in the exact sum and in all three
+// approximations alike.  err[(pair * ndeg + di) * 3 + type].
 template <int KERN>
 __global__ void __launch_bounds__(kErrThreads) k_pair_errors(const int32_t* __restrict__ pairs, int64_t npairs,
                                                             ErrTrees T, DegreeSet deg, int S, double kappa,
@@ -417,7 +421,9 @@ __global__ void __launch_bounds__(kErrThreads) k_pair_errors(const int32_t* __re
   if (pi >= npairs) return;
   const int t = pairs[2 * pi], s = pairs[2 * pi + 1];
   const int d = deg.d[di], P = d + 1, np = P * P * P;
-  const int32_t tb = T.tb[t], nt = T.te[t] - tb, sb = T.sb[s], ns = T.se[s] - sb;
+  const int32_t tb = T.tb[t], nt = T.te[t] - tb, sb = T.sb[s], ns_all = T.se[s] - sb;
+  const int32_t sst = (ns_all + kErrMaxSources - 1) / kErrMaxSources;   // source stride
+  const int32_t ns = (ns_all + sst - 1) / sst;                          // sources used
   const int m = nt < S ? nt : S;
   double* tn = sm;                     // [3][P] target nodes
   double* sn = tn + 3 * P;             // [3][P] source nodes
@@ -447,7 +453,7 @@ __global__ void __launch_bounds__(kErrThreads) k_pair_errors(const int32_t* __re
       const int dd = task / kErrChunk, j = task % kErrChunk;
       const double* crd = dd == 0 ? T.sx : (dd == 1 ? T.sy : T.sz);
       if (j < cnt)
-        basis(crd[sb + base + j], sn + dd * P, d, Bj + (dd * P) * kErrChunk + j, kErrChunk);
+        basis(crd[sb + (int64_t)(base + j) * sst], sn + dd * P, d, Bj + (dd * P) * kErrChunk + j, kErrChunk);
       else
         for (int k = 0; k < P; ++k) Bj[(dd * P + k) * kErrChunk + j] = 0.0;
     }
@@ -457,7 +463,7 @@ __global__ void __launch_bounds__(kErrThreads) k_pair_errors(const int32_t* __re
       double a = 0.0;
       for (int j = 0; j < cnt; ++j)
         a += Bj[k1 * kErrChunk + j] * Bj[(P + k2) * kErrChunk + j] * Bj[(2 * P + k3) * kErrChunk + j] *
-             T.q[sb + base + j];
+             T.q[sb + (int64_t)(base + j) * sst];
       qh[o] += a;
     }
     __syncthreads();
@@ -474,8 +480,10 @@ __global__ void __launch_bounds__(kErrThreads) k_pair_errors(const int32_t* __re
     const int64_t pos = tb + (int64_t)i * nt / m;
     const double x = T.tx[pos], y = T.ty[pos], z = T.tz[pos];
     double ex = 0.0, pc = 0.0;
-    for (int j = lane; j < ns; j += 32)
-      ex += g64<KERN>(x - T.sx[sb + j], y - T.sy[sb + j], z - T.sz[sb + j], kappa) * T.q[sb + j];
+    for (int j = lane; j < ns; j += 32) {
+      const int64_t y0 = sb + (int64_t)j * sst;
+      ex += g64<KERN>(x - T.sx[y0], y - T.sy[y0], z - T.sz[y0], kappa) * T.q[y0];
+    }
     for (int o = lane; o < np; o += 32) {
       const int k1 = o / (P * P), k2 = (o / P) % P, k3 = o % P;
       pc += g64<KERN>(x - sn[k1], y - sn[P + k2], z - sn[2 * P + k3], kappa) * qh[o];
@@ -494,8 +502,10 @@ __global__ void __launch_bounds__(kErrThreads) k_pair_errors(const int32_t* __re
     const int k1 = o / (P * P), k2 = (o / P) % P, k3 = o % P;
     const double x = tn[k1], y = tn[P + k2], z = tn[2 * P + k3];
     double cp = 0.0, cc = 0.0;
-    for (int j = 0; j < ns; ++j)
-      cp += g64<KERN>(x - T.sx[sb + j], y - T.sy[sb + j], z - T.sz[sb + j], kappa) * T.q[sb + j];
+    for (int j = 0; j < ns; ++j) {
+      const int64_t y0 = sb + (int64_t)j * sst;
+      cp += g64<KERN>(x - T.sx[y0], y - T.sy[y0], z - T.sz[y0], kappa) * T.q[y0];
+    }
     for (int r = 0; r < np; ++r) {
       const int r1 = r / (P * P), r2 = (r / P) % P, r3 = r % P;
       cc += g64<KERN>(x - sn[r1], y - sn[P + r2], z - sn[2 * P + r3], kappa) * qh[r];

@@ -1,0 +1,53 @@
+"""What the trained selector gains over the method without it.
+
+The selector is trained on the GPU (labels from the library's FP64 pair-error
+kernel on training problems with their own seeds, the library's training
+kernels, a per-pair budget calibrated on another problem), then used on a
+held-out problem: 1E6 uniform points, Coulomb, leaves of 2000, FP32 bulk.
+Against the fixed rule of the paper (n = 8, theta = 0.7) it must meet the
+same 1e-6 budget against the FP64 direct sum while doing clearly less work."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2012_06925_gb300 import binding as B
+from paper_2012_06925_gb300 import selector as S
+from paper_2012_06925_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def trained():
+    sel, report = S.train_selector(budget=1e-6, epochs=150, seed=0)
+    return sel, report
+
+
+def test_training_converges(trained):
+    sel, report = trained
+    assert report["pairs"] > 10_000
+    assert report["loss"] < 1.0                      # mean squared error in decades^2
+    # a looser per-pair budget buys less work and a larger error
+    table = sorted(report["calibration"])
+    assert table[-1][2] < table[0][2] and table[-1][1] > table[0][1]
+
+
+def test_learned_selector_beats_the_fixed_rule(trained):
+    sel, _ = trained
+    t, _, q = W.make_problem("uniform", 1_000_000, seed=2)
+    dt, dq = torch.from_numpy(t).cuda(), torch.from_numpy(q).cuda()
+    idx = np.random.default_rng(9).choice(t.shape[1], 2000, replace=False)
+    out = {}
+    for name in ("fixed", "learned"):
+        if name == "fixed":
+            plan = B.Plan(dt, dt, dq, n=8, theta=0.7, N0=2000, M0=2000, precision=B.FP32_BULK)
+        else:
+            plan = B.Plan.learned(dt, dt, dq, sel, theta=0.7, N0=2000, M0=2000, precision=B.FP32_BULK)
+        with plan:
+            phi = plan.compute().cpu().numpy()
+            plan.check_error()
+            st = plan.stats()
+        out[name] = (S.sampled_error(t, q, phi, idx), sum(st["interactions"]), st["ms_interact"])
+    (e_fix, w_fix, _), (e_learn, w_learn, _) = out["fixed"], out["learned"]
+    assert e_fix <= 1e-6 and e_learn <= 1e-6
+    assert w_learn <= 0.8 * w_fix, (w_learn, w_fix)
