@@ -42,6 +42,49 @@ __device__ __forceinline__ void basis_1d(double x, const double* nodes, int n, T
   }
 }
 
+// FP32_BULK form of the same basis: x and the nodes are split into float
+// pairs (hi = fl(v), lo = fl(v - hi)), so d_k = (x_hi - t_hi) + (x_lo - t_lo)
+// is x - t_k to within u |d_k| + u^2 |x|; d_k == 0 (x and t_k equal to ~48
+// bits) takes the guard.  The weights are exact; the quotients and their sum
+// are float.  nodes_hl: [2][n+1] (hi row, lo row).
+__device__ __forceinline__ void basis_1d_f32(double x, const float* nodes_hl, int n, float* out,
+                                             int stride) {
+  float xh, xl;
+  split_f64(x, xh, xl);
+  float r[kMaxP];
+  int hit = -1;
+  float sum = 0.f;
+#pragma unroll
+  for (int k = 0; k < kMaxP; ++k) {
+    if (k <= n) {
+      const float d = __fadd_rn(__fsub_rn(xh, nodes_hl[k]), __fsub_rn(xl, nodes_hl[kMaxP + k]));
+      if (d == 0.f && hit < 0) hit = k;
+      r[k] = d == 0.f ? 0.f : __fdividef((float)bary_weight(k, n), d);
+      sum += r[k];
+    }
+  }
+  const float inv = __fdividef(1.f, sum);
+#pragma unroll
+  for (int k = 0; k < kMaxP; ++k) {
+    if (k <= n) out[k * stride] = hit >= 0 ? (k == hit ? 1.f : 0.f) : r[k] * inv;
+  }
+}
+
+// Compensated float sum of products: s + c carries sum a_i b_i with the
+// rounding errors of every product (FMA) and every addition (TwoSum).
+struct CompSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float pe = __fmaf_rn(a, b, -p);
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    c = __fadd_rn(c, __fadd_rn(e, pe));
+    s = t;
+  }
+};
+
 // ---------------------------------------------------------------------------
 // Charges into source tree order
 // ---------------------------------------------------------------------------
@@ -76,12 +119,20 @@ __global__ void __launch_bounds__(kUpThreads) k_up_leaf(
     int n, double* __restrict__ qhat) {
   using T = typename std::conditional<F32, float, double>::type;
   __shared__ double snodes[3][kMaxP];
+  __shared__ float shl[3][2 * kMaxP];          // FP32_BULK: float split of the nodes
   __shared__ T sB[3][kMaxP][kUpStride];
   __shared__ T sq[kUpChunk];
   const int P = n + 1, np = P * P * P;
   const int c = leaf_ids[blockIdx.x];
   const int32_t b = begin[c], e = end[c];
-  if (threadIdx.x < 3 * P) snodes[threadIdx.x / P][threadIdx.x % P] = nodes[(int64_t)c * 3 * P + threadIdx.x];
+  if (threadIdx.x < 3 * P) {
+    const double v = nodes[(int64_t)c * 3 * P + threadIdx.x];
+    snodes[threadIdx.x / P][threadIdx.x % P] = v;
+    float h, l;
+    split_f64(v, h, l);
+    shl[threadIdx.x / P][threadIdx.x % P] = h;
+    shl[threadIdx.x / P][kMaxP + threadIdx.x % P] = l;
+  }
   double acc[kMaxOutPerThread];
 #pragma unroll
   for (int r = 0; r < kMaxOutPerThread; ++r) acc[r] = 0.0;
@@ -92,7 +143,10 @@ __global__ void __launch_bounds__(kUpThreads) k_up_leaf(
     for (int task = threadIdx.x; task < 3 * kUpChunk; task += kUpThreads) {
       int d = task / kUpChunk, j = task % kUpChunk;
       if (j < cnt) {
-        basis_1d<T>(coord[d][base + j], snodes[d], n, &sB[d][0][j], kUpStride);
+        if constexpr (F32)
+          basis_1d_f32(coord[d][base + j], shl[d], n, &sB[d][0][j], kUpStride);
+        else
+          basis_1d<T>(coord[d][base + j], snodes[d], n, &sB[d][0][j], kUpStride);
       } else {
         for (int k = 0; k < P; ++k) sB[d][k][j] = (T)0;
       }
@@ -572,27 +626,57 @@ __global__ void __launch_bounds__(kDownThreads) k_down_leaf(
   double* sL = snodes + 3 * P;                              // [threads][stride]
   T* sphi = reinterpret_cast<T*>(sL + (size_t)kDownThreads * stride);   // [np]
   T* sLz = sphi + np;                                       // [threads][tstride] z factors in T
+  float* shl = reinterpret_cast<float*>(sLz + (size_t)kDownThreads * tstride);   // [3][2][kMaxP]
   const int c = leaf_ids[blockIdx.x];
-  for (int t = threadIdx.x; t < 3 * P; t += blockDim.x) snodes[t] = nodes[(int64_t)c * 3 * P + t];
+  for (int t = threadIdx.x; t < 3 * P; t += blockDim.x) {
+    const double v = nodes[(int64_t)c * 3 * P + t];
+    snodes[t] = v;
+    float h, l;
+    split_f64(v, h, l);
+    shl[(t / P) * 2 * kMaxP + t % P] = h;
+    shl[(t / P) * 2 * kMaxP + kMaxP + t % P] = l;
+  }
   for (int o = threadIdx.x; o < np; o += blockDim.x) sphi[o] = (T)phit[(int64_t)c * np + o];
   __syncthreads();
   double* L = sL + (size_t)threadIdx.x * stride;
+  float* Lf = reinterpret_cast<float*>(L);                  // FP32_BULK: the basis in float
   for (int32_t i = begin[c] + threadIdx.x; i < end[c]; i += blockDim.x) {
-    basis_1d<double>(x[i], snodes, n, L, 1);
-    basis_1d<double>(y[i], snodes + P, n, L + P, 1);
-    basis_1d<double>(z[i], snodes + 2 * P, n, L + 2 * P, 1);
     T* Lz = sLz + (size_t)threadIdx.x * tstride;
-    for (int k3 = 0; k3 < P; ++k3) Lz[k3] = (T)L[2 * P + k3];
     double acc = 0.0;
-    for (int k1 = 0; k1 < P; ++k1) {
-      double s1 = 0.0;
-      for (int k2 = 0; k2 < P; ++k2) {
-        const T* row = sphi + (k1 * P + k2) * P;
-        T s2 = (T)0;
-        for (int k3 = 0; k3 < P; ++k3) s2 += Lz[k3] * row[k3];
-        s1 += L[P + k2] * (double)s2;
+    if constexpr (F32) {
+      basis_1d_f32(x[i], shl, n, Lf, 1);
+      basis_1d_f32(y[i], shl + 2 * kMaxP, n, Lf + P, 1);
+      basis_1d_f32(z[i], shl + 4 * kMaxP, n, Lz, 1);
+      // s2 in float; the two outer sums compensated (exact products by FMA,
+      // exact sums by TwoSum), so they add no rounding beyond s2's own.
+      CompSum a1;
+      for (int k1 = 0; k1 < P; ++k1) {
+        CompSum a2;
+        for (int k2 = 0; k2 < P; ++k2) {
+          const T* row = sphi + (k1 * P + k2) * P;
+          T s2 = (T)0;
+          for (int k3 = 0; k3 < P; ++k3) s2 += Lz[k3] * row[k3];
+          a2.add_prod(Lf[P + k2], (float)s2);
+        }
+        a1.add_prod(Lf[k1], a2.s);
+        a1.add_prod(Lf[k1], a2.c);
       }
-      acc += L[k1] * s1;
+      acc = (double)a1.s + (double)a1.c;
+    } else {
+      basis_1d<double>(x[i], snodes, n, L, 1);
+      basis_1d<double>(y[i], snodes + P, n, L + P, 1);
+      basis_1d<double>(z[i], snodes + 2 * P, n, L + 2 * P, 1);
+      for (int k3 = 0; k3 < P; ++k3) Lz[k3] = (T)L[2 * P + k3];
+      for (int k1 = 0; k1 < P; ++k1) {
+        double s1 = 0.0;
+        for (int k2 = 0; k2 < P; ++k2) {
+          const T* row = sphi + (k1 * P + k2) * P;
+          T s2 = (T)0;
+          for (int k3 = 0; k3 < P; ++k3) s2 += Lz[k3] * row[k3];
+          s1 += L[P + k2] * (double)s2;
+        }
+        acc += L[k1] * s1;
+      }
     }
     phi_user[perm[i]] = phi_near[i] + acc;
   }
@@ -618,12 +702,14 @@ int downward_pass(bldtt_plan* p, double* phi_user, cudaStream_t s) {
   const int stride = 3 * P + ((3 * P) % 2 == 0 ? 1 : 0);
   const size_t tz = (size_t)kDownThreads * (P | 1);
   if (p->precision == BLDTT_FP32_BULK) {
-    size_t bytes = sizeof(double) * (3 * P + (size_t)kDownThreads * stride) + sizeof(float) * (np + tz);
+    size_t bytes = sizeof(double) * (3 * P + (size_t)kDownThreads * stride) + sizeof(float) * (np + tz) +
+                   sizeof(float) * 6 * kMaxP;
     k_down_leaf<true><<<T.nleaves, kDownThreads, bytes, s>>>(T.leaf_ids, T.begin, T.end, T.x, T.y,
                                                               T.z, T.perm, T.nodes, p->n, p->phit,
                                                               p->phi_near, phi_user);
   } else {
-    size_t bytes = sizeof(double) * (3 * P + (size_t)kDownThreads * stride + np + tz);
+    size_t bytes = sizeof(double) * (3 * P + (size_t)kDownThreads * stride + np + tz) +
+                   sizeof(float) * 6 * kMaxP;
     k_down_leaf<false><<<T.nleaves, kDownThreads, bytes, s>>>(T.leaf_ids, T.begin, T.end, T.x, T.y,
                                                                T.z, T.perm, T.nodes, p->n, p->phit,
                                                                p->phi_near, phi_user);
