@@ -23,6 +23,7 @@ namespace bldtt {
 
 constexpr int kTreeChunk = 2048;
 constexpr int kTreeThreads = 256;
+static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // Chebyshev point of the 2nd kind, s_k = cos(pi k / n), symmetrised so that
 // s_0 = 1, s_n = -1, s_{n-k} = -s_k and s_{n/2} = 0 (Sec. 2.1, Eq. (4)).
@@ -296,20 +297,37 @@ __global__ void k_tree_scatter(int32_t ls, const int32_t* __restrict__ chunk_clu
 }
 
 // Shrink every new cluster to the bounding box of its particles (Sec. 2.3):
-// each cluster is cut into `slices` slices (up to kBoxSlices, chosen per level
-// from the average cluster size) reduced by separate CTAs, then one warp per
-// cluster combines the slices.  Min/max are exact, so the result does not
-// depend on the split.
-constexpr int kBoxSlices = 32;
+// every cluster is cut into slices of kBoxSlice particles (at least one), one
+// CTA per slice (the slice's cluster found by binary search in the prefix of
+// slice counts, which stays on the device), then one warp per cluster
+// combines its slices.  Min/max are exact, so the result does not depend on
+// the cut.  Slices per cluster follow its own size, so one very populous
+// cluster (a Plummer core) still spreads over many CTAs.
+constexpr int kBoxSlice = 8192;
 
-__global__ void k_tree_child_bbox(int32_t first, const int32_t* __restrict__ begin,
+__global__ void k_box_slices(int32_t first, int32_t nc, const int32_t* __restrict__ begin,
+                             const int32_t* __restrict__ end, int32_t* __restrict__ nslice) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nc) return;
+  const int32_t cnt = end[first + j] - begin[first + j];
+  nslice[j] = cnt > kBoxSlice ? (cnt + kBoxSlice - 1) / kBoxSlice : 1;
+}
+
+__global__ void k_tree_child_bbox(int32_t first, int32_t nc, const int32_t* __restrict__ slice_off,
+                                  const int32_t* __restrict__ nslice, const int32_t* __restrict__ begin,
                                   const int32_t* __restrict__ end, const double* __restrict__ x,
                                   const double* __restrict__ y, const double* __restrict__ z,
                                   double* __restrict__ part) {
-  const int c = first + blockIdx.x;
-  const int32_t b = begin[c], cnt = end[c] - b;
-  const int32_t len = (cnt + gridDim.y - 1) / gridDim.y;
-  const int32_t s0 = b + blockIdx.y * len, s1 = min(s0 + len, b + cnt);
+  const int32_t b = blockIdx.x;
+  if (b >= slice_off[nc - 1] + nslice[nc - 1]) return;
+  int lo_j = 0, hi_j = nc;   // last cluster whose first slice is <= b
+  while (hi_j - lo_j > 1) {
+    const int m = (lo_j + hi_j) >> 1;
+    if (slice_off[m] <= b) lo_j = m; else hi_j = m;
+  }
+  const int c = first + lo_j;
+  const int32_t s0 = begin[c] + (b - slice_off[lo_j]) * kBoxSlice;
+  const int32_t s1 = min(end[c], s0 + kBoxSlice);
   double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   for (int32_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
     double v[3] = {x[i], y[i], z[i]};
@@ -335,23 +353,51 @@ __global__ void k_tree_child_bbox(int32_t first, const int32_t* __restrict__ beg
     double r = sm[0][threadIdx.x];
     for (int w = 1; w < kTreeThreads / 32; ++w)
       r = threadIdx.x < 3 ? fmin(r, sm[w][threadIdx.x]) : fmax(r, sm[w][threadIdx.x]);
-    part[((int64_t)blockIdx.x * gridDim.y + blockIdx.y) * 6 + threadIdx.x] = r;
+    part[(int64_t)b * 6 + threadIdx.x] = r;
   }
 }
 
-__global__ void k_tree_child_bbox_combine(int32_t first, int32_t nc, int slices,
+__global__ void k_tree_child_bbox_combine(int32_t first, int32_t nc, const int32_t* __restrict__ slice_off,
+                                          const int32_t* __restrict__ nslice,
                                           const double* __restrict__ part, double* __restrict__ box) {
   const int j = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (j >= nc) return;
+  const int32_t p0 = slice_off[j], ns = nslice[j];
   for (int k = 0; k < 6; ++k) {
-    double r = lane < slices ? part[((int64_t)j * slices + lane) * 6 + k] : (k < 3 ? INFINITY : -INFINITY);
+    double r = k < 3 ? INFINITY : -INFINITY;
+    for (int32_t t = lane; t < ns; t += 32) {
+      const double v = part[(int64_t)(p0 + t) * 6 + k];
+      r = k < 3 ? fmin(r, v) : fmax(r, v);
+    }
     for (int off = 16; off; off >>= 1) {
       double o = __shfl_down_sync(0xffffffffu, r, off);
       r = k < 3 ? fmin(r, o) : fmax(r, o);
     }
     if (lane == 0) box[(int64_t)(first + j) * 6 + k] = r;
   }
+}
+
+// Bounding boxes of the nc clusters [first, first + nc) of a tree of n particles.
+static int cluster_boxes(Tree& T, int32_t first, int32_t nc, int32_t n, cudaStream_t s, Counters& cnt) {
+  int32_t *nslice = nullptr, *slice_off = nullptr;
+  double* part = nullptr;
+  const int64_t bound = (int64_t)n / kBoxSlice + nc + 1;   // slices <= n / kBoxSlice + nc
+  BL_TRY(dalloc_n(&nslice, nc, s));
+  BL_TRY(dalloc_n(&slice_off, nc, s));
+  BL_TRY(dalloc_n(&part, (size_t)bound * 6, s));
+  k_box_slices<<<nblk(nc, 128), 128, 0, s>>>(first, nc, T.begin, T.end, nslice);
+  BL_LAUNCHED(cnt.launches);
+  BL_TRY(scan_exclusive(nslice, slice_off, nc, nullptr, s, cnt));
+  k_tree_child_bbox<<<(unsigned)bound, kTreeThreads, 0, s>>>(first, nc, slice_off, nslice, T.begin, T.end,
+                                                             T.x, T.y, T.z, part);
+  BL_LAUNCHED(cnt.launches);
+  k_tree_child_bbox_combine<<<nblk(nc, 4), 128, 0, s>>>(first, nc, slice_off, nslice, part, T.box);
+  BL_LAUNCHED(cnt.launches);
+  dfree(part, s);
+  dfree(slice_off, s);
+  dfree(nslice, s);
+  return BLDTT_OK;
 }
 
 // Centre = box centre, radius = half the diagonal, proxy points c + h s_k.
@@ -410,7 +456,6 @@ static int grow_clusters(Tree& T, size_t need, size_t keep, cudaStream_t s) {
   return BLDTT_OK;
 }
 
-static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 int build_tree(Tree& T, const double* coords, int32_t n, const std::vector<int32_t>& roots,
                int32_t max_leaf, int degree, int* bad_dev, cudaStream_t s, Counters& cnt) {
@@ -443,16 +488,7 @@ int build_tree(Tree& T, const double* coords, int32_t n, const std::vector<int32
     BL_TRY(check_finite(T.y, n, bad_dev, s, cnt));
     BL_TRY(check_finite(T.z, n, bad_dev, s, cnt));
     // root boxes: the minimal bounding box of each problem's particles (Sec. 2.3)
-    int64_t per = (int64_t)n / nroots;
-    int slices = (int)std::min<int64_t>(32, std::max<int64_t>(1, per / 16384));
-    double* part = nullptr;
-    BL_TRY(dalloc_n(&part, (size_t)nroots * slices * 6, s));
-    k_tree_child_bbox<<<dim3(nroots, slices), kTreeThreads, 0, s>>>(0, T.begin, T.end, T.x, T.y,
-                                                                    T.z, part);
-    BL_LAUNCHED(cnt.launches);
-    k_tree_child_bbox_combine<<<nblk(nroots, 4), 128, 0, s>>>(0, nroots, slices, part, T.box);
-    BL_LAUNCHED(cnt.launches);
-    dfree(part, s);
+    BL_TRY(cluster_boxes(T, 0, nroots, n, s, cnt));
     dfree(d_roots, s);
   }
 
@@ -512,17 +548,7 @@ int build_tree(Tree& T, const double* coords, int32_t n, const std::vector<int32
     { double* t = T.y; T.y = y2; y2 = t; }
     { double* t = T.z; T.z = z2; z2 = t; }
     { int32_t* t = T.perm; T.perm = perm2; perm2 = t; }
-    // slices per new cluster: about 16K particles each, at most kBoxSlices
-    int64_t per = (int64_t)n / nc;
-    int slices = (int)std::min<int64_t>(kBoxSlices, std::max<int64_t>(1, per / 16384));
-    double* part = nullptr;
-    BL_TRY(dalloc_n(&part, (size_t)nc * slices * 6, s));
-    k_tree_child_bbox<<<dim3(nc, slices), kTreeThreads, 0, s>>>(le, T.begin, T.end, T.x, T.y, T.z,
-                                                                part);
-    BL_LAUNCHED(cnt.launches);
-    k_tree_child_bbox_combine<<<nblk(nc, 4), 128, 0, s>>>(le, nc, slices, part, T.box);
-    BL_LAUNCHED(cnt.launches);
-    dfree(part, s);
+    BL_TRY(cluster_boxes(T, le, nc, n, s, cnt));
     T.level_start.push_back(le + nc);
     dfree(splitmask, s); dfree(mid, s); dfree(nchunks, s); dfree(chunk_off, s);
     dfree(chunk_cluster, s); dfree(chunk_start, s); dfree(counts, s); dfree(chunk_base, s);
