@@ -71,7 +71,7 @@ void release(bldtt_plan* p) {
   if (!p) return;
   cudaStream_t s = p->stream;
   free_tree(p->tt, s);
-  free_tree(p->st, s);
+  if (!p->shared_tree) free_tree(p->st, s);
   dfree_ptr(p->q_tree, s);
   dfree_ptr(p->list_ptr, s);
   dfree_ptr(p->list_src, s);
@@ -141,12 +141,20 @@ int setup_impl(bldtt_plan* p, const double* targets, const double* sources, cons
   BL_TRY(dalloc_n(&bad, 1, s));
   BL_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
   BL_CUDA(cudaEventRecord(p->ev[0], s));
+  // Targets that are the sources, with the same leaf size and problem
+  // offsets, give two identical trees (the build is deterministic): build one
+  // and let the source tree alias it.
+  p->shared_tree = targets == sources && p->M == p->N && p->M0 == p->N0 && p->t_off == p->s_off;
   BL_TRY(build_tree(p->tt, targets, (int32_t)p->M, p->t_off, p->M0, p->n, bad, s,
                     p->setup_counter));
-  BL_TRY(build_tree(p->st, sources, (int32_t)p->N, p->s_off, p->N0, p->n, bad, s,
-                    p->setup_counter));
-  BL_TRY(morton_order_leaves(p->tt, s, p->setup_counter));
-  BL_TRY(morton_order_leaves(p->st, s, p->setup_counter));
+  BL_TRY(morton_order_leaves(p->tt, p->M0, s, p->setup_counter));
+  if (p->shared_tree) {
+    p->st = p->tt;
+  } else {
+    BL_TRY(build_tree(p->st, sources, (int32_t)p->N, p->s_off, p->N0, p->n, bad, s,
+                      p->setup_counter));
+    BL_TRY(morton_order_leaves(p->st, p->N0, s, p->setup_counter));
+  }
   BL_TRY(dalloc_n(&p->q_tree, p->N, s));
   BL_TRY(permute_charges(p, charges, s));
   BL_TRY(check_finite(p->q_tree, p->N, bad, s, p->setup_counter));

@@ -107,19 +107,27 @@ __global__ void k_key_hist(const uint32_t* __restrict__ keys, int64_t n, int32_t
   if (i < n) atomicAdd(&cnt[keys[i]], 1);
 }
 
-// Kernel evaluations per list class (Eqs. (6), (8), (12), (15)); integer sums, exact.
+// Kernel evaluations per list class (Eqs. (6), (8), (12), (15)); integer sums,
+// exact.  Each CTA sums its entries per class in shared memory first, so the
+// global counters see one atomic per class and CTA.
 __global__ void k_count_evals(const int32_t* __restrict__ et, const int32_t* __restrict__ es,
                               const uint32_t* __restrict__ key, int64_t n, int32_t nct,
                               TreeView tt, TreeView st, DegreeSet deg,
                               unsigned long long* __restrict__ out) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int c = (int)(key[i] / (uint32_t)nct);
-  const int type = class_type(c);
-  const int64_t np = deg.np[class_degree(c)];
-  int64_t ct = tt.end[et[i]] - tt.begin[et[i]], cs = st.end[es[i]] - st.begin[es[i]];
-  int64_t v = type == BLDTT_PP ? ct * cs : type == BLDTT_PC ? ct * np : type == BLDTT_CP ? np * cs : np * np;
-  atomicAdd(&out[c], (unsigned long long)v);
+  __shared__ unsigned long long part[kMaxClasses];
+  if (threadIdx.x < kMaxClasses) part[threadIdx.x] = 0ull;
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const int c = (int)(key[i] / (uint32_t)nct);
+    const int type = class_type(c);
+    const int64_t np = deg.np[class_degree(c)];
+    int64_t ct = tt.end[et[i]] - tt.begin[et[i]], cs = st.end[es[i]] - st.begin[es[i]];
+    int64_t v = type == BLDTT_PP ? ct * cs : type == BLDTT_PC ? ct * np : type == BLDTT_CP ? np * cs : np * np;
+    atomicAdd(&part[c], (unsigned long long)v);
+  }
+  __syncthreads();
+  if (threadIdx.x < kMaxClasses && part[threadIdx.x]) atomicAdd(&out[threadIdx.x], part[threadIdx.x]);
 }
 
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -170,9 +178,16 @@ int build_lists(bldtt_plan* p, cudaStream_t s) {
                                                 p->variant, choice, nkids, isentry, action);
     BL_LAUNCHED(cnt.launches);
     if (choice) dfree(choice, s);
-    int32_t K = 0, En = 0;
-    BL_TRY(scan_exclusive(nkids, koff, F, &K, s, cnt));
-    BL_TRY(scan_exclusive(isentry, eoff, F, &En, s, cnt));
+    // both prefix sums first, then one synchronisation for both totals
+    BL_TRY(scan_exclusive(nkids, koff, F, nullptr, s, cnt));
+    BL_TRY(scan_exclusive(isentry, eoff, F, nullptr, s, cnt));
+    int32_t last[4];
+    BL_CUDA(cudaMemcpyAsync(&last[0], koff + F - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    BL_CUDA(cudaMemcpyAsync(&last[1], nkids + F - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    BL_CUDA(cudaMemcpyAsync(&last[2], eoff + F - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    BL_CUDA(cudaMemcpyAsync(&last[3], isentry + F - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    BL_CUDA(cudaStreamSynchronize(s));
+    const int32_t K = last[0] + last[1], En = last[2] + last[3];
     if ((size_t)K > ncap) {
       size_t c = ncap;
       BL_TRY(dgrow(&next, &c, (size_t)K, 0, s));

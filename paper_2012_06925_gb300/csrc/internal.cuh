@@ -186,6 +186,7 @@ struct bldtt_plan {
   cudaStream_t stream = nullptr;      // stream of the last call (for synchronisation)
 
   bldtt::Tree tt, st;                 // target and source trees
+  bool shared_tree = false;           // st aliases tt (targets are the sources)
   // Degrees (bldtt::DegreeSet); n above is the highest.  Per degree index i
   // below the highest: proxy nodes of both trees [C][3][d+1], the proxy
   // charges and potentials [C][np], and the (d+1) x (n+1) matrix
@@ -281,7 +282,7 @@ int check_finite(const double* v, int64_t n, int* bad_dev, cudaStream_t s, Count
 int build_tree(Tree& T, const double* coords_user, int32_t n, const std::vector<int32_t>& roots,
                int32_t max_leaf, int degree, int* bad_dev, cudaStream_t s, Counters& c);
 // Reorder the particles inside every leaf along a Morton curve of the leaf's box.
-int morton_order_leaves(Tree& T, cudaStream_t s, Counters& c);
+int morton_order_leaves(Tree& T, int32_t max_leaf, cudaStream_t s, Counters& c);
 void free_tree(Tree& T, cudaStream_t s);
 
 // ---- traversal, lists and work items (dtt.cu) ----

@@ -459,44 +459,39 @@ __device__ __forceinline__ void store_chunk(float4* info, int64_t q, const doubl
   info[kChunkInfo * q + 1] = make_float4(ef[0], ef[1], ef[2], tau);
 }
 
-__global__ void k_frames_particles(int32_t nleaves, const int32_t* __restrict__ leaf_ids,
-                                   const int32_t* __restrict__ begin, const int32_t* __restrict__ end,
-                                   const int32_t* __restrict__ pad_prefix, const double* __restrict__ x,
-                                   const double* __restrict__ y, const double* __restrict__ z,
-                                   float4* __restrict__ frame) {
-  // one warp per chunk
-  const int64_t q = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+// One CTA per source leaf, one warp per chunk of the leaf's pool segment.
+__global__ void k_frames_particles(const int32_t* __restrict__ leaf_ids, const int32_t* __restrict__ begin,
+                                   const int32_t* __restrict__ end, const int32_t* __restrict__ pad_prefix,
+                                   const double* __restrict__ x, const double* __restrict__ y,
+                                   const double* __restrict__ z, float4* __restrict__ frame) {
+  const int lf = blockIdx.x;
+  const int c = leaf_ids[lf];
+  const int64_t q0 = pad_prefix[lf] / kChunk, q1 = pad_prefix[lf + 1] / kChunk;
   const int lane = threadIdx.x & 31;
-  const int64_t first = q * kChunk;
-  if (first >= pad_prefix[nleaves]) return;
-  int lo = 0, hi = nleaves;   // leaf holding pool entry `first`
-  while (hi - lo > 1) {
-    int m = (lo + hi) >> 1;
-    if (pad_prefix[m] <= first) lo = m; else hi = m;
-  }
-  const int c = leaf_ids[lo];
-  const int64_t b = begin[c] + (first - pad_prefix[lo]);
-  const int64_t e = min((int64_t)end[c], b + kChunk);
-  double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-  for (int64_t i = b + lane; i < e; i += 32) {
-    double v[3] = {x[i], y[i], z[i]};
-    for (int d = 0; d < 3; ++d) {
-      mn[d] = fmin(mn[d], v[d]);
-      mx[d] = fmax(mx[d], v[d]);
+  for (int64_t q = q0 + (threadIdx.x >> 5); q < q1; q += blockDim.x >> 5) {
+    const int64_t b = begin[c] + (q - q0) * kChunk;
+    const int64_t e = min((int64_t)end[c], b + kChunk);
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = b + lane; i < e; i += 32) {
+      double v[3] = {x[i], y[i], z[i]};
+      for (int d = 0; d < 3; ++d) {
+        mn[d] = fmin(mn[d], v[d]);
+        mx[d] = fmax(mx[d], v[d]);
+      }
     }
-  }
-  for (int d = 0; d < 3; ++d)
-    for (int off = 16; off; off >>= 1) {
-      mn[d] = fmin(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], off));
-      mx[d] = fmax(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], off));
+    for (int d = 0; d < 3; ++d)
+      for (int off = 16; off; off >>= 1) {
+        mn[d] = fmin(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], off));
+        mx[d] = fmax(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], off));
+      }
+    if (lane == 0) {
+      double c3[3], e3[3];
+      for (int d = 0; d < 3; ++d) {
+        c3[d] = b < e ? 0.5 * (mn[d] + mx[d]) : 0.0;
+        e3[d] = b < e ? 0.5 * (mx[d] - mn[d]) : 0.0;
+      }
+      store_chunk(frame, q, c3, e3, (int)(e > b ? e - b : 0), true);
     }
-  if (lane == 0) {
-    double c3[3], e3[3];
-    for (int d = 0; d < 3; ++d) {
-      c3[d] = b < e ? 0.5 * (mn[d] + mx[d]) : 0.0;
-      e3[d] = b < e ? 0.5 * (mx[d] - mn[d]) : 0.0;
-    }
-    store_chunk(frame, q, c3, e3, (int)(e > b ? e - b : 0), true);
   }
 }
 
@@ -544,8 +539,8 @@ int build_chunk_frames(bldtt_plan* p, cudaStream_t s) {
   BL_TRY(dalloc_n(&p->chunk_frame, (size_t)nchunks * kChunkInfo, s));
   const int64_t pchunks = p->pool_particles / kChunk;
   if (pchunks > 0) {
-    k_frames_particles<<<nblk(pchunks, 4), 128, 0, s>>>(T.nleaves, T.leaf_ids, T.begin, T.end,
-                                                        p->pad_prefix, T.x, T.y, T.z, p->chunk_frame);
+    k_frames_particles<<<T.nleaves, 128, 0, s>>>(T.leaf_ids, T.begin, T.end, p->pad_prefix, T.x, T.y,
+                                                 T.z, p->chunk_frame);
     BL_LAUNCHED(cnt.launches);
   }
   for (int i = 0; i < p->deg.n; ++i) {

@@ -671,7 +671,7 @@ __global__ void __launch_bounds__(kMortonThreads) k_leaf_morton(
   }
 }
 
-int morton_order_leaves(Tree& T, cudaStream_t s, Counters& cnt) {
+int morton_order_leaves(Tree& T, int32_t max_leaf, cudaStream_t s, Counters& cnt) {
   if (T.nleaves == 0) return BLDTT_OK;
   double *x2 = nullptr, *y2 = nullptr, *z2 = nullptr;
   int32_t* perm2 = nullptr;
@@ -679,7 +679,10 @@ int morton_order_leaves(Tree& T, cudaStream_t s, Counters& cnt) {
   BL_TRY(dalloc_n(&y2, T.n, s));
   BL_TRY(dalloc_n(&z2, T.n, s));
   BL_TRY(dalloc_n(&perm2, T.n, s));
-  k_leaf_morton<<<T.nleaves, kMortonThreads, 0, s>>>(T.leaf_ids, T.begin, T.end, T.box, T.x, T.y,
+  // threads: a quarter of the largest leaf's padded size (four keys each), 64..512
+  int threads = 64;
+  while (threads < kMortonThreads && threads * 4 < max_leaf) threads *= 2;
+  k_leaf_morton<<<T.nleaves, threads, 0, s>>>(T.leaf_ids, T.begin, T.end, T.box, T.x, T.y,
                                                      T.z, T.perm, x2, y2, z2, perm2);
   BL_LAUNCHED(cnt.launches);
   std::swap(T.x, x2);
