@@ -36,6 +36,24 @@ WORKLOAD = "uniform_n1e6"
 FLOPS_PER_EVAL = {0: 20.0, 1: 28.0}   # Coulomb, Yukawa (stated flop counts)
 
 
+def max_over_ranks(ms: float, dist=None) -> float:
+    """The slowest rank's time (all ranks get it); ms itself for one process.
+    NCCL groups reduce on the GPU, gloo groups on the CPU."""
+    if dist is None:
+        return ms
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(targets_per_rank: int, steps: int, world: int, total_ms: float) -> float:
+    """Whole-job targets/s: every rank solves its own replica (weak scaling),
+    timed by the slowest rank."""
+    return targets_per_rank * steps * world / (total_ms / 1000.0)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default=WORKLOAD,
@@ -302,17 +320,14 @@ def run_gpu(args):
             times.append(e0.elapsed_time(e1))
     barrier()
     total_ms = sum(times)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return 0
 
     st = st_list[-1]
-    value = M * args.steps * world / (total_ms / 1000.0)
+    value = job_rate(M, args.steps, world, total_ms)
     ms_interact = statistics.mean(s["ms_interact"] for s in st_list)
     evals = sum(st["interactions"])
     flops = FLOPS_PER_EVAL.get(kw["kernel"], 20.0) * evals
@@ -497,16 +512,13 @@ def run_gpu_batched(args):
             times.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
     total_ms = sum(times)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return 0
     st = stats[-1]
-    value = M * args.steps * world / (total_ms / 1000.0)
+    value = job_rate(M, args.steps, world, total_ms)
     evals = sum(st["interactions"])
     ms_int = statistics.mean(s["ms_interact"] for s in stats)
     nyuk = sum(1 for k in kernels if k == B.YUKAWA)
@@ -617,17 +629,14 @@ def run_gpu_learned(args):
     if dist is not None:
         dist.barrier()
     total_ms, sts, csum = timed("learned")
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist)
     fixed_ms, fsts, _ = timed("fixed")
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return 0
     st, fst = sts[-1], fsts[-1]
-    value = M * args.steps * world / (total_ms / 1000.0)
+    value = job_rate(M, args.steps, world, total_ms)
     ms_interact = statistics.mean(s["ms_interact"] for s in sts)
     flops = 20.0 * sum(st["interactions"])
     achieved = flops / (ms_interact / 1000.0) / 1e12
