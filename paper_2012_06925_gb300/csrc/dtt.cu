@@ -268,8 +268,10 @@ int build_lists(bldtt_plan* p, cudaStream_t s) {
     p->list_count[k] = 0;
     p->interactions[k] = 0.0;
   }
+  for (int i = 0; i < kMaxDegrees; ++i) p->deg_used[i] = i == p->deg.n - 1;   // the highest always
   for (int c = 0; c < nclass; ++c) {
     p->class_count[c] = h_ptr[c + 1] - h_ptr[c];
+    if (c > 0 && p->class_count[c] > 0) p->deg_used[class_degree(c)] = true;
     p->class_evals[c] = (double)h_evals[c];
     p->list_count[class_type(c)] += p->class_count[c];
     p->interactions[class_type(c)] += p->class_evals[c];

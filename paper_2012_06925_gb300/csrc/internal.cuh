@@ -193,6 +193,7 @@ struct bldtt_plan {
   // A[k][k'] = L^(d)_k(s^(n)_k') of Chebyshev points on [-1, 1].
   bldtt::DegreeSet deg;
   int nclass = 4;
+  bool deg_used[bldtt::kMaxDegrees] = {};   // some list entry has this degree (set by build_lists)
   double* nodes_t[bldtt::kMaxDegrees] = {};
   double* nodes_s[bldtt::kMaxDegrees] = {};
   double* qhat_d[bldtt::kMaxDegrees] = {};

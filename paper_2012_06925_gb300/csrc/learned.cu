@@ -82,16 +82,18 @@ __device__ bool pair_features(const PairTrees& T, int t, int s, double kappa, do
 
 // ---- network forward (one warp per sample) -----------------------------------
 struct NetSmem {
-  const __nv_bfloat16* w;   // W1 | W2 | W3 | W4, row-major [out][in]
+  const __nv_bfloat16* w;   // W1 | W2 | W3 | W4, each stored transposed [in][out] in shared memory
   const float* b;           // b1 | b2 | b3 | b4
   int nout;
 };
 
-// z_j for neurons j = lane, lane + 32 (or lane < n for the output layer).
-__device__ __forceinline__ float neuron(const __nv_bfloat16* W, const float* b, int j, int K, const float* a) {
+// z_j for neurons j = lane, lane + 32 (or lane < n for the output layer);
+// Wt is the layer's weights transposed ([K][J]), so the lanes of a warp read
+// consecutive entries; the sum over k runs in increasing order.
+__device__ __forceinline__ float neuron(const __nv_bfloat16* Wt, const float* b, int j, int K, int J,
+                                        const float* a) {
   float z = b[j];
-  const __nv_bfloat16* row = W + (int64_t)j * K;
-  for (int k = 0; k < K; ++k) z = fmaf(__bfloat162float(row[k]), a[k], z);
+  for (int k = 0; k < K; ++k) z = fmaf(__bfloat162float(Wt[(int64_t)k * J + j]), a[k], z);
   return z;
 }
 
@@ -110,7 +112,7 @@ __device__ float mlp_forward_warp(const NetSmem& net, const float* x, float* act
     float zz[2];
     for (int h = 0; h < 2; ++h) {
       const int j = lane + 32 * h;
-      zz[h] = neuron(W, b, j, K[l], in);
+      zz[h] = neuron(W, b, j, K[l], kHidden, in);
     }
     __syncwarp();
     for (int h = 0; h < 2; ++h) {
@@ -127,13 +129,24 @@ __device__ float mlp_forward_warp(const NetSmem& net, const float* x, float* act
     b += kHidden;
     in = out;
   }
-  return lane < net.nout ? neuron(W, b, lane, kHidden, in) : 0.f;
+  return lane < net.nout ? neuron(W, b, lane, kHidden, net.nout, in) : 0.f;
 }
 
-// Load bf16 weights and float biases into shared memory.
+// Load bf16 weights (row-major [out][in] in global memory, transposed to
+// [in][out] in shared memory) and float biases.
 __device__ void load_net(const __nv_bfloat16* gw, const float* gb, int nout, __nv_bfloat16* sw, float* sb) {
-  const int64_t nw = sel_weight_count(nout), nb = sel_bias_count(nout);
-  for (int64_t i = threadIdx.x; i < nw; i += blockDim.x) sw[i] = gw[i];
+  const int K[4] = {kFeatures, kHidden, kHidden, kHidden};
+  const int J[4] = {kHidden, kHidden, kHidden, nout};
+  int64_t o = 0;
+  for (int l = 0; l < 4; ++l) {
+    const int64_t n = (int64_t)K[l] * J[l];
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const int64_t j = i / K[l], k = i % K[l];
+      sw[o + k * J[l] + j] = gw[o + i];
+    }
+    o += n;
+  }
+  const int64_t nb = sel_bias_count(nout);
   for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) sb[i] = gb[i];
   __syncthreads();
 }

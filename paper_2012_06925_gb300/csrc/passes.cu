@@ -333,6 +333,7 @@ int upward_pass(bldtt_plan* p, cudaStream_t s) {
   // Proxy charges of the lower degrees from those of the highest.
   const int Pm = p->P;
   for (int i = 0; i + 1 < p->deg.n; ++i) {
+    if (!p->deg_used[i]) continue;   // no entry reads these proxy charges
     const int Pi = p->deg.d[i] + 1;
     k_mode3<<<T.nclusters, kUpThreads, mode3_smem_bytes(Pm, Pi), s>>>(T.nclusters, p->xfer[i], Pm, 1,
                                                                       Pm, Pi, p->qhat, p->qhat_d[i], 0);
@@ -409,6 +410,7 @@ int build_pool(bldtt_plan* p, cudaStream_t s) {
                                                        (float4*)p->pool);
     BL_LAUNCHED(cnt.launches);
     for (int i = 0; i < p->deg.n; ++i) {
+      if (!p->deg_used[i]) continue;
       k_pool_proxies<float4><<<T.nclusters, 256, 0, s>>>(p->deg.d[i], p->deg.np_pad[i],
                                                          p->deg.proxy_base[i], p->nodes_s[i],
                                                          p->chunk_frame, p->qhat_d[i],
@@ -421,6 +423,7 @@ int build_pool(bldtt_plan* p, cudaStream_t s) {
                                                         (double4*)p->pool);
     BL_LAUNCHED(cnt.launches);
     for (int i = 0; i < p->deg.n; ++i) {
+      if (!p->deg_used[i]) continue;
       k_pool_proxies<double4><<<T.nclusters, 256, 0, s>>>(p->deg.d[i], p->deg.np_pad[i],
                                                           p->deg.proxy_base[i], p->nodes_s[i],
                                                           p->chunk_frame, p->qhat_d[i],
@@ -544,6 +547,7 @@ int build_chunk_frames(bldtt_plan* p, cudaStream_t s) {
     BL_LAUNCHED(cnt.launches);
   }
   for (int i = 0; i < p->deg.n; ++i) {
+    if (!p->deg_used[i]) continue;
     const int32_t cpc = p->deg.np_pad[i] / kChunk;
     k_frames_proxies<<<nblk((int64_t)T.nclusters * cpc, 256), 256, 0, s>>>(
         T.nclusters, p->deg.proxy_base[i] / kChunk, cpc, p->deg.np[i], T.center, T.box,
@@ -682,6 +686,7 @@ int downward_pass(bldtt_plan* p, double* phi_user, cudaStream_t s) {
   const Tree& T = p->tt;
   // Proxy potentials of the lower degrees onto the highest degree's grid.
   for (int i = 0; i + 1 < p->deg.n; ++i) {
+    if (!p->deg_used[i]) continue;   // no CP/CC entry wrote these proxy potentials
     const int Pi = p->deg.d[i] + 1, Pm = p->P;
     k_mode3<<<T.nclusters, kUpThreads, mode3_smem_bytes(Pi, Pm), s>>>(T.nclusters, p->xfer[i], 1, Pm,
                                                                       Pi, Pm, p->phit_d[i], p->phit, 1);
