@@ -81,3 +81,30 @@ def test_fp32_bulk_against_fp64_and_direct(full):
     # Sec. 4.1 reports 3.67E-8 at this size; FP32 evaluation adds at most ~1E-6.
     assert 3e-9 <= e64 <= 3e-7
     assert e32 <= e64 + 1e-6
+
+
+def test_unequal_yukawa_full_size():
+    """The unequal-set workload at its full size (1E7 uniform targets, 5E6
+    Plummer sources, Yukawa kappa=0.5, n=7, theta=0.8, leaves 2000) in the
+    benchmarked configuration: FP32_BULK against the FP64 BLDTT on the whole
+    output, and both against the FP64 direct sum on 2000 sampled targets."""
+    cfg = W.CONFIGS["unequal_yukawa"]
+    tgt, src, q = W.make_problem(cfg["kind"], cfg["M"], cfg["N"], seed=cfg["seed"],
+                                 sources_kind=cfg["sources_kind"])
+    kw = dict(kernel=cfg["kernel"], kappa=cfg["kappa"], n=cfg["n"], theta=cfg["theta"],
+              N0=cfg["N0"], M0=cfg["M0"])
+    dt, ds, dq = to_dev(tgt), to_dev(src), to_dev(q)
+    phi = {}
+    for prec in (B.FP64, B.FP32_BULK):
+        with B.Plan(dt, ds, dq, precision=prec, **kw) as plan:
+            phi[prec] = plan.compute().cpu().numpy()
+            plan.check_error()
+    err = O.relative_l2_error(phi[B.FP64], phi[B.FP32_BULK])
+    assert err <= 1e-6
+    idx = np.sort(np.random.default_rng(8).choice(tgt.shape[1], size=2000, replace=False))
+    direct = B.direct_sum(to_dev(tgt[:, idx]), ds, dq, cfg["kernel"], cfg["kappa"]).cpu().numpy()
+    e64 = O.relative_l2_error(direct, phi[B.FP64][idx])
+    e32 = O.relative_l2_error(direct, phi[B.FP32_BULK][idx])
+    print(f"unequal_yukawa: FP32 vs FP64 {err:.2e}, FP64 vs direct {e64:.2e}, FP32 vs direct {e32:.2e}")
+    assert e64 <= 1e-5                # the method's error at n=7, theta=0.8
+    assert e32 <= e64 + 1e-6
