@@ -112,3 +112,44 @@ def test_setup_batch_rejects_bad_batches(lib):
     assert call(2, I64(0, 5, 9), I64(0, 5, 9), kernels=(ctypes.c_int * 2)(0, 7)) == 1
     assert call(2, I64(0, 5, 9), I64(0, 5, 9), kappas=(ctypes.c_double * 2)(0.0, -1.0)) == 1
     assert not h
+
+
+def test_setup_learned_rejects_bad_selectors(lib):
+    h = ctypes.c_void_p()
+    prm = B.Params(0, 0.0, 5, 0.7, 10, 10, 1, 0)
+
+    def call(degrees, lo=None, hi=None, budget=-6.0, weights=None, prm_=prm):
+        st = B.SelectorStruct()
+        st.num_degrees = len(degrees)
+        for i, d in enumerate(degrees):
+            st.degrees[i] = d
+        for i in range(6):
+            st.feature_lo[i] = 0.0 if lo is None else lo[i]
+            st.feature_hi[i] = 1.0 if hi is None else hi[i]
+        st.log10_budget = budget
+        if weights is not None:
+            st.weights = weights
+        return lib.bldtt_setup_learned(ctypes.byref(h), DUMMY, 100, DUMMY, 100, DUMMY,
+                                       ctypes.byref(prm_), ctypes.byref(st), None)
+    assert call([]) == 1                                   # no degrees
+    assert call([3, 4, 5, 5]) == 1                         # not strictly increasing
+    assert call([3, 4]) == 1                               # highest degree != params n
+    assert call([3, 17]) == 1                              # degree out of range
+    assert call([3, 5], lo=[0, 0, 0, 0, 2, 0], hi=[1] * 6) == 1    # empty feature box
+    assert call([3, 5], budget=float("nan")) == 1
+    assert lib.bldtt_setup_learned(ctypes.byref(h), DUMMY, 100, DUMMY, 100, DUMMY,
+                                   ctypes.byref(prm), None, None) == 1
+    assert not h
+
+
+def test_training_entry_points_reject_bad_arguments(lib):
+    assert lib.bldtt_selector_param_count(0) == -1
+    assert lib.bldtt_selector_param_count(6) == 64 * 6 + 64 + 2 * (64 * 64 + 64) + 18 * 64 + 18
+    assert lib.bldtt_mlp_forward(None, 3, DUMMY, 10, DUMMY, None) == 1
+    assert lib.bldtt_mlp_forward(DUMMY, 25, DUMMY, 10, DUMMY, None) == 1      # > 24 outputs
+    assert lib.bldtt_mlp_gradients(DUMMY, 3, DUMMY, DUMMY, None, 10, DUMMY, None, None) == 1
+    assert lib.bldtt_mlp_adam(DUMMY, DUMMY, DUMMY, DUMMY, 10, 0, 1e-3, None) == 1   # step counts from 1
+    deg = (ctypes.c_int * 2)(3, 5)
+    assert lib.bldtt_pair_errors(None, 1, DUMMY, 64, 2, deg, DUMMY, None) == 1
+    assert lib.bldtt_pair_features(None, 1, DUMMY, DUMMY, None) == 1
+    assert lib.bldtt_list_classes(None, None, None, None) == 1
