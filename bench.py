@@ -337,6 +337,40 @@ def run_gpu(args):
     peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
     csum = clocks.summary()
     launches = sum(s["launches_setup"] + s["launches_compute"] for s in st_list)
+    peaks = measured_peaks()
+    load_mhz = peaks.get("clocks_under_load", {}).get("sm_mhz_median")
+
+    # Issue ceilings beside the peak, from the library's pipe microbenchmark
+    # (operations per clock per SM).  Per Coulomb evaluation the packed path
+    # issues 3.5 FP32x2 instructions (7 lanes) and one MUFU.RSQ; Yukawa adds
+    # one MUFU.EX2 and two lanes.
+    rates = B.pipe_rates(stream)
+    sms = props.multi_processor_count
+    clock = (csum.get("sm_mhz") or sm_max) * 1e6
+    fma_lanes_per_eval = 7.0 if kw["kernel"] == 0 else 9.0
+    mufu_clk_per_eval = 1.0 / rates["mufu_rsqrt"] + (0.0 if kw["kernel"] == 0 else 1.0 / rates["mufu_ex2"])
+    ceilings = {
+        "unit": "evaluations/clk/SM",
+        "fp32_pipe": rates["ffma2_lanes"] / fma_lanes_per_eval,
+        "mufu": 1.0 / mufu_clk_per_eval,
+        "achieved": evals / (ms_interact / 1000.0) / clock / sms,
+        "measured_ops_per_clk_sm": {k: round(v, 2) for k, v in rates.items()},
+    }
+
+    # Leaf passes: algorithmic bytes (32 B per particle read, the proxy arrays
+    # of every cluster twice) and flops (2 n_p per particle), per phase time.
+    np_ = (kw["n"] + 1) ** 3
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    passes = {}
+    for name, count, clusters in (("upward", N, st["num_source_clusters"]),
+                                  ("downward", M, st["num_target_clusters"])):
+        ms = st["ms_" + name]
+        byts = 32.0 * count + 2.0 * 8.0 * np_ * clusters
+        pflops = 2.0 * np_ * count
+        passes[name] = {"ms": ms, "bytes": byts, "gbs": byts / (ms / 1000.0) / 1e9,
+                        "hbm_frac": byts / (ms / 1000.0) / 1e9 / hbm,
+                        "tflops": pflops / (ms / 1000.0) / 1e12,
+                        "fp32_frac": pflops / (ms / 1000.0) / 1e12 / peak}
 
     # FP64 comparator: the plain FP64 BLDTT step.
     fp64 = None
@@ -409,7 +443,11 @@ def run_gpu(args):
                      "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
                                    f"{sm_max:.0f} MHz",
                      "frac_at_sampled_clock": (achieved / peak * sm_max / csum["sm_mhz"])
-                     if csum.get("sm_mhz") else None},
+                     if csum.get("sm_mhz") else None,
+                     "frac_at_under_load_clock": (achieved / peak * sm_max / load_mhz)
+                     if load_mhz else None,
+                     "ceilings": ceilings},
+        "passes_roofline": passes,
         "fp64_plain": fp64,
         "speedup_vs_fp64": (value / world) / fp64["value"] if fp64 else None,
         "e2e": e2e, "gpu_launches": launches, "clocks": csum, "cpu_baseline": cpu,

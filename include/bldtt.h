@@ -331,6 +331,17 @@ int bldtt_compute_graph(bldtt_plan* plan, double* phi, void* cuda_stream);
  */
 int bldtt_autotune(bldtt_plan* plan, double* phi, void* cuda_stream, int* chosen);
 
+/*
+ * bldtt_pipe_rates - measured throughput of the pipes the interaction kernel
+ * uses, for the roofline's issue ceilings (no counterpart in the paper): one
+ * CTA of 1024 threads per SM runs independent chains of one operation and the
+ * SM's cycle counter times it.  out (host, 5 doubles) receives operations
+ * (lanes) per clock per SM of: FP32 FMA, packed FP32x2 FMA (counted per
+ * lane, two per instruction), MUFU rsqrt, MUFU exp2, FP64 FMA (median CTA).
+ * Synchronous on cuda_stream.  Errors: EINVAL (NULL out), ENOMEM, ECUDA.
+ */
+int bldtt_pipe_rates(double* out, void* cuda_stream);
+
 /* Synchronise the plan's last stream and report a device-side error flag
  * (ETIMEOUT from a bounded wait, EINTERNAL from a bounds check). */
 int bldtt_check_error(bldtt_plan* plan);

@@ -29,7 +29,7 @@ EXPORTED = (
     "bldtt_export_proxy_potentials", "bldtt_direct_sum", "bldtt_solve_host",
     "bldtt_bounding_box_noalloc", "bldtt_selector_param_count", "bldtt_setup_learned",
     "bldtt_list_classes", "bldtt_mlp_forward", "bldtt_mlp_gradients", "bldtt_mlp_adam",
-    "bldtt_pair_features", "bldtt_pair_errors",
+    "bldtt_pair_features", "bldtt_pair_errors", "bldtt_pipe_rates",
 )
 
 
@@ -125,6 +125,7 @@ def load_library(path: str = LIB_PATH):
         "bldtt_mlp_adam": (i32, [vp, vp, vp, vp, i64, i32, ctypes.c_float, vp]),
         "bldtt_pair_features": (i32, [vp, i64, vp, vp, vp]),
         "bldtt_pair_errors": (i32, [vp, i64, vp, i32, i32, ctypes.POINTER(ctypes.c_int), vp, vp]),
+        "bldtt_pipe_rates": (i32, [P_dbl, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -458,6 +459,14 @@ def pair_errors(plan, pairs, degrees, samples=64, stream=None):
                                             deg.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                                             _fptr(out, out.numel(), "float64"), _stream_ptr(stream)))
     return out
+
+
+def pipe_rates(stream=None) -> dict:
+    """Measured operations per clock per SM of the FP32 FMA pipe (scalar and
+    packed, per lane), MUFU rsqrt and exp2, and FP64 FMA (bldtt_pipe_rates)."""
+    out = np.zeros(5, dtype=np.float64)
+    _check(load_library().bldtt_pipe_rates(_np_ptr(out, ctypes.c_double), _stream_ptr(stream)))
+    return dict(ffma=out[0], ffma2_lanes=out[1], mufu_rsqrt=out[2], mufu_ex2=out[3], dfma=out[4])
 
 
 def direct_sum(targets, sources, charges, kernel=COULOMB, kappa=0.0, phi=None, stream=None):
