@@ -232,18 +232,28 @@ def measured_peaks():
         return {}
 
 
+def code_hash(path):
+    """sha256 of a source file's code: // comments, blank lines and
+    indentation removed, so that editing a comment does not change it."""
+    import hashlib
+    lines = []
+    with open(path) as f:
+        for line in f:
+            code = line.split("//", 1)[0].strip()
+            if code:
+                lines.append(code)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()
+
+
 def interact_traffic():
     """DRAM bytes per launch of the interaction kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
-    import hashlib
+    summary, if it was taken on the current kernel code."""
     src = os.path.join(ROOT, "paper_2012_06925_gb300", "csrc", "interact.cu")
     path = os.path.join(ROOT, "profiles", "interact_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        with open(src, "rb") as f:
-            h = hashlib.sha256(f.read()).hexdigest()
-        if d.get("interact_cu_sha256") == h:
+        if d.get("interact_cu_code_sha256") == code_hash(src):
             return d.get("dram_bytes_per_launch_full_size")
     except (OSError, ValueError):
         pass

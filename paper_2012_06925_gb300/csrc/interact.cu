@@ -1,14 +1,16 @@
 // PP, PC, CP and CC interactions (Sec. 2.4, Eqs. (6), (8), (12), (15)) in one
-// persistent kernel.
+// persistent kernel, launched once per kernel type of the plan.
 //
 // All four interaction types are "targets x sources" sums (Sec. 3.3): the
 // targets are particles (PP, PC) or proxy points (CP, CC) of a target cluster,
 // the sources are particles (PP, CP) or proxy points with proxy charges
 // (PC, CC) of a source cluster.  A work item is a tile of up to kTile targets
 // of one target cluster; its sources are the concatenation of
-//   particle tiles: PP and PC entries of the leaf and of every ancestor
-//                   (an entry on an ancestor applies to all its particles)
-//   proxy tiles:    CP and CC entries of the cluster itself.
+//   particle tiles: PP and PC (every degree) entries of the leaf and of every
+//                   ancestor (an entry on an ancestor applies to all its
+//                   particles)
+//   proxy tiles:    CP and CC entries of one degree on the cluster itself
+//                   (the targets are that degree's proxy points).
 // Each item owns its outputs, so there are no atomics and the summation order
 // is fixed.
 //
@@ -34,9 +36,17 @@
 // Chunks carry their real source count, so padding is neither copied nor
 // evaluated.
 //
+// Close pairs (FP32_BULK): every chunk also carries its half-extents and a
+// near distance tau; the producer flags the 32-target groups whose box comes
+// within tau of a particle chunk and then also stages the chunk's frame
+// residuals; a flagged warp adds the residuals of both points to the
+// coordinate differences of its near targets (see eval_chunk_f32).
+//
 // A pair at distance 0 contributes nothing.  The fast path evaluates
 // 1/sqrt(r^2) unguarded; a chunk whose partial sum is not finite (only
-// possible when some r^2 == 0) is recomputed by the warp with the guard.
+// possible when some r^2 == 0) is recomputed by the warp with the guard, in
+// the same arithmetic and order, so that a target's result never depends on
+// which warp or consumer layout evaluated it.
 #include <type_traits>
 
 #include "internal.cuh"
