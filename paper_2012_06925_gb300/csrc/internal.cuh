@@ -150,6 +150,7 @@ struct Tree {
   double* center = nullptr;           // [C][3]
   double* radius = nullptr;           // [C]
   double* nodes = nullptr;            // [C][3][P], P = n + 1 of the plan's highest degree
+  double* xfer_u = nullptr;           // [C][3][P][P]: parent's basis at the cluster's nodes
   int32_t* leaf_ids = nullptr;        // leaf order (by begin) -> cluster
   int32_t *leaf_first = nullptr, *leaf_last = nullptr;   // per cluster: leaf-order range
   std::vector<int32_t> level_start;   // host: level l holds clusters [ls[l], ls[l+1])

@@ -70,6 +70,27 @@ __device__ __forceinline__ void basis_1d_f32(double x, const float* nodes_hl, in
   }
 }
 
+// basis_1d_f32 for a grid of P points fixed at compile time, into registers
+// (the same operations in the same order).
+template <int P>
+__device__ __forceinline__ void basis_f32_fixed(double x, const float* nodes_hl, float (&out)[P]) {
+  float xh, xl;
+  split_f64(x, xh, xl);
+  float r[P];
+  int hit = -1;
+  float sum = 0.f;
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    const float d = __fadd_rn(__fsub_rn(xh, nodes_hl[k]), __fsub_rn(xl, nodes_hl[kMaxP + k]));
+    if (d == 0.f && hit < 0) hit = k;
+    r[k] = d == 0.f ? 0.f : __fdividef((float)bary_weight(k, P - 1), d);
+    sum += r[k];
+  }
+  const float inv = __fdividef(1.f, sum);
+#pragma unroll
+  for (int k = 0; k < P; ++k) out[k] = hit >= 0 ? (k == hit ? 1.f : 0.f) : r[k] * inv;
+}
+
 // Compensated float sum of products: s + c carries sum a_i b_i with the
 // rounding errors of every product (FMA) and every addition (TwoSum).
 struct CompSum {
@@ -172,95 +193,182 @@ __global__ void __launch_bounds__(kUpThreads) k_up_leaf(
   }
 }
 
-// Shared layout of the parent/child kernels (dynamic shared memory).
-struct TransferSmem {
-  double* pn;   // [3][P] parent nodes
-  double* cn;   // [3][P] child nodes
-  double* U;    // [3][P][P]  U[d][k][k'] = L^par_k(t^child_k')
-  double* A;    // [np]
-  double* B;    // [np]
+// FP32_BULK form of Eq. (9) for a grid of P points fixed at compile time
+// (P <= 16).  Thread (g, k2, k3) of a P^2 x G layout owns the P outputs
+// (k1, k2, k3), k1 = 0..P-1, over the particles of group g (every G-th
+// particle of a chunk): per particle it forms w = (L_k2(y2) q) L_k3(y3) once
+// and adds L_k1(y1) w to its P outputs, reading the k1 row as float4
+// broadcasts, so every basis value loaded serves P products.  Each output's
+// float run over one chunk (RUN terms) is added to a float pair by TwoSum; the
+// groups' pairs are summed in FP64 at the end (fixed order).
+template <int P>
+struct UpLeafShape {
+  static constexpr int P2 = P * P;
+  static constexpr int G = kUpThreads / P2;            // particle groups
+  static constexpr int RUN = 512 / G < 32 ? 512 / G : 32;   // particles of a group per chunk
+  static constexpr int CH = G * RUN;                   // particles per chunk
+  static constexpr int RS = (P + 3) / 4 * 4;           // k1-row stride (float4 aligned)
+  static constexpr int LS = CH + 1;                    // odd stride of the k2 and k3 rows
 };
-__device__ __forceinline__ TransferSmem carve(double* base, int P) {
-  TransferSmem t;
-  t.pn = base;
-  t.cn = t.pn + 3 * P;
-  t.U = t.cn + 3 * P;
-  t.A = t.U + 3 * P * P;
-  t.B = t.A + P * P * P;
-  return t;
-}
-static size_t transfer_smem_bytes(int P) {
-  return sizeof(double) * (size_t)(6 * P + 3 * P * P + 2 * P * P * P);
-}
 
-__device__ void load_transfer_matrices(const TransferSmem& S, const double* __restrict__ nodes,
-                                       int par, int ch, int n) {
-  const int P = n + 1;
-  for (int t = threadIdx.x; t < 3 * P; t += blockDim.x) {
-    S.pn[t] = nodes[(int64_t)par * 3 * P + t];
-    S.cn[t] = nodes[(int64_t)ch * 3 * P + t];
+template <int P>
+__global__ void __launch_bounds__(kUpThreads) k_up_leaf_f32(
+    const int32_t* __restrict__ leaf_ids, const int32_t* __restrict__ begin,
+    const int32_t* __restrict__ end, const double* __restrict__ x, const double* __restrict__ y,
+    const double* __restrict__ z, const double* __restrict__ q, const double* __restrict__ nodes,
+    double* __restrict__ qhat) {
+  using S = UpLeafShape<P>;
+  static_assert(S::G >= 1, "P^2 must not exceed the block size");
+  constexpr int NP = P * P * P;
+  __shared__ float shl[3][2 * kMaxP];
+  __shared__ __align__(16) float s1[S::CH][S::RS];     // L_k1(y1), one row per particle
+  __shared__ float s2[P][S::LS];                        // L_k2(y2) q
+  __shared__ float s3[P][S::LS];                        // L_k3(y3)
+  __shared__ double sred[S::G][NP];
+  const int tid = threadIdx.x;
+  const int c = leaf_ids[blockIdx.x];
+  const int32_t b = begin[c], e = end[c];
+  if (tid < 3 * P) {
+    float h, l;
+    split_f64(nodes[(int64_t)c * 3 * P + tid], h, l);
+    shl[tid / P][tid % P] = h;
+    shl[tid / P][kMaxP + tid % P] = l;
   }
-  __syncthreads();
-  // U[d][k][k'] = L^par_k(s^child_k'): the parent's basis at the child's nodes.
-  for (int t = threadIdx.x; t < 3 * P; t += blockDim.x) {
-    int d = t / P, kp = t % P;
-    basis_1d<double>(S.cn[d * P + kp], S.pn + d * P, n, S.U + (d * P) * P + kp, P);
-  }
-  __syncthreads();
-}
-
-// Eq. (16): qhat^par_k = sum_children sum_k' L^par_k(s^child_k') qhat^child_k',
-// as three mode products with the P x P matrices U_d.
-__global__ void k_up_parent(int32_t ls, const int32_t* __restrict__ nchild,
-                            const int32_t* __restrict__ first_child, const double* __restrict__ nodes,
-                            int n, double* __restrict__ qhat) {
-  extern __shared__ double smem[];
-  const int P = n + 1, np = P * P * P;
-  const int c = ls + blockIdx.x;
-  if (nchild[c] == 0) return;
-  TransferSmem S = carve(smem, P);
-  double acc[kMaxOutPerThread];
+  const bool active = tid < S::P2 * S::G;
+  const int g = tid / S::P2, u = tid % S::P2, k2 = u / P, k3 = u % P;
+  float hi[P], lo[P];
 #pragma unroll
-  for (int r = 0; r < kMaxOutPerThread; ++r) acc[r] = 0.0;
-  for (int ci = 0; ci < nchild[c]; ++ci) {
-    const int ch = first_child[c] + ci;
-    load_transfer_matrices(S, nodes, c, ch, n);
-    for (int o = threadIdx.x; o < np; o += blockDim.x) S.A[o] = qhat[(int64_t)ch * np + o];
-    __syncthreads();
-    // B[k1][k2'][k3'] = sum_k1' U1[k1][k1'] A[k1'][k2'][k3']
-    for (int o = threadIdx.x; o < np; o += blockDim.x) {
-      int k1 = o / (P * P), rest = o % (P * P);
-      double v = 0.0;
-      for (int a = 0; a < P; ++a) v += S.U[(0 * P + k1) * P + a] * S.A[a * P * P + rest];
-      S.B[o] = v;
+  for (int k = 0; k < P; ++k) hi[k] = lo[k] = 0.f;
+  __syncthreads();
+  for (int32_t base = b; base < e; base += S::CH) {
+    const int cnt = min(S::CH, e - base);
+    for (int task = tid; task < 3 * S::CH; task += kUpThreads) {
+      const int d = task / S::CH, j = task % S::CH;
+      float L[P];
+      if (j < cnt) {
+        const double* cd = d == 0 ? x : (d == 1 ? y : z);
+        basis_f32_fixed<P>(cd[base + j], shl[d], L);
+      } else {
+#pragma unroll
+        for (int k = 0; k < P; ++k) L[k] = 0.f;
+      }
+      if (d == 0) {
+#pragma unroll
+        for (int k = 0; k < S::RS; ++k) s1[j][k] = k < P ? L[k < P ? k : 0] : 0.f;
+      } else if (d == 1) {
+        const float qj = j < cnt ? (float)q[base + j] : 0.f;
+#pragma unroll
+        for (int k = 0; k < P; ++k) s2[k][j] = L[k] * qj;
+      } else {
+#pragma unroll
+        for (int k = 0; k < P; ++k) s3[k][j] = L[k];
+      }
     }
     __syncthreads();
-    // A[k1][k2][k3'] = sum_k2' U2[k2][k2'] B[k1][k2'][k3']
-    for (int o = threadIdx.x; o < np; o += blockDim.x) {
-      int k1 = o / (P * P), k2 = (o / P) % P, k3 = o % P;
-      double v = 0.0;
-      for (int a = 0; a < P; ++a) v += S.U[(1 * P + k2) * P + a] * S.B[(k1 * P + a) * P + k3];
-      S.A[o] = v;
-    }
-    __syncthreads();
-    // out[k1][k2][k3] += sum_k3' U3[k3][k3'] A[k1][k2][k3']
+    if (active) {
+      float part[P];
 #pragma unroll
-    for (int r = 0; r < kMaxOutPerThread; ++r) {
-      int o = threadIdx.x + r * blockDim.x;
-      if (o < np) {
-        int k12 = o / P, k3 = o % P;
-        double v = 0.0;
-        for (int a = 0; a < P; ++a) v += S.U[(2 * P + k3) * P + a] * S.A[k12 * P + a];
-        acc[r] += v;
+      for (int k = 0; k < P; ++k) part[k] = 0.f;
+      for (int i = 0; i < S::RUN; ++i) {
+        const int j = g + S::G * i;
+        if (j >= cnt) break;
+        const float w = s2[k2][j] * s3[k3][j];
+        float l1[S::RS];
+        const float4* row = reinterpret_cast<const float4*>(s1[j]);
+#pragma unroll
+        for (int v = 0; v < S::RS / 4; ++v) {
+          const float4 t = row[v];
+          l1[4 * v] = t.x;
+          l1[4 * v + 1] = t.y;
+          l1[4 * v + 2] = t.z;
+          l1[4 * v + 3] = t.w;
+        }
+#pragma unroll
+        for (int k = 0; k < P; ++k) part[k] = fmaf(l1[k], w, part[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        const float t = __fadd_rn(hi[k], part[k]);
+        lo[k] = __fadd_rn(lo[k], two_sum_err(hi[k], part[k], t));
+        hi[k] = t;
       }
     }
     __syncthreads();
   }
+  if (active) {
 #pragma unroll
-  for (int r = 0; r < kMaxOutPerThread; ++r) {
-    int o = threadIdx.x + r * blockDim.x;
-    if (o < np) qhat[(int64_t)c * np + o] = acc[r];
+    for (int k = 0; k < P; ++k) sred[g][k * S::P2 + u] = (double)hi[k] + (double)lo[k];
   }
+  __syncthreads();
+  for (int o = tid; o < NP; o += kUpThreads) {
+    double v = 0.0;
+    for (int gg = 0; gg < S::G; ++gg) v += sred[gg][o];
+    qhat[(int64_t)c * NP + o] = v;
+  }
+}
+
+// Grids of 2..9 points take the specialised FP32_BULK leaf kernels.
+constexpr int kFixedPMin = 2, kFixedPMax = 9;
+
+// Transfer matrices of Eqs. (16) and (20): U[c][d][k][k'] = L^par_k(t^c_k'),
+// the parent's 1D basis (Eq. (3)) at the cluster's own proxy coordinates, for
+// every non-root cluster c (one thread per (c, d, k')).  They depend on the
+// tree alone, so the set-up computes them once for the upward and downward
+// passes of every compute call.
+__global__ void k_transfer_matrices(int32_t C, const int32_t* __restrict__ parent,
+                                    const double* __restrict__ nodes, int n, double* __restrict__ U) {
+  const int P = n + 1;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)C * 3 * P) return;
+  const int c = (int)(t / (3 * P)), dk = (int)(t % (3 * P)), d = dk / P, kp = dk % P;
+  const int par = parent[c];
+  if (par < 0) return;
+  basis_1d<double>(nodes[(int64_t)c * 3 * P + dk], nodes + (int64_t)par * 3 * P + d * P, n,
+                   U + ((int64_t)c * 3 + d) * P * P + kp, P);
+}
+
+constexpr int kXferThreads = 128;
+
+// Eq. (16) as three mode products with the children's U_d, one CTA per
+// (parent, k1): qhat^par[k1][k2][k3] = sum over children (in child order) of
+// sum_c U3[k3][c] sum_b U2[k2][b] sum_a U1[k1][a] qhat^child[a][b][c].  The P
+// slices of a parent run on P SMs, which matters on levels with few clusters
+// because FP64 issues at a small fraction of the FP32 rate.
+__global__ void __launch_bounds__(kXferThreads) k_up_parent(int32_t ls, const int32_t* __restrict__ nchild,
+                                                           const int32_t* __restrict__ first_child,
+                                                           const double* __restrict__ U, int n,
+                                                           double* __restrict__ qhat) {
+  __shared__ double T1[kMaxP * kMaxP], T2[kMaxP * kMaxP], out[kMaxP * kMaxP];
+  const int P = n + 1, P2 = P * P, np = P2 * P;
+  const int c = ls + blockIdx.x, k1 = blockIdx.y;
+  if (nchild[c] == 0) return;
+  for (int o = threadIdx.x; o < P2; o += blockDim.x) out[o] = 0.0;
+  for (int ci = 0; ci < nchild[c]; ++ci) {
+    const int ch = first_child[c] + ci;
+    const double* Uc = U + (int64_t)ch * 3 * P2;
+    const double* A = qhat + (int64_t)ch * np;
+    for (int o = threadIdx.x; o < P2; o += blockDim.x) {     // (b, c)
+      double v = 0.0;
+      for (int a = 0; a < P; ++a) v += Uc[k1 * P + a] * A[a * P2 + o];
+      T1[o] = v;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < P2; o += blockDim.x) {     // (k2, c)
+      const int k2 = o / P, cc = o % P;
+      double v = 0.0;
+      for (int b = 0; b < P; ++b) v += Uc[P2 + k2 * P + b] * T1[b * P + cc];
+      T2[o] = v;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < P2; o += blockDim.x) {     // (k2, k3)
+      const int k2 = o / P, k3 = o % P;
+      double v = 0.0;
+      for (int cc = 0; cc < P; ++cc) v += Uc[2 * P2 + k3 * P + cc] * T2[k2 * P + cc];
+      out[o] += v;
+    }
+    __syncthreads();
+  }
+  for (int o = threadIdx.x; o < P2; o += blockDim.x) qhat[(int64_t)c * np + k1 * P2 + o] = out[o];
 }
 
 // Degree change on one proxy grid (same box): with A[k][k'] = L^(d)_k(s^(n)_k')
@@ -317,17 +425,29 @@ static size_t mode3_smem_bytes(int Pin, int Pout) {
 int upward_pass(bldtt_plan* p, cudaStream_t s) {
   Counters& cnt = p->compute_counter;
   const Tree& T = p->st;
-  if (p->precision == BLDTT_FP32_BULK)
+  const bool f32 = p->precision == BLDTT_FP32_BULK;
+  if (f32 && p->P >= kFixedPMin && p->P <= kFixedPMax) {
+    switch (p->P) {
+#define BL_UP_LEAF(PP)                                                                          \
+  case PP:                                                                                      \
+    k_up_leaf_f32<PP><<<T.nleaves, kUpThreads, 0, s>>>(T.leaf_ids, T.begin, T.end, T.x, T.y, T.z, \
+                                                       p->q_tree, T.nodes, p->qhat);            \
+    break;
+      BL_UP_LEAF(2) BL_UP_LEAF(3) BL_UP_LEAF(4) BL_UP_LEAF(5)
+      BL_UP_LEAF(6) BL_UP_LEAF(7) BL_UP_LEAF(8) BL_UP_LEAF(9)
+#undef BL_UP_LEAF
+    }
+  } else if (f32)
     k_up_leaf<true><<<T.nleaves, kUpThreads, 0, s>>>(T.leaf_ids, T.begin, T.end, T.x, T.y, T.z,
                                                       p->q_tree, T.nodes, p->n, p->qhat);
   else
     k_up_leaf<false><<<T.nleaves, kUpThreads, 0, s>>>(T.leaf_ids, T.begin, T.end, T.x, T.y, T.z,
                                                        p->q_tree, T.nodes, p->n, p->qhat);
   BL_LAUNCHED(cnt.launches);
-  size_t sm = transfer_smem_bytes(p->P);
   for (int lvl = T.nlevels - 2; lvl >= 0; --lvl) {
     int32_t ls = T.level_start[lvl], nl = T.level_start[lvl + 1] - ls;
-    k_up_parent<<<nl, kUpThreads, sm, s>>>(ls, T.nchild, T.first_child, T.nodes, p->n, p->qhat);
+    k_up_parent<<<dim3(nl, p->P), kXferThreads, 0, s>>>(ls, T.nchild, T.first_child, T.xfer_u, p->n,
+                                                         p->qhat);
     BL_LAUNCHED(cnt.launches);
   }
   // Proxy charges of the lower degrees from those of the highest.
@@ -568,40 +688,35 @@ int build_chunk_frames(bldtt_plan* p, cudaStream_t s) {
 // Downward pass
 // ---------------------------------------------------------------------------
 
-// Eq. (20): phi(t^child_k') += sum_k L^par_k(t^child_k') phi(t^par_k), three
-// mode products with the transposed U_d.
-__global__ void k_down_parent(int32_t ls, const int32_t* __restrict__ parent,
-                              const double* __restrict__ nodes, int n, double* __restrict__ phit) {
-  extern __shared__ double smem[];
-  const int P = n + 1, np = P * P * P;
-  const int c = ls + blockIdx.x;
-  const int par = parent[c];
-  TransferSmem S = carve(smem, P);
-  load_transfer_matrices(S, nodes, par, c, n);
-  for (int o = threadIdx.x; o < np; o += blockDim.x) S.A[o] = phit[(int64_t)par * np + o];
-  __syncthreads();
-  // B[k1'][k2][k3] = sum_k1 U1[k1][k1'] A[k1][k2][k3]
-  for (int o = threadIdx.x; o < np; o += blockDim.x) {
-    int k1 = o / (P * P), rest = o % (P * P);
+// Eq. (20) as three mode products with the transposed U_d, one CTA per
+// (cluster, k1'): phi(t^c)[k1'][k2'][k3'] += sum_c U3[c][k3'] sum_b U2[b][k2']
+// sum_a U1[a][k1'] phi(t^par)[a][b][c].
+__global__ void __launch_bounds__(kXferThreads) k_down_parent(int32_t ls, const int32_t* __restrict__ parent,
+                                                             const double* __restrict__ U, int n,
+                                                             double* __restrict__ phit) {
+  __shared__ double T1[kMaxP * kMaxP], T2[kMaxP * kMaxP];
+  const int P = n + 1, P2 = P * P, np = P2 * P;
+  const int c = ls + blockIdx.x, k1 = blockIdx.y;
+  const double* Uc = U + (int64_t)c * 3 * P2;
+  const double* A = phit + (int64_t)parent[c] * np;
+  for (int o = threadIdx.x; o < P2; o += blockDim.x) {       // (b, c)
     double v = 0.0;
-    for (int a = 0; a < P; ++a) v += S.U[(0 * P + a) * P + k1] * S.A[a * P * P + rest];
-    S.B[o] = v;
+    for (int a = 0; a < P; ++a) v += Uc[a * P + k1] * A[a * P2 + o];
+    T1[o] = v;
   }
   __syncthreads();
-  // A[k1'][k2'][k3] = sum_k2 U2[k2][k2'] B[k1'][k2][k3]
-  for (int o = threadIdx.x; o < np; o += blockDim.x) {
-    int k1 = o / (P * P), k2 = (o / P) % P, k3 = o % P;
+  for (int o = threadIdx.x; o < P2; o += blockDim.x) {       // (k2', c)
+    const int k2 = o / P, cc = o % P;
     double v = 0.0;
-    for (int a = 0; a < P; ++a) v += S.U[(1 * P + a) * P + k2] * S.B[(k1 * P + a) * P + k3];
-    S.A[o] = v;
+    for (int b = 0; b < P; ++b) v += Uc[P2 + b * P + k2] * T1[b * P + cc];
+    T2[o] = v;
   }
   __syncthreads();
-  // phit^child[k1'][k2'][k3'] += sum_k3 U3[k3][k3'] A[k1'][k2'][k3]
-  for (int o = threadIdx.x; o < np; o += blockDim.x) {
-    int k12 = o / P, k3 = o % P;
+  for (int o = threadIdx.x; o < P2; o += blockDim.x) {       // (k2', k3')
+    const int k2 = o / P, k3 = o % P;
     double v = 0.0;
-    for (int a = 0; a < P; ++a) v += S.U[(2 * P + a) * P + k3] * S.A[k12 * P + a];
-    phit[(int64_t)c * np + o] += v;
+    for (int cc = 0; cc < P; ++cc) v += Uc[2 * P2 + cc * P + k3] * T2[k2 * P + cc];
+    phit[(int64_t)c * np + k1 * P2 + o] += v;
   }
 }
 
@@ -681,6 +796,70 @@ __global__ void __launch_bounds__(kDownThreads) k_down_leaf(
   }
 }
 
+// FP32_BULK form of k_down_leaf for a grid of P points fixed at compile time:
+// the particle's three basis rows stay in registers and each (k1, k2) row of
+// the proxy potentials is read as float4 broadcasts; the arithmetic and its
+// order are those of k_down_leaf<true>.  A leaf's particles are shared by
+// kDownF32Split CTAs (blockIdx.y), which balances the SMs at a few leaves each.
+constexpr int kDownF32Threads = 256;
+constexpr int kDownF32Split = 2;
+
+template <int P>
+__global__ void __launch_bounds__(kDownF32Threads, 3) k_down_leaf_f32(
+    const int32_t* __restrict__ leaf_ids, const int32_t* __restrict__ begin,
+    const int32_t* __restrict__ end, const double* __restrict__ x, const double* __restrict__ y,
+    const double* __restrict__ z, const int32_t* __restrict__ perm, const double* __restrict__ nodes,
+    const double* __restrict__ phit, const double* __restrict__ phi_near,
+    double* __restrict__ phi_user) {
+  constexpr int RS = (P + 3) / 4 * 4, NP = P * P * P;
+  __shared__ __align__(16) float sphi[P * P][RS];
+  __shared__ float shl[3][2 * kMaxP];
+  const int c = leaf_ids[blockIdx.x];
+  for (int t = threadIdx.x; t < 3 * P; t += blockDim.x) {
+    float h, l;
+    split_f64(nodes[(int64_t)c * 3 * P + t], h, l);
+    shl[t / P][t % P] = h;
+    shl[t / P][kMaxP + t % P] = l;
+  }
+  for (int o = threadIdx.x; o < P * P * RS; o += blockDim.x) {
+    const int row = o / RS, k = o % RS;
+    sphi[row][k] = k < P ? (float)phit[(int64_t)c * NP + row * P + k] : 0.f;
+  }
+  __syncthreads();
+  for (int32_t i = begin[c] + blockIdx.y * blockDim.x + threadIdx.x; i < end[c];
+       i += kDownF32Split * blockDim.x) {
+    float L1[P], L2[P], L3[P];
+    basis_f32_fixed<P>(x[i], shl[0], L1);
+    basis_f32_fixed<P>(y[i], shl[1], L2);
+    basis_f32_fixed<P>(z[i], shl[2], L3);
+    CompSum a1;
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) {
+      CompSum a2;
+#pragma unroll
+      for (int k2 = 0; k2 < P; ++k2) {
+        float r[RS];
+        const float4* row = reinterpret_cast<const float4*>(sphi[k1 * P + k2]);
+#pragma unroll
+        for (int v = 0; v < RS / 4; ++v) {
+          const float4 t = row[v];
+          r[4 * v] = t.x;
+          r[4 * v + 1] = t.y;
+          r[4 * v + 2] = t.z;
+          r[4 * v + 3] = t.w;
+        }
+        float s2 = 0.f;
+#pragma unroll
+        for (int k3 = 0; k3 < P; ++k3) s2 = fmaf(L3[k3], r[k3], s2);
+        a2.add_prod(L2[k2], s2);
+      }
+      a1.add_prod(L1[k1], a2.s);
+      a1.add_prod(L1[k1], a2.c);
+    }
+    phi_user[perm[i]] = phi_near[i] + ((double)a1.s + (double)a1.c);
+  }
+}
+
 int downward_pass(bldtt_plan* p, double* phi_user, cudaStream_t s) {
   Counters& cnt = p->compute_counter;
   const Tree& T = p->tt;
@@ -692,16 +871,27 @@ int downward_pass(bldtt_plan* p, double* phi_user, cudaStream_t s) {
                                                                       Pi, Pm, p->phit_d[i], p->phit, 1);
     BL_LAUNCHED(cnt.launches);
   }
-  size_t sm = transfer_smem_bytes(p->P);
   for (int lvl = 1; lvl < T.nlevels; ++lvl) {
     int32_t ls = T.level_start[lvl], nl = T.level_start[lvl + 1] - ls;
-    k_down_parent<<<nl, kUpThreads, sm, s>>>(ls, T.parent, T.nodes, p->n, p->phit);
+    k_down_parent<<<dim3(nl, p->P), kXferThreads, 0, s>>>(ls, T.parent, T.xfer_u, p->n, p->phit);
     BL_LAUNCHED(cnt.launches);
   }
   const int P = p->P, np = p->np;
   const int stride = 3 * P + ((3 * P) % 2 == 0 ? 1 : 0);
   const size_t tz = (size_t)kDownThreads * (P | 1);
-  if (p->precision == BLDTT_FP32_BULK) {
+  if (p->precision == BLDTT_FP32_BULK && P >= kFixedPMin && P <= kFixedPMax) {
+    switch (P) {
+#define BL_DOWN_LEAF(PP)                                                                      \
+  case PP:                                                                                    \
+    k_down_leaf_f32<PP><<<dim3(T.nleaves, kDownF32Split), kDownF32Threads, 0, s>>>(T.leaf_ids, T.begin, T.end, T.x, \
+                                                              T.y, T.z, T.perm, T.nodes,      \
+                                                              p->phit, p->phi_near, phi_user); \
+    break;
+      BL_DOWN_LEAF(2) BL_DOWN_LEAF(3) BL_DOWN_LEAF(4) BL_DOWN_LEAF(5)
+      BL_DOWN_LEAF(6) BL_DOWN_LEAF(7) BL_DOWN_LEAF(8) BL_DOWN_LEAF(9)
+#undef BL_DOWN_LEAF
+    }
+  } else if (p->precision == BLDTT_FP32_BULK) {
     size_t bytes = sizeof(double) * (3 * P + (size_t)kDownThreads * stride) + sizeof(float) * (np + tz) +
                    sizeof(float) * 6 * kMaxP;
     k_down_leaf<true><<<T.nleaves, kDownThreads, bytes, s>>>(T.leaf_ids, T.begin, T.end, T.x, T.y,
@@ -721,8 +911,6 @@ int downward_pass(bldtt_plan* p, double* phi_user, cudaStream_t s) {
 // Opt the dynamic-shared-memory kernels in to large allocations (n up to 16).
 int configure_pass_kernels() {
   int big = 200 * 1024;
-  BL_CUDA(cudaFuncSetAttribute(k_up_parent, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  BL_CUDA(cudaFuncSetAttribute(k_down_parent, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   BL_CUDA(cudaFuncSetAttribute(k_down_leaf<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   BL_CUDA(cudaFuncSetAttribute(k_down_leaf<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   BL_CUDA(cudaFuncSetAttribute(k_mode3, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
@@ -768,9 +956,23 @@ static void host_basis(double x, int n, double* out) {
   for (int k = 0; k <= n; ++k) out[k] = hit >= 0 ? (k == hit ? 1.0 : 0.0) : r[k] / sum;
 }
 
+static int transfer_matrices(Tree& T, int n, cudaStream_t s, Counters& cnt) {
+  const int P = n + 1;
+  const int64_t work = (int64_t)T.nclusters * 3 * P;
+  BL_TRY(dalloc_n(&T.xfer_u, (size_t)work * P, s));
+  k_transfer_matrices<<<nblk(work, 128), 128, 0, s>>>(T.nclusters, T.parent, T.nodes, n, T.xfer_u);
+  BL_LAUNCHED(cnt.launches);
+  return BLDTT_OK;
+}
+
 int setup_degrees(bldtt_plan* p, cudaStream_t s) {
   Counters& cnt = p->setup_counter;
   const int m = p->deg.n - 1, nmax = p->deg.d[m];
+  BL_TRY(transfer_matrices(p->tt, nmax, s, cnt));
+  if (p->shared_tree)
+    p->st.xfer_u = p->tt.xfer_u;
+  else
+    BL_TRY(transfer_matrices(p->st, nmax, s, cnt));
   p->nodes_t[m] = p->tt.nodes;
   p->nodes_s[m] = p->st.nodes;
   for (int i = 0; i < m; ++i) {

@@ -702,6 +702,7 @@ void free_tree(Tree& T, cudaStream_t s) {
   dfree_ptr(T.first_child, s); dfree_ptr(T.nchild, s); dfree_ptr(T.level, s);
   dfree_ptr(T.problem, s);
   dfree_ptr(T.box, s); dfree_ptr(T.center, s); dfree_ptr(T.radius, s); dfree_ptr(T.nodes, s);
+  dfree_ptr(T.xfer_u, s);
   dfree_ptr(T.leaf_ids, s); dfree_ptr(T.leaf_first, s); dfree_ptr(T.leaf_last, s);
   T.cap = 0;
   T.nclusters = T.nlevels = T.nleaves = 0;
