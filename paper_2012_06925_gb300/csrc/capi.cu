@@ -4,6 +4,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.cuh"
@@ -116,6 +118,51 @@ float fp32_parameter(int kernel, double kappa) {
   return (float)kappa;
 }
 
+// Target and source trees of unequal sets are independent: the source tree is
+// built on a second stream by a helper thread while this thread builds the
+// target tree (each build synchronises with the host once per level, so one
+// thread would serialise the two).  The stream of the call then waits for both.
+static int build_two_trees(bldtt_plan* p, const double* targets, const double* sources, int* bad,
+                           cudaStream_t s) {
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t go = nullptr, done = nullptr;
+  BL_CUDA(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+  BL_CUDA(cudaEventCreateWithFlags(&go, cudaEventDisableTiming));
+  BL_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+  BL_CUDA(cudaEventRecord(go, s));   // the inputs and the flag, as of this call
+  BL_CUDA(cudaStreamWaitEvent(s2, go, 0));
+  Counters c2;
+  int rc2 = BLDTT_OK;
+  std::string err2;
+  std::thread worker([&] {
+    if (cudaSetDevice(p->device) != cudaSuccess) {
+      rc2 = BLDTT_ECUDA;
+      err2 = "cudaSetDevice failed in the source-tree thread";
+      return;
+    }
+    rc2 = build_tree(p->st, sources, (int32_t)p->N, p->s_off, p->N0, p->n, bad, s2, c2);
+    if (rc2 == BLDTT_OK) rc2 = morton_order_leaves(p->st, p->N0, s2, c2);
+    if (rc2 != BLDTT_OK) err2 = last_error();
+  });
+  int rc1 = build_tree(p->tt, targets, (int32_t)p->M, p->t_off, p->M0, p->n, bad, s, p->setup_counter);
+  if (rc1 == BLDTT_OK) rc1 = morton_order_leaves(p->tt, p->M0, s, p->setup_counter);
+  worker.join();
+  p->setup_counter.launches += c2.launches;
+  const cudaError_t e1 = cudaEventRecord(done, s2);
+  const cudaError_t e2 = cudaStreamWaitEvent(s, done, 0);
+  cudaEventDestroy(go);
+  cudaEventDestroy(done);
+  cudaStreamDestroy(s2);   // released once its work has completed
+  if (rc1 != BLDTT_OK) return rc1;
+  if (rc2 != BLDTT_OK) {
+    set_error("%s", err2.c_str());
+    return rc2;
+  }
+  BL_CUDA(e1);
+  BL_CUDA(e2);
+  return BLDTT_OK;
+}
+
 int setup_impl(bldtt_plan* p, const double* targets, const double* sources, const double* charges) {
   cudaStream_t s = p->stream;
   BL_CUDA(cudaGetDevice(&p->device));
@@ -145,15 +192,13 @@ int setup_impl(bldtt_plan* p, const double* targets, const double* sources, cons
   // offsets, give two identical trees (the build is deterministic): build one
   // and let the source tree alias it.
   p->shared_tree = targets == sources && p->M == p->N && p->M0 == p->N0 && p->t_off == p->s_off;
-  BL_TRY(build_tree(p->tt, targets, (int32_t)p->M, p->t_off, p->M0, p->n, bad, s,
-                    p->setup_counter));
-  BL_TRY(morton_order_leaves(p->tt, p->M0, s, p->setup_counter));
   if (p->shared_tree) {
+    BL_TRY(build_tree(p->tt, targets, (int32_t)p->M, p->t_off, p->M0, p->n, bad, s,
+                      p->setup_counter));
+    BL_TRY(morton_order_leaves(p->tt, p->M0, s, p->setup_counter));
     p->st = p->tt;
   } else {
-    BL_TRY(build_tree(p->st, sources, (int32_t)p->N, p->s_off, p->N0, p->n, bad, s,
-                      p->setup_counter));
-    BL_TRY(morton_order_leaves(p->st, p->N0, s, p->setup_counter));
+    BL_TRY(build_two_trees(p, targets, sources, bad, s));
   }
   BL_TRY(dalloc_n(&p->q_tree, p->N, s));
   BL_TRY(permute_charges(p, charges, s));

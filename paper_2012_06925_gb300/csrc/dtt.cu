@@ -436,7 +436,9 @@ __global__ void k_item_boxes(int32_t nitems, const int4* __restrict__ items, con
   if (w >= (int64_t)nitems * kItemGroups) return;
   const int4 it = items[w / kItemGroups];
   const int r = (int)(w % kItemGroups) * 32 + lane;
-  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  // float bounds (rounded outward) first: min/max commute with the monotone
+  // roundings, and float min/max avoid the FP64 pipe
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   if (r < it.z) {
     double v[3];
     if (it.w == kItemParticles) {
@@ -452,18 +454,19 @@ __global__ void k_item_boxes(int32_t nitems, const int4* __restrict__ items, con
       v[1] = nd[P + (l / P) % P];
       v[2] = nd[2 * P + l % P];
     }
-    for (int d = 0; d < 3; ++d) lo[d] = hi[d] = v[d];
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = __double2float_rd(v[d]);
+      hi[d] = __double2float_ru(v[d]);
+    }
   }
   for (int d = 0; d < 3; ++d)
     for (int o = 16; o; o >>= 1) {
-      lo[d] = fmin(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
-      hi[d] = fmax(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+      lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+      hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
     }
   if (lane == 0) {
-    box[2 * w] = make_float4(__double2float_rd(lo[0]), __double2float_rd(lo[1]),
-                             __double2float_rd(lo[2]), 0.f);
-    box[2 * w + 1] = make_float4(__double2float_ru(hi[0]), __double2float_ru(hi[1]),
-                                 __double2float_ru(hi[2]), 0.f);
+    box[2 * w] = make_float4(lo[0], lo[1], lo[2], 0.f);
+    box[2 * w + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
   }
 }
 

@@ -79,6 +79,22 @@ __device__ __forceinline__ float frame_resid(float hi, float lo, float c) {
   const float d = __fsub_rn(hi, c);
   return __fadd_rn(two_sum_err(hi, -c, d), two_sum_err(d, lo, __fadd_rn(d, lo)));
 }
+// Order-preserving integer image of a finite double: for finite a and b,
+// a < b exactly when okey(a) < okey(b), and okey(-0.0) == okey(+0.0).  The
+// set-up's coordinate comparisons, minima and maxima run on the integer pipe
+// with the results the FP64 operations give: on GB300 FP64 instructions issue
+// at about 1/64 of the FP32 rate.  okey_inv maps a key back (-0.0 as +0.0).
+__device__ __forceinline__ long long okey(double v) {
+  long long k = __double_as_longlong(v);
+  k = k == (long long)0x8000000000000000ULL ? 0LL : k;
+  return k ^ ((k >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double okey_inv(long long k) {
+  return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+constexpr long long kKeyPosInf = 0x7ff0000000000000LL;                 // okey(+inf)
+constexpr long long kKeyNegInf = (long long)0x800fffffffffffffULL;     // okey(-inf)
+
 __device__ __forceinline__ void split_f64(double v, float& hi, float& lo) {
   hi = __double2float_rn(v);
   lo = __double2float_rn(__dsub_rn(v, (double)hi));
@@ -274,8 +290,6 @@ int radix_sort_pairs(uint32_t* keys, int32_t* vals, int64_t n, int bits, cudaStr
                      Counters& c);
 // Component-wise min/max of three coordinate arrays; writes 6 doubles to
 // out_dev (lo x,y,z, hi x,y,z) and raises *bad_dev if any value is not finite.
-int bbox_reduce(const double* x, const double* y, const double* z, int64_t n, double* out_dev,
-                int* bad_dev, cudaStream_t s, Counters& c);
 // Raise *bad_dev if any of n doubles is not finite.
 int check_finite(const double* v, int64_t n, int* bad_dev, cudaStream_t s, Counters& c);
 

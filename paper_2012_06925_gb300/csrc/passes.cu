@@ -594,21 +594,26 @@ __global__ void k_frames_particles(const int32_t* __restrict__ leaf_ids, const i
   for (int64_t q = q0 + (threadIdx.x >> 5); q < q1; q += blockDim.x >> 5) {
     const int64_t b = begin[c] + (q - q0) * kChunk;
     const int64_t e = min((int64_t)end[c], b + kChunk);
-    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    // exact minima and maxima, on the order-preserving keys
+    long long kn[3] = {kKeyPosInf, kKeyPosInf, kKeyPosInf}, kx[3] = {kKeyNegInf, kKeyNegInf, kKeyNegInf};
     for (int64_t i = b + lane; i < e; i += 32) {
-      double v[3] = {x[i], y[i], z[i]};
+      const long long v[3] = {okey(x[i]), okey(y[i]), okey(z[i])};
       for (int d = 0; d < 3; ++d) {
-        mn[d] = fmin(mn[d], v[d]);
-        mx[d] = fmax(mx[d], v[d]);
+        kn[d] = min(kn[d], v[d]);
+        kx[d] = max(kx[d], v[d]);
       }
     }
     for (int d = 0; d < 3; ++d)
       for (int off = 16; off; off >>= 1) {
-        mn[d] = fmin(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], off));
-        mx[d] = fmax(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], off));
+        kn[d] = min(kn[d], __shfl_xor_sync(0xffffffffu, kn[d], off));
+        kx[d] = max(kx[d], __shfl_xor_sync(0xffffffffu, kx[d], off));
       }
     if (lane == 0) {
-      double c3[3], e3[3];
+      double c3[3], e3[3], mn[3], mx[3];
+      for (int d = 0; d < 3; ++d) {
+        mn[d] = okey_inv(kn[d]);
+        mx[d] = okey_inv(kx[d]);
+      }
       for (int d = 0; d < 3; ++d) {
         c3[d] = b < e ? 0.5 * (mn[d] + mx[d]) : 0.0;
         e3[d] = b < e ? 0.5 * (mx[d] - mn[d]) : 0.0;

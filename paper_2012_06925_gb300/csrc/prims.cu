@@ -1,6 +1,6 @@
 // Device-wide primitives used by tree building, the traversal and work-list
-// construction: exclusive scan, stable LSD radix sort of (key, value) pairs,
-// bounding-box reduction and a finiteness check.  Deterministic: no result
+// construction: exclusive scan, stable LSD radix sort of (key, value) pairs
+// and a finiteness check.  Deterministic: no result
 // depends on the order in which atomics land.
 #include <cstdarg>
 #include <cstdio>
@@ -274,86 +274,6 @@ constexpr int kRedThreads = 256;
 
 __device__ __forceinline__ bool finite_d(double v) {
   return (__double_as_longlong(v) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
-}
-
-__global__ void k_bbox_partial(const double* __restrict__ x, const double* __restrict__ y,
-                               const double* __restrict__ z, int64_t n, double* __restrict__ part,
-                               int* __restrict__ bad) {
-  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  bool ok = true;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    double v[3] = {x[i], y[i], z[i]};
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      ok = ok && finite_d(v[d]);
-      lo[d] = fmin(lo[d], v[d]);
-      hi[d] = fmax(hi[d], v[d]);
-    }
-  }
-  __shared__ double sm[kRedThreads / 32][6];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    for (int off = 16; off; off >>= 1) {
-      lo[d] = fmin(lo[d], __shfl_down_sync(0xffffffffu, lo[d], off));
-      hi[d] = fmax(hi[d], __shfl_down_sync(0xffffffffu, hi[d], off));
-    }
-  }
-  if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicExch(bad, 1);
-  if (lane == 0) {
-    for (int d = 0; d < 3; ++d) {
-      sm[warp][d] = lo[d];
-      sm[warp][3 + d] = hi[d];
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < 6) {
-    double r = sm[0][threadIdx.x];
-    for (int w = 1; w < kRedThreads / 32; ++w)
-      r = threadIdx.x < 3 ? fmin(r, sm[w][threadIdx.x]) : fmax(r, sm[w][threadIdx.x]);
-    part[blockIdx.x * 6 + threadIdx.x] = r;
-  }
-}
-
-__global__ void k_bbox_final(const double* __restrict__ part, int nparts, double* __restrict__ out) {
-  double v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
-  for (int b = threadIdx.x; b < nparts; b += blockDim.x)
-    for (int k = 0; k < 6; ++k) {
-      double p = part[b * 6 + k];
-      v[k] = k < 3 ? fmin(v[k], p) : fmax(v[k], p);
-    }
-  __shared__ double sm[kRedThreads / 32][6];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k = 0; k < 6; ++k)
-    for (int off = 16; off; off >>= 1) {
-      double o = __shfl_down_sync(0xffffffffu, v[k], off);
-      v[k] = k < 3 ? fmin(v[k], o) : fmax(v[k], o);
-    }
-  if (lane == 0)
-    for (int k = 0; k < 6; ++k) sm[warp][k] = v[k];
-  __syncthreads();
-  if (threadIdx.x < 6) {
-    double r = sm[0][threadIdx.x];
-    for (int w = 1; w < kRedThreads / 32; ++w)
-      r = threadIdx.x < 3 ? fmin(r, sm[w][threadIdx.x]) : fmax(r, sm[w][threadIdx.x]);
-    out[threadIdx.x] = r;
-  }
-}
-
-int bbox_reduce(const double* x, const double* y, const double* z, int64_t n, double* out_dev,
-                int* bad_dev, cudaStream_t s, Counters& c) {
-  int blocks = (int)((n + kRedThreads - 1) / kRedThreads);
-  if (blocks > 1024) blocks = 1024;
-  if (blocks < 1) blocks = 1;
-  double* part = nullptr;
-  BL_TRY(dalloc_n(&part, (size_t)blocks * 6, s));
-  k_bbox_partial<<<blocks, kRedThreads, 0, s>>>(x, y, z, n, part, bad_dev);
-  BL_LAUNCHED(c.launches);
-  k_bbox_final<<<1, kRedThreads, 0, s>>>(part, blocks, out_dev);
-  BL_LAUNCHED(c.launches);
-  dfree(part, s);
-  return BLDTT_OK;
 }
 
 __global__ void k_check_finite(const double* __restrict__ v, int64_t n, int* __restrict__ bad) {

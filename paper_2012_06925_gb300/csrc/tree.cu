@@ -112,12 +112,14 @@ __global__ void k_tree_chunks(int32_t nl, int32_t ls, const int32_t* __restrict_
   chunk_start[q] = begin[ls + j] + (q - chunk_off[j]) * kTreeChunk;
 }
 
+// Child code of a particle: bit (4 >> d) set when coordinate d is at or above
+// the midpoint (a plain FP64 comparison, done on the order-preserving keys).
 __device__ __forceinline__ int child_code(double px, double py, double pz, uint8_t mask,
-                                          const double* m) {
+                                          const long long* mk) {
   int code = 0;
-  if ((mask & 4) && px >= m[0]) code |= 4;
-  if ((mask & 2) && py >= m[1]) code |= 2;
-  if ((mask & 1) && pz >= m[2]) code |= 1;
+  if ((mask & 4) && okey(px) >= mk[0]) code |= 4;
+  if ((mask & 2) && okey(py) >= mk[1]) code |= 2;
+  if ((mask & 1) && okey(pz) >= mk[2]) code |= 1;
   return code;
 }
 
@@ -135,11 +137,16 @@ __global__ void k_tree_count(int32_t ls, const int32_t* __restrict__ chunk_clust
   int32_t s0 = chunk_start[q];
   int32_t s1 = min(s0 + kTreeChunk, end[ls + j]);
   uint8_t mask = splitmask[j];
-  double m[3] = {mid[(int64_t)j * 3], mid[(int64_t)j * 3 + 1], mid[(int64_t)j * 3 + 2]};
-  for (int32_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
-    int c = child_code(x[i], y[i], z[i], mask, m);
-    code[i] = (uint8_t)c;
-    atomicAdd(&cnt[c], 1);
+  const long long mk[3] = {okey(mid[(int64_t)j * 3]), okey(mid[(int64_t)j * 3 + 1]),
+                           okey(mid[(int64_t)j * 3 + 2])};
+  const int lane = threadIdx.x & 31;
+  for (int32_t i0 = s0; i0 < s1; i0 += blockDim.x) {   // warp-uniform trip count
+    const int32_t i = i0 + threadIdx.x;
+    const bool valid = i < s1;
+    const int c = valid ? child_code(x[i], y[i], z[i], mask, mk) : 8;
+    if (valid) code[i] = (uint8_t)c;
+    const unsigned peers = __match_any_sync(0xffffffffu, c);
+    if (valid && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&cnt[c], __popc(peers));
   }
   __syncthreads();
   if (threadIdx.x < 8) counts[(int64_t)q * 8 + threadIdx.x] = cnt[threadIdx.x];
@@ -328,20 +335,21 @@ __global__ void k_tree_child_bbox(int32_t first, int32_t nc, const int32_t* __re
   const int c = first + lo_j;
   const int32_t s0 = begin[c] + (b - slice_off[lo_j]) * kBoxSlice;
   const int32_t s1 = min(end[c], s0 + kBoxSlice);
-  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  // exact minima and maxima, on the order-preserving keys
+  long long lo[3] = {kKeyPosInf, kKeyPosInf, kKeyPosInf}, hi[3] = {kKeyNegInf, kKeyNegInf, kKeyNegInf};
   for (int32_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
-    double v[3] = {x[i], y[i], z[i]};
+    const long long v[3] = {okey(x[i]), okey(y[i]), okey(z[i])};
     for (int d = 0; d < 3; ++d) {
-      lo[d] = fmin(lo[d], v[d]);
-      hi[d] = fmax(hi[d], v[d]);
+      lo[d] = min(lo[d], v[d]);
+      hi[d] = max(hi[d], v[d]);
     }
   }
-  __shared__ double sm[kTreeThreads / 32][6];
+  __shared__ long long sm[kTreeThreads / 32][6];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int d = 0; d < 3; ++d)
     for (int off = 16; off; off >>= 1) {
-      lo[d] = fmin(lo[d], __shfl_down_sync(0xffffffffu, lo[d], off));
-      hi[d] = fmax(hi[d], __shfl_down_sync(0xffffffffu, hi[d], off));
+      lo[d] = min(lo[d], __shfl_down_sync(0xffffffffu, lo[d], off));
+      hi[d] = max(hi[d], __shfl_down_sync(0xffffffffu, hi[d], off));
     }
   if (lane == 0)
     for (int d = 0; d < 3; ++d) {
@@ -350,10 +358,10 @@ __global__ void k_tree_child_bbox(int32_t first, int32_t nc, const int32_t* __re
     }
   __syncthreads();
   if (threadIdx.x < 6) {
-    double r = sm[0][threadIdx.x];
+    long long r = sm[0][threadIdx.x];
     for (int w = 1; w < kTreeThreads / 32; ++w)
-      r = threadIdx.x < 3 ? fmin(r, sm[w][threadIdx.x]) : fmax(r, sm[w][threadIdx.x]);
-    part[(int64_t)b * 6 + threadIdx.x] = r;
+      r = threadIdx.x < 3 ? min(r, sm[w][threadIdx.x]) : max(r, sm[w][threadIdx.x]);
+    part[(int64_t)b * 6 + threadIdx.x] = okey_inv(r);
   }
 }
 
@@ -591,10 +599,12 @@ int build_tree(Tree& T, const double* coords, int32_t n, const std::vector<int32
 // The order of particles inside a leaf is not part of the method; putting
 // them along a Morton curve of the leaf box makes every run of 64 consecutive
 // sources spatially compact, which the FP32 interaction path exploits (its
-// coordinate frames are per run of 64).  Leaves above kMortonMax particles
-// keep their order.
+// coordinate frames are per run of 64).  A leaf is sorted by one CTA (bitonic
+// network in shared memory, one compare-exchange per thread and step); leaves
+// above the power of two covering max_leaf (only degenerate ones, whose
+// particles share a point) or above kMortonMax particles keep their order.
 constexpr int kMortonMax = 4096;
-constexpr int kMortonThreads = 512;
+constexpr int kMortonThreads = 256;
 
 __device__ __forceinline__ uint32_t spread10(uint32_t v) {
   v &= 0x3ffu;
@@ -605,11 +615,10 @@ __device__ __forceinline__ uint32_t spread10(uint32_t v) {
   return v;
 }
 
-__device__ __forceinline__ uint32_t quantize10(double v, double lo, double hi) {
-  double e = hi - lo;
-  if (!(e > 0.0)) return 0u;
-  double t = (v - lo) / e * 1024.0;
-  int q = (int)t;
+// 10-bit cell of a coordinate in [lo, lo + 1024 / scale): an ordering key
+// only, so FP32 suffices (scale = 0 for a zero-width box).
+__device__ __forceinline__ uint32_t quantize10(double v, float lo, float scale) {
+  const int q = (int)(__fsub_rn((float)v, lo) * scale);
   return (uint32_t)(q < 0 ? 0 : (q > 1023 ? 1023 : q));
 }
 
@@ -618,12 +627,12 @@ __global__ void __launch_bounds__(kMortonThreads) k_leaf_morton(
     const int32_t* __restrict__ end, const double* __restrict__ box, const double* __restrict__ x,
     const double* __restrict__ y, const double* __restrict__ z, const int32_t* __restrict__ perm,
     double* __restrict__ x2, double* __restrict__ y2, double* __restrict__ z2,
-    int32_t* __restrict__ perm2) {
-  __shared__ unsigned long long key[kMortonMax];
+    int32_t* __restrict__ perm2, int cap) {
+  extern __shared__ unsigned long long key[];   // [cap], cap a power of two
   const int c = leaf_ids[blockIdx.x];
   const int32_t b = begin[c];
   const int m = end[c] - b;
-  if (m > kMortonMax || m < 2) {   // keep the order
+  if (m > cap || m < 2) {   // keep the order
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
       x2[b + i] = x[b + i];
       y2[b + i] = y[b + i];
@@ -635,11 +644,17 @@ __global__ void __launch_bounds__(kMortonThreads) k_leaf_morton(
   int n2 = 1;
   while (n2 < m) n2 <<= 1;
   const double* bx = box + (int64_t)c * 6;
+  float lo[3], sc[3];
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = (float)bx[d];
+    const float e = (float)bx[3 + d] - lo[d];
+    sc[d] = e > 0.f ? 1024.f / e : 0.f;
+  }
   for (int i = threadIdx.x; i < n2; i += blockDim.x) {
     if (i < m) {
-      uint32_t code = (spread10(quantize10(x[b + i], bx[0], bx[3])) << 2) |
-                      (spread10(quantize10(y[b + i], bx[1], bx[4])) << 1) |
-                      spread10(quantize10(z[b + i], bx[2], bx[5]));
+      uint32_t code = (spread10(quantize10(x[b + i], lo[0], sc[0])) << 2) |
+                      (spread10(quantize10(y[b + i], lo[1], sc[1])) << 1) |
+                      spread10(quantize10(z[b + i], lo[2], sc[2]));
       key[i] = ((unsigned long long)code << 32) | (unsigned)i;   // unique: ties by position
     } else {
       key[i] = ~0ull;
@@ -648,15 +663,14 @@ __global__ void __launch_bounds__(kMortonThreads) k_leaf_morton(
   __syncthreads();
   for (int k = 2; k <= n2; k <<= 1) {        // bitonic sort, ascending
     for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-        int ixj = i ^ j;
-        if (ixj > i) {
-          unsigned long long a = key[i], bb = key[ixj];
-          bool up = (i & k) == 0;
-          if ((a > bb) == up) {
-            key[i] = bb;
-            key[ixj] = a;
-          }
+      for (int t = threadIdx.x; t < (n2 >> 1); t += blockDim.x) {   // one compare-exchange each
+        const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));          // lower index of pair t
+        const int ixj = i | j;
+        const unsigned long long a = key[i], bb = key[ixj];
+        const bool up = (i & k) == 0;
+        if ((a > bb) == up) {
+          key[i] = bb;
+          key[ixj] = a;
         }
       }
       __syncthreads();
@@ -679,11 +693,13 @@ int morton_order_leaves(Tree& T, int32_t max_leaf, cudaStream_t s, Counters& cnt
   BL_TRY(dalloc_n(&y2, T.n, s));
   BL_TRY(dalloc_n(&z2, T.n, s));
   BL_TRY(dalloc_n(&perm2, T.n, s));
-  // threads: a quarter of the largest leaf's padded size (four keys each), 64..512
-  int threads = 64;
-  while (threads < kMortonThreads && threads * 4 < max_leaf) threads *= 2;
-  k_leaf_morton<<<T.nleaves, threads, 0, s>>>(T.leaf_ids, T.begin, T.end, T.box, T.x, T.y,
-                                                     T.z, T.perm, x2, y2, z2, perm2);
+  // keys of the largest sorted leaf (leaves hold at most max_leaf particles)
+  int n2max = 2;
+  while (n2max < max_leaf && n2max < kMortonMax) n2max <<= 1;
+  const size_t smem = sizeof(unsigned long long) * (size_t)n2max;
+  BL_CUDA(cudaFuncSetAttribute(k_leaf_morton, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_leaf_morton<<<T.nleaves, kMortonThreads, smem, s>>>(T.leaf_ids, T.begin, T.end, T.box, T.x, T.y,
+                                                        T.z, T.perm, x2, y2, z2, perm2, n2max);
   BL_LAUNCHED(cnt.launches);
   std::swap(T.x, x2);
   std::swap(T.y, y2);
