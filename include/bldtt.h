@@ -66,7 +66,7 @@ enum bldtt_precision {
     BLDTT_FP64 = 0,       /* plain FP64 everywhere */
     BLDTT_FP32_BULK = 1   /* kernel evaluations and Lagrange contractions in FP32, in
                              coordinate frames local to each source cluster, summed in
-                             FP64 every 64 sources; barycentric weights, the
+                             FP64 every 256 sources; barycentric weights, the
                              coincident-point guard, proxy points, proxy charges,
                              proxy potentials and the final phi stay FP64 */
 };

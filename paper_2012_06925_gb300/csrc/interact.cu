@@ -16,7 +16,7 @@
 //
 // Per CTA, one producer warp grabs items from a global counter, walks their
 // lists and streams the sources, kChunk at a time, from the source pool into
-// a kStages-deep shared-memory ring with cp.async.bulk (TMA) copies that
+// a shared-memory ring (3 or 4 stages) with cp.async.bulk (TMA) copies that
 // complete on mbarriers; NCW consumer warps evaluate G for K targets per
 // thread against every staged source (NCW * 32 * K == kTile).
 //
@@ -236,7 +236,7 @@ __device__ __forceinline__ double pair_f64(double dx, double dy, double dz, doub
 }
 
 // ---- producer: walks an item's segments ------------------------------------
-template <typename Vec, int RES>
+template <typename Vec, int RES, int STAGES>
 struct Producer {
   const InteractView& v;
   Vec (*buf)[kChunk];
@@ -293,8 +293,8 @@ struct Producer {
   }
 
   __device__ bool acquire(int& s) {
-    s = (int)(it % kStages);
-    return mbar_wait(&empty[s], ((it / kStages) & 1u) ^ 1u, v.err);
+    s = (int)(it % STAGES);
+    return mbar_wait(&empty[s], ((it / STAGES) & 1u) ^ 1u, v.err);
   }
 
   // Stream pool entries [off, off + len) in kChunk pieces (real entries only).
@@ -381,8 +381,8 @@ struct Producer {
       }
     }
     // Error path: let the copies already issued land before the CTA exits.
-    uint32_t first = it > (uint32_t)kStages ? it - kStages : 0;
-    for (uint32_t j = first; j < it; ++j) mbar_wait(&full[j % kStages], (j / kStages) & 1u, v.err);
+    uint32_t first = it > (uint32_t)STAGES ? it - STAGES : 0;
+    for (uint32_t j = first; j < it; ++j) mbar_wait(&full[j % STAGES], (j / STAGES) & 1u, v.err);
   }
 };
 
@@ -730,20 +730,20 @@ __device__ __forceinline__ void eval_chunk_f64(const void* buf, int count, const
   }
 }
 
-template <bool F32, int KERN, int NCW, int K, int MINB>
+template <bool F32, int KERN, int NCW, int K, int MINB, int STAGES>
 __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_interact(InteractView v) {
   static_assert(NCW * 32 * K == kTile, "a CTA covers exactly one work-item tile");
   constexpr int kConsumers = NCW * 32;
   using Vec = typename std::conditional<F32, float4, double4>::type;
-  __shared__ __align__(128) Vec sbuf[kStages][kChunk];
+  __shared__ __align__(128) Vec sbuf[STAGES][kChunk];
   constexpr int kRes = F32 ? kChunk : 1;     // frame residual records (FP32 only)
-  __shared__ __align__(128) float4 sres[kStages][kRes];
-  __shared__ __align__(16) StageMeta smeta[kStages];
-  __shared__ __align__(8) uint64_t full[kStages];
-  __shared__ __align__(8) uint64_t empty[kStages];
+  __shared__ __align__(128) float4 sres[STAGES][kRes];
+  __shared__ __align__(16) StageMeta smeta[STAGES];
+  __shared__ __align__(8) uint64_t full[STAGES];
+  __shared__ __align__(8) uint64_t empty[STAGES];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], NCW);
     }
@@ -754,7 +754,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_interact(InteractView 
   if (warp == NCW) {
     if (lane == 0) {
       __shared__ float s_ibox[6];
-      Producer<Vec, kRes> prod(v, sbuf, sres, smeta, full, empty, s_ibox);
+      Producer<Vec, kRes, STAGES> prod(v, sbuf, sres, smeta, full, empty, s_ibox);
       prod.run();
     }
     return;
@@ -773,8 +773,8 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_interact(InteractView 
   float prm = 0.f;              // its FP32 parameter
   double kappa = 0.0;           // its FP64 parameter
   for (uint32_t it = 0;; ++it) {
-    const int s = (int)(it % kStages);
-    if (!mbar_wait(&full[s], (it / kStages) & 1u, v.err)) return;
+    const int s = (int)(it % STAGES);
+    if (!mbar_wait(&full[s], (it / STAGES) & 1u, v.err)) return;
     const int mi = smeta[s].item;
     if (mi != cur) {
       if (cur >= 0) {
@@ -836,20 +836,22 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_interact(InteractView 
   }
 }
 
-// Consumer layouts the kernel is instantiated for (NCW warps x K targets, and
-// the CTAs per SM the register allocation is sized for).
+// Consumer layouts the kernel is instantiated for: NCW warps x K targets, the
+// CTAs per SM the register allocation is sized for, and the depth of the
+// shared-memory ring (3 stages let six CTAs share an SM; 4 stages at five
+// CTAs hide the producer's list walks better on short items).
 struct Layout {
-  int ncw, k, minb;
+  int ncw, k, minb, stages;
 };
-static const Layout kLayouts[] = {{4, 2, 6}, {2, 4, 6}, {4, 2, 8}};
+static const Layout kLayouts[] = {{4, 2, 6, 3}, {2, 4, 6, 3}, {4, 2, 5, 4}};
 
 template <bool F32, int KERN>
 static const void* kernel_for(int layout) {
   if constexpr (KERN == BLDTT_COULOMB) {
-    if (layout == 1) return reinterpret_cast<const void*>(&k_interact<F32, KERN, 2, 4, 6>);
-    if (layout == 2) return reinterpret_cast<const void*>(&k_interact<F32, KERN, 4, 2, 8>);
+    if (layout == 1) return reinterpret_cast<const void*>(&k_interact<F32, KERN, 2, 4, 6, 3>);
+    if (layout == 2) return reinterpret_cast<const void*>(&k_interact<F32, KERN, 4, 2, 5, 4>);
   }
-  return reinterpret_cast<const void*>(&k_interact<F32, KERN, 4, 2, 6>);
+  return reinterpret_cast<const void*>(&k_interact<F32, KERN, 4, 2, 6, 3>);
 }
 
 // Layouts instantiated for a kernel (the autotuner tries these).

@@ -28,9 +28,8 @@ namespace bldtt {
 
 constexpr int kMaxDegree = 16;                 // n <= 16  ->  P = n + 1 <= 17
 constexpr int kMaxP = kMaxDegree + 1;
-constexpr int kChunk = 64;                     // sources per staged chunk
+constexpr int kChunk = 256;                    // sources per staged chunk (one coordinate frame)
 constexpr int kTile = 256;                     // targets per work item of the interaction kernel
-constexpr int kStages = 6;                     // depth of the shared-memory ring
 constexpr int kChunkInfo = 2;                  // float4 per pool chunk description
 constexpr int kItemGroups = kTile / 32;        // 32-row target groups per work item
 constexpr int kMaxDegrees = 8;                 // interpolation degrees of one plan

@@ -597,9 +597,9 @@ int build_tree(Tree& T, const double* coords, int32_t n, const std::vector<int32
 // Morton order inside leaves
 // ---------------------------------------------------------------------------
 // The order of particles inside a leaf is not part of the method; putting
-// them along a Morton curve of the leaf box makes every run of 64 consecutive
-// sources spatially compact, which the FP32 interaction path exploits (its
-// coordinate frames are per run of 64).  A leaf is sorted by one CTA (bitonic
+// them along a Morton curve of the leaf box makes every run of kChunk
+// consecutive sources spatially compact, which the FP32 interaction path
+// exploits (its coordinate frames are per run of kChunk).  A leaf is sorted by one CTA (bitonic
 // network in shared memory, one compare-exchange per thread and step); leaves
 // above the power of two covering max_leaf (only degenerate ones, whose
 // particles share a point) or above kMortonMax particles keep their order.
