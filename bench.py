@@ -232,28 +232,36 @@ def measured_peaks():
         return {}
 
 
-def code_hash(path):
-    """sha256 of a source file's code: // comments, blank lines and
-    indentation removed, so that editing a comment does not change it."""
+def code_hash(*paths):
+    """sha256 of source files' code: // comments, blank lines and indentation
+    removed, so that editing a comment does not change it."""
     import hashlib
     lines = []
-    with open(path) as f:
-        for line in f:
-            code = line.split("//", 1)[0].strip()
-            if code:
-                lines.append(code)
+    for path in paths:
+        with open(path) as f:
+            for line in f:
+                code = line.split("//", 1)[0].strip()
+                if code:
+                    lines.append(code)
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()
+
+
+INTERACT_SOURCES = ("interact.cu", "internal.cuh")   # the kernel and its constants
+
+
+def interact_code_hash():
+    csrc = os.path.join(ROOT, "paper_2012_06925_gb300", "csrc")
+    return code_hash(*(os.path.join(csrc, f) for f in INTERACT_SOURCES))
 
 
 def interact_traffic():
     """DRAM bytes per launch of the interaction kernel from the committed ncu
     summary, if it was taken on the current kernel code."""
-    src = os.path.join(ROOT, "paper_2012_06925_gb300", "csrc", "interact.cu")
     path = os.path.join(ROOT, "profiles", "interact_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        if d.get("interact_cu_code_sha256") == code_hash(src):
+        if d.get("interact_code_sha256") == interact_code_hash():
             return d.get("dram_bytes_per_launch_full_size")
     except (OSError, ValueError):
         pass

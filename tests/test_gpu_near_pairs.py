@@ -1,6 +1,6 @@
 """FP32_BULK accuracy on close pairs.
 
-The FP32 path carries coordinates relative to a frame centre per 64-source
+The FP32 path carries coordinates relative to a frame centre per 256-source
 chunk, so a pair at distance r inside a chunk of half-size rho sees a rounding
 error of about u rho / r on r (u = 2^-24).  Targets near a particle chunk add
 the frame residuals of both points, which keeps the error at a few u for any
