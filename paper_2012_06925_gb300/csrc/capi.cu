@@ -105,6 +105,7 @@ void release(bldtt_plan* p) {
   dfree_ptr(p->sel_b, s);
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
   cudaStreamSynchronize(s);
+  if (p->mempool) cudaMemPoolDestroy(p->mempool);   // every allocation from it is freed
   for (auto& e : p->ev)
     if (e) cudaEventDestroy(e);
   cudaGetLastError();
@@ -135,6 +136,7 @@ static int build_two_trees(bldtt_plan* p, const double* targets, const double* s
   int rc2 = BLDTT_OK;
   std::string err2;
   std::thread worker([&] {
+    PoolScope scope(p->mempool);
     if (cudaSetDevice(p->device) != cudaSuccess) {
       rc2 = BLDTT_ECUDA;
       err2 = "cudaSetDevice failed in the source-tree thread";
@@ -239,6 +241,8 @@ int setup_impl(bldtt_plan* p, const double* targets, const double* sources, cons
   BL_TRY(interaction_grids(p));
   BL_CUDA(cudaEventRecord(p->ev[2], s));
   BL_CUDA(cudaStreamSynchronize(s));
+  // hand back what the set-up's temporaries held; the plan's arrays stay
+  BL_CUDA(cudaMemPoolTrimTo(p->mempool, 0));
   p->ms_tree = elapsed(p->ev[0], p->ev[1]);
   p->ms_lists = elapsed(p->ev[1], p->ev[2]);
   return BLDTT_OK;
@@ -316,6 +320,23 @@ static int upload_selector(bldtt_plan* p, const float* weights) {
   BL_CUDA(cudaMemcpyAsync(p->sel_w, w.data(), w.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, s));
   BL_CUDA(cudaMemcpyAsync(p->sel_b, b.data(), b.size() * sizeof(float), cudaMemcpyHostToDevice, s));
   BL_CUDA(cudaStreamSynchronize(s));
+  return BLDTT_OK;
+}
+
+// The plan's memory pool: device memory, kept when freed (release threshold
+// at the maximum) until the plan is destroyed or the set-up trims it.
+static int create_pool(bldtt_plan* p) {
+  int dev = 0;
+  BL_CUDA(cudaGetDevice(&dev));
+  cudaMemPoolProps props;
+  std::memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.handleTypes = cudaMemHandleTypeNone;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  BL_CUDA(cudaMemPoolCreate(&p->mempool, &props));
+  uint64_t keep = UINT64_MAX;
+  BL_CUDA(cudaMemPoolSetAttribute(p->mempool, cudaMemPoolAttrReleaseThreshold, &keep));
   return BLDTT_OK;
 }
 
@@ -422,8 +443,9 @@ static int setup_common(bldtt_plan** plan, const double* targets, const int64_t*
     p->deg.np_pad[i] = (p->deg.np[i] + kChunk - 1) / kChunk * kChunk;
   }
   p->nclass = 1 + 3 * p->deg.n;
-  int st = BLDTT_OK;
-  if (sel) {
+  int st = create_pool(p);
+  PoolScope scope(p->mempool);
+  if (st == BLDTT_OK && sel) {
     p->learned = true;
     p->selector_net = sel->weights != nullptr;
     p->sel_nout = 3 * p->deg.n;

@@ -135,8 +135,21 @@ void set_error(const char* fmt, ...);
     if (s_ != BLDTT_OK) return s_;                                                         \
   } while (0)
 
-// Stream-ordered device allocation helpers.
+// Stream-ordered device allocation helpers.  Allocations come from the memory
+// pool set for the calling thread (a plan's own pool during its set-up), else
+// from the device's default pool.  A plan's pool keeps the memory that its
+// set-up frees between tree and traversal levels for reuse, where the default
+// pool hands it back to the driver at every host synchronisation.
 int dalloc(void** p, size_t bytes, cudaStream_t s);
+void set_thread_pool(cudaMemPool_t pool);
+cudaMemPool_t thread_pool();
+struct PoolScope {
+  cudaMemPool_t prev;
+  explicit PoolScope(cudaMemPool_t pool) : prev(thread_pool()) { set_thread_pool(pool); }
+  ~PoolScope() { set_thread_pool(prev); }
+  PoolScope(const PoolScope&) = delete;
+  PoolScope& operator=(const PoolScope&) = delete;
+};
 template <class T>
 inline int dalloc_n(T** p, size_t n, cudaStream_t s) {
   return dalloc(reinterpret_cast<void**>(p), n * sizeof(T) + (n == 0 ? sizeof(T) : 0), s);
@@ -274,6 +287,7 @@ struct bldtt_plan {
 
   // Captured compute phase (bldtt_compute_graph).
   cudaGraphExec_t graph_exec = nullptr;
+  cudaMemPool_t mempool = nullptr;    // the plan's device memory pool (see dalloc)
   double* graph_phi = nullptr;
 };
 

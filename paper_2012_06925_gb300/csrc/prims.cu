@@ -22,9 +22,15 @@ void set_error(const char* fmt, ...) {
 
 const char* last_error() { return g_err; }
 
+namespace {
+thread_local cudaMemPool_t t_pool = nullptr;
+}
+void set_thread_pool(cudaMemPool_t pool) { t_pool = pool; }
+cudaMemPool_t thread_pool() { return t_pool; }
+
 int dalloc(void** p, size_t bytes, cudaStream_t s) {
   *p = nullptr;
-  cudaError_t e = cudaMallocAsync(p, bytes, s);
+  cudaError_t e = t_pool ? cudaMallocFromPoolAsync(p, bytes, t_pool, s) : cudaMallocAsync(p, bytes, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
