@@ -106,6 +106,7 @@ void release(bldtt_plan* p) {
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
   cudaStreamSynchronize(s);
   if (p->mempool) cudaMemPoolDestroy(p->mempool);   // every allocation from it is freed
+  if (p->h_pinned) cudaFreeHost(p->h_pinned);
   for (auto& e : p->ev)
     if (e) cudaEventDestroy(e);
   cudaGetLastError();
@@ -136,7 +137,7 @@ static int build_two_trees(bldtt_plan* p, const double* targets, const double* s
   int rc2 = BLDTT_OK;
   std::string err2;
   std::thread worker([&] {
-    PoolScope scope(p->mempool);
+    PlanScope scope(p->mempool, static_cast<char*>(p->h_pinned) + kPinnedSlot);
     if (cudaSetDevice(p->device) != cudaSuccess) {
       rc2 = BLDTT_ECUDA;
       err2 = "cudaSetDevice failed in the source-tree thread";
@@ -172,7 +173,8 @@ int setup_impl(bldtt_plan* p, const double* targets, const double* sources, cons
   for (auto& e : p->ev) BL_CUDA(cudaEventCreate(&e));
   {
     const int P = p->nprob;
-    std::vector<float> prm(P);
+    std::vector<float>& prm = p->prob_prm_h;   // the plan keeps the staged host vectors
+    prm.resize(P);
     for (int i = 0; i < P; ++i) prm[i] = fp32_parameter(p->prob_kernel_h[i], p->prob_kappa_h[i]);
     BL_TRY(dalloc_n(&p->prob_kernel, P, s));
     BL_TRY(dalloc_n(&p->prob_kappa, P, s));
@@ -182,7 +184,6 @@ int setup_impl(bldtt_plan* p, const double* targets, const double* sources, cons
     BL_CUDA(cudaMemcpyAsync(p->prob_kappa, p->prob_kappa_h.data(), P * sizeof(double),
                             cudaMemcpyHostToDevice, s));
     BL_CUDA(cudaMemcpyAsync(p->prob_prm, prm.data(), P * sizeof(float), cudaMemcpyHostToDevice, s));
-    BL_CUDA(cudaStreamSynchronize(s));   // host staging vectors go out of scope
   }
   BL_TRY(dalloc_n(&p->dev_err, 1, s));
   BL_CUDA(cudaMemsetAsync(p->dev_err, 0, sizeof(int), s));
@@ -324,7 +325,8 @@ static int upload_selector(bldtt_plan* p, const float* weights) {
 }
 
 // The plan's memory pool: device memory, kept when freed (release threshold
-// at the maximum) until the plan is destroyed or the set-up trims it.
+// at the maximum) until the plan is destroyed or the set-up trims it; and its
+// pinned host slots for the set-up's small device-to-host reads.
 static int create_pool(bldtt_plan* p) {
   int dev = 0;
   BL_CUDA(cudaGetDevice(&dev));
@@ -337,6 +339,7 @@ static int create_pool(bldtt_plan* p) {
   BL_CUDA(cudaMemPoolCreate(&p->mempool, &props));
   uint64_t keep = UINT64_MAX;
   BL_CUDA(cudaMemPoolSetAttribute(p->mempool, cudaMemPoolAttrReleaseThreshold, &keep));
+  BL_CUDA(cudaMallocHost(&p->h_pinned, 2 * kPinnedSlot));
   return BLDTT_OK;
 }
 
@@ -444,7 +447,7 @@ static int setup_common(bldtt_plan** plan, const double* targets, const int64_t*
   }
   p->nclass = 1 + 3 * p->deg.n;
   int st = create_pool(p);
-  PoolScope scope(p->mempool);
+  PlanScope scope(p->mempool, p->h_pinned);
   if (st == BLDTT_OK && sel) {
     p->learned = true;
     p->selector_net = sel->weights != nullptr;

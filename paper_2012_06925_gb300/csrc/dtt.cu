@@ -132,6 +132,14 @@ __global__ void k_count_evals(const int32_t* __restrict__ et, const int32_t* __r
 
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Offsets list_ptr[k * nct], k = 0..nclass, written as int32 after the
+// kMaxClasses evaluation counters of `out`.
+__global__ void k_class_bounds(const int32_t* __restrict__ list_ptr, int32_t nct, int nclass,
+                               unsigned long long* __restrict__ out) {
+  int32_t* o = reinterpret_cast<int32_t*>(out + kMaxClasses);
+  for (int k = threadIdx.x; k <= nclass; k += blockDim.x) o[k] = list_ptr[(int64_t)k * nct];
+}
+
 int build_lists(bldtt_plan* p, cudaStream_t s) {
   bldtt::Counters& cnt = p->setup_counter;
   const TreeView tt = view(p->tt), st = view(p->st);
@@ -161,33 +169,32 @@ int build_lists(bldtt_plan* p, cudaStream_t s) {
   int32_t F = P;
   int64_t E = 0;
   const int imax = p->deg.n - 1;
+  // per-level scratch, grown as the front grows; the two totals of a level
+  // come back to the host in one read
+  size_t cap_k = 0, cap_i = 0, cap_o = 0, cap_e = 0, cap_a = 0, cap_c = 0;
+  int32_t *nkids = nullptr, *isentry = nullptr, *koff = nullptr, *eoff = nullptr, *tot2 = nullptr;
+  int8_t* action = nullptr;
+  int16_t* choice = nullptr;
+  BL_TRY(dalloc_n(&tot2, 2, s));
   while (F > 0) {
-    int32_t *nkids = nullptr, *isentry = nullptr, *koff = nullptr, *eoff = nullptr;
-    int8_t* action = nullptr;
-    int16_t* choice = nullptr;
-    BL_TRY(dalloc_n(&nkids, F, s));
-    BL_TRY(dalloc_n(&isentry, F, s));
-    BL_TRY(dalloc_n(&koff, F, s));
-    BL_TRY(dalloc_n(&eoff, F, s));
-    BL_TRY(dalloc_n(&action, F, s));
+    BL_TRY(dgrow(&nkids, &cap_k, (size_t)F, 0, s));
+    BL_TRY(dgrow(&isentry, &cap_i, (size_t)F, 0, s));
+    BL_TRY(dgrow(&koff, &cap_o, (size_t)F, 0, s));
+    BL_TRY(dgrow(&eoff, &cap_e, (size_t)F, 0, s));
+    BL_TRY(dgrow(&action, &cap_a, (size_t)F, 0, s));
     if (p->learned) {
-      BL_TRY(dalloc_n(&choice, F, s));
+      BL_TRY(dgrow(&choice, &cap_c, (size_t)F, 0, s));
       BL_TRY(select_pairs(p, front, F, choice, s));
     }
     k_dtt_classify<<<nblk(F, 256), 256, 0, s>>>(front, F, tt, st, p->deg.np[imax], imax, p->theta,
-                                                p->variant, choice, nkids, isentry, action);
+                                                p->variant, p->learned ? choice : nullptr, nkids,
+                                                isentry, action);
     BL_LAUNCHED(cnt.launches);
-    if (choice) dfree(choice, s);
-    // both prefix sums first, then one synchronisation for both totals
-    BL_TRY(scan_exclusive(nkids, koff, F, nullptr, s, cnt));
-    BL_TRY(scan_exclusive(isentry, eoff, F, nullptr, s, cnt));
-    int32_t last[4];
-    BL_CUDA(cudaMemcpyAsync(&last[0], koff + F - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    BL_CUDA(cudaMemcpyAsync(&last[1], nkids + F - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    BL_CUDA(cudaMemcpyAsync(&last[2], eoff + F - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    BL_CUDA(cudaMemcpyAsync(&last[3], isentry + F - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    BL_CUDA(cudaStreamSynchronize(s));
-    const int32_t K = last[0] + last[1], En = last[2] + last[3];
+    BL_TRY(scan_exclusive_dev(nkids, koff, F, tot2, s, cnt));
+    BL_TRY(scan_exclusive_dev(isentry, eoff, F, tot2 + 1, s, cnt));
+    int32_t h2[2];
+    BL_TRY(read_device(tot2, h2, sizeof(h2), s));
+    const int32_t K = h2[0], En = h2[1];
     if ((size_t)K > ncap) {
       size_t c = ncap;
       BL_TRY(dgrow(&next, &c, (size_t)K, 0, s));
@@ -205,12 +212,13 @@ int build_lists(bldtt_plan* p, cudaStream_t s) {
     k_dtt_emit<<<nblk(F, 256), 256, 0, s>>>(front, F, action, koff, eoff, tt, st, next, ent_t, ent_s,
                                             ent_key, E, nct);
     BL_LAUNCHED(cnt.launches);
-    dfree(nkids, s); dfree(isentry, s); dfree(koff, s); dfree(eoff, s); dfree(action, s);
     E += En;
     int2* tmp = front; front = next; next = tmp;
     size_t tc = fcap; fcap = ncap; ncap = tc;
     F = K;
   }
+  dfree(nkids, s); dfree(isentry, s); dfree(koff, s); dfree(eoff, s); dfree(tot2, s);
+  dfree(action, s); dfree(choice, s);
   dfree(front, s);
   dfree(next, s);
 
@@ -247,21 +255,23 @@ int build_lists(bldtt_plan* p, cudaStream_t s) {
   BL_TRY(scan_exclusive(hist, p->list_ptr, nkeys, &total, s, cnt));
   BL_CUDA(cudaMemcpyAsync(p->list_ptr + nkeys, &total, sizeof(int32_t), cudaMemcpyHostToDevice, s));
 
+  // evals: kMaxClasses counters, then room for the nclass + 1 class offsets
+  constexpr int kRead = kMaxClasses + (kMaxClasses + 2) / 2;
   unsigned long long* evals = nullptr;
-  BL_TRY(dalloc_n(&evals, kMaxClasses, s));
-  BL_CUDA(cudaMemsetAsync(evals, 0, kMaxClasses * sizeof(unsigned long long), s));
+  BL_TRY(dalloc_n(&evals, kRead, s));
+  BL_CUDA(cudaMemsetAsync(evals, 0, kRead * sizeof(unsigned long long), s));
   if (E > 0) {
     k_count_evals<<<nblk(E, 256), 256, 0, s>>>(p->list_tgt, p->list_src, ent_key, E, nct, tt, st,
                                                p->deg, evals);
     BL_LAUNCHED(cnt.launches);
   }
-  unsigned long long h_evals[kMaxClasses];
-  int32_t h_ptr[kMaxClasses + 1];
-  for (int k = 0; k <= nclass; ++k)
-    BL_CUDA(cudaMemcpyAsync(&h_ptr[k], p->list_ptr + (int64_t)k * nct, sizeof(int32_t),
-                            cudaMemcpyDeviceToHost, s));
-  BL_CUDA(cudaMemcpyAsync(h_evals, evals, sizeof(h_evals), cudaMemcpyDeviceToHost, s));
-  BL_CUDA(cudaStreamSynchronize(s));
+  // class boundaries of the CSR and the evaluation counts, in one read
+  unsigned long long h_read[kMaxClasses + (kMaxClasses + 2) / 2];
+  k_class_bounds<<<1, 32, 0, s>>>(p->list_ptr, nct, nclass, evals);
+  BL_LAUNCHED(cnt.launches);
+  BL_TRY(read_device(evals, h_read, sizeof(h_read), s));
+  const unsigned long long* h_evals = h_read;
+  const int32_t* h_ptr = reinterpret_cast<const int32_t*>(h_read + kMaxClasses);
   p->class_count.assign(nclass, 0);
   p->class_evals.assign(nclass, 0.0);
   for (int k = 0; k < 4; ++k) {
@@ -544,7 +554,6 @@ int build_work_items(bldtt_plan* p, cudaStream_t s) {
     BL_LAUNCHED(cnt.launches);
   }
   int32_t h_first[8];
-  BL_CUDA(cudaMemcpyAsync(h_first, seg_first, sizeof(h_first), cudaMemcpyDeviceToHost, s));
   if (ni > 0) {
     k_gather_items<<<nblk(ni, 256), 256, 0, s>>>(items, vals, p->items, ni);
     BL_LAUNCHED(cnt.launches);
@@ -558,8 +567,8 @@ int build_work_items(bldtt_plan* p, cudaStream_t s) {
     BL_LAUNCHED(cnt.launches);
   }
   unsigned long long h_exec = 0;
-  BL_CUDA(cudaMemcpyAsync(&h_exec, executed, sizeof(h_exec), cudaMemcpyDeviceToHost, s));
-  BL_CUDA(cudaStreamSynchronize(s));
+  BL_TRY(read_device(seg_first, h_first, sizeof(h_first), s));
+  BL_TRY(read_device(executed, &h_exec, sizeof(h_exec), s));
   p->executed_evaluations = (double)h_exec;
   dfree(seg_first, s);
   p->segments.clear();

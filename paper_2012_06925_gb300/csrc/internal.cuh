@@ -141,14 +141,21 @@ void set_error(const char* fmt, ...);
 // set-up frees between tree and traversal levels for reuse, where the default
 // pool hands it back to the driver at every host synchronisation.
 int dalloc(void** p, size_t bytes, cudaStream_t s);
-void set_thread_pool(cudaMemPool_t pool);
+// Per-thread context of the plan being set up: its memory pool and a pinned
+// host slot of kPinnedSlot bytes for small device-to-host reads.
+constexpr size_t kPinnedSlot = 1024;
+void set_thread_context(cudaMemPool_t pool, void* pinned);
 cudaMemPool_t thread_pool();
-struct PoolScope {
-  cudaMemPool_t prev;
-  explicit PoolScope(cudaMemPool_t pool) : prev(thread_pool()) { set_thread_pool(pool); }
-  ~PoolScope() { set_thread_pool(prev); }
-  PoolScope(const PoolScope&) = delete;
-  PoolScope& operator=(const PoolScope&) = delete;
+void* thread_pinned();
+struct PlanScope {
+  cudaMemPool_t prev_pool;
+  void* prev_pinned;
+  PlanScope(cudaMemPool_t pool, void* pinned) : prev_pool(thread_pool()), prev_pinned(thread_pinned()) {
+    set_thread_context(pool, pinned);
+  }
+  ~PlanScope() { set_thread_context(prev_pool, prev_pinned); }
+  PlanScope(const PlanScope&) = delete;
+  PlanScope& operator=(const PlanScope&) = delete;
 };
 template <class T>
 inline int dalloc_n(T** p, size_t n, cudaStream_t s) {
@@ -208,6 +215,7 @@ struct bldtt_plan {
   std::vector<int32_t> t_off, s_off;  // host, nprob + 1 entries
   std::vector<int> prob_kernel_h;     // host copies
   std::vector<double> prob_kappa_h;
+  std::vector<float> prob_prm_h;      // host copy of prob_prm
   int* prob_kernel = nullptr;         // device [nprob]
   double* prob_kappa = nullptr;       // device [nprob]
   float* prob_prm = nullptr;          // device [nprob] FP32 form of the parameter
@@ -288,6 +296,7 @@ struct bldtt_plan {
   // Captured compute phase (bldtt_compute_graph).
   cudaGraphExec_t graph_exec = nullptr;
   cudaMemPool_t mempool = nullptr;    // the plan's device memory pool (see dalloc)
+  void* h_pinned = nullptr;           // two pinned slots (set-up thread, source-tree thread)
   double* graph_phi = nullptr;
 };
 
@@ -298,11 +307,16 @@ namespace bldtt {
 // the sum (the call then synchronises the stream).
 int scan_exclusive(const int32_t* in, int32_t* out, int64_t n, int32_t* total_host,
                    cudaStream_t s, Counters& c);
+// The same with the sum left in device memory (*total_dev; 0 when n == 0).
+int scan_exclusive_dev(const int32_t* in, int32_t* out, int64_t n, int32_t* total_dev,
+                       cudaStream_t s, Counters& c);
+// Copy `bytes` of device memory to the host after the stream's prior work, then
+// synchronise it: through the calling thread's pinned slot when it has one
+// (a pinned copy costs ~1 us against ~9 us for a pageable one).
+int read_device(const void* dev, void* host, size_t bytes, cudaStream_t s);
 // Stable ascending sort of (key, value) pairs on the low `bits` bits of key.
 int radix_sort_pairs(uint32_t* keys, int32_t* vals, int64_t n, int bits, cudaStream_t s,
                      Counters& c);
-// Component-wise min/max of three coordinate arrays; writes 6 doubles to
-// out_dev (lo x,y,z, hi x,y,z) and raises *bad_dev if any value is not finite.
 // Raise *bad_dev if any of n doubles is not finite.
 int check_finite(const double* v, int64_t n, int* bad_dev, cudaStream_t s, Counters& c);
 

@@ -4,6 +4,7 @@
 // depends on the order in which atomics land.
 #include <cstdarg>
 #include <cstdio>
+#include <cstring>
 
 #include "internal.cuh"
 
@@ -24,9 +25,26 @@ const char* last_error() { return g_err; }
 
 namespace {
 thread_local cudaMemPool_t t_pool = nullptr;
+thread_local void* t_pinned = nullptr;
 }
-void set_thread_pool(cudaMemPool_t pool) { t_pool = pool; }
+void set_thread_context(cudaMemPool_t pool, void* pinned) {
+  t_pool = pool;
+  t_pinned = pinned;
+}
 cudaMemPool_t thread_pool() { return t_pool; }
+void* thread_pinned() { return t_pinned; }
+
+int read_device(const void* dev, void* host, size_t bytes, cudaStream_t s) {
+  if (t_pinned && bytes <= kPinnedSlot) {
+    BL_CUDA(cudaMemcpyAsync(t_pinned, dev, bytes, cudaMemcpyDeviceToHost, s));
+    BL_CUDA(cudaStreamSynchronize(s));
+    std::memcpy(host, t_pinned, bytes);
+  } else {
+    BL_CUDA(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, s));
+    BL_CUDA(cudaStreamSynchronize(s));
+  }
+  return BLDTT_OK;
+}
 
 int dalloc(void** p, size_t bytes, cudaStream_t s) {
   *p = nullptr;
@@ -61,6 +79,9 @@ template int dgrow<int32_t>(int32_t**, size_t*, size_t, size_t, cudaStream_t);
 template int dgrow<double>(double**, size_t*, size_t, size_t, cudaStream_t);
 template int dgrow<int2>(int2**, size_t*, size_t, size_t, cudaStream_t);
 template int dgrow<uint8_t>(uint8_t**, size_t*, size_t, size_t, cudaStream_t);
+template int dgrow<int8_t>(int8_t**, size_t*, size_t, size_t, cudaStream_t);
+template int dgrow<int16_t>(int16_t**, size_t*, size_t, size_t, cudaStream_t);
+template int dgrow<int4>(int4**, size_t*, size_t, size_t, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Exclusive scan (reduce, scan the tile sums, apply)
@@ -171,11 +192,20 @@ int scan_exclusive(const int32_t* in, int32_t* out, int64_t n, int32_t* total_ho
   if (total_host) BL_TRY(dalloc_n(&tot, 1, s));
   BL_TRY(scan_impl(in, out, n, tot, s, c));
   if (total_host) {
-    BL_CUDA(cudaMemcpyAsync(total_host, tot, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    const int rc = read_device(tot, total_host, sizeof(int32_t), s);
     dfree(tot, s);
-    BL_CUDA(cudaStreamSynchronize(s));
+    return rc;
   }
   return BLDTT_OK;
+}
+
+int scan_exclusive_dev(const int32_t* in, int32_t* out, int64_t n, int32_t* total_dev,
+                       cudaStream_t s, Counters& c) {
+  if (n <= 0) {
+    BL_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(int32_t), s));
+    return BLDTT_OK;
+  }
+  return scan_impl(in, out, n, total_dev, s, c);
 }
 
 // ---------------------------------------------------------------------------

@@ -59,7 +59,8 @@ __global__ void k_tree_decide(int32_t ls, int32_t nl, const int32_t* __restrict_
                               const int32_t* __restrict__ end, const double* __restrict__ box,
                               int32_t max_leaf, uint8_t* __restrict__ splitmask,
                               double* __restrict__ mid, int32_t* __restrict__ nchunks,
-                              int32_t* __restrict__ first_child, int32_t* __restrict__ nchild) {
+                              int32_t* __restrict__ first_child, int32_t* __restrict__ nchild,
+                              int32_t* __restrict__ nsplit) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nl) return;
   int c = ls + j;
@@ -94,7 +95,10 @@ __global__ void k_tree_decide(int32_t ls, int32_t nl, const int32_t* __restrict_
   }
   splitmask[j] = mask;
   for (int d = 0; d < 3; ++d) mid[(int64_t)j * 3 + d] = __dmul_rn(__dadd_rn(b[d], b[3 + d]), 0.5);
-  nchunks[j] = mask ? (int32_t)((cnt + kTreeChunk - 1) / kTreeChunk) : 0;
+  // every cluster of the level is streamed: split ones are scattered to their
+  // children, the others (leaves) copied to the same place of the other buffer
+  nchunks[j] = (int32_t)((cnt + kTreeChunk - 1) / kTreeChunk);
+  if (mask) atomicAdd(nsplit, 1);
 }
 
 __global__ void k_tree_chunks(int32_t nl, int32_t ls, const int32_t* __restrict__ chunk_off,
@@ -130,13 +134,14 @@ __global__ void k_tree_count(int32_t ls, const int32_t* __restrict__ chunk_clust
                              const double* __restrict__ mid, uint8_t* __restrict__ code,
                              int32_t* __restrict__ counts) {
   __shared__ int32_t cnt[8];
-  if (threadIdx.x < 8) cnt[threadIdx.x] = 0;
-  __syncthreads();
   int q = blockIdx.x;
   int j = chunk_cluster[q];
+  uint8_t mask = splitmask[j];
+  if (!mask) return;   // a leaf's chunk: copied, not counted
+  if (threadIdx.x < 8) cnt[threadIdx.x] = 0;
+  __syncthreads();
   int32_t s0 = chunk_start[q];
   int32_t s1 = min(s0 + kTreeChunk, end[ls + j]);
-  uint8_t mask = splitmask[j];
   const long long mk[3] = {okey(mid[(int64_t)j * 3]), okey(mid[(int64_t)j * 3 + 1]),
                            okey(mid[(int64_t)j * 3 + 2])};
   const int lane = threadIdx.x & 31;
@@ -257,7 +262,8 @@ __global__ void k_tree_children(int32_t nl, int32_t ls, int32_t le, int32_t lvl,
 
 __global__ void k_tree_scatter(int32_t ls, const int32_t* __restrict__ chunk_cluster,
                                const int32_t* __restrict__ chunk_start,
-                               const int32_t* __restrict__ end, const uint8_t* __restrict__ code,
+                               const int32_t* __restrict__ end, const uint8_t* __restrict__ splitmask,
+                               const uint8_t* __restrict__ code,
                                const int32_t* __restrict__ chunk_base, const double* __restrict__ x,
                                const double* __restrict__ y, const double* __restrict__ z,
                                const int32_t* __restrict__ perm, double* __restrict__ x2,
@@ -271,6 +277,15 @@ __global__ void k_tree_scatter(int32_t ls, const int32_t* __restrict__ chunk_clu
   int q = blockIdx.x;
   int32_t s0 = chunk_start[q];
   int32_t s1 = min(s0 + kTreeChunk, end[ls + chunk_cluster[q]]);
+  if (!splitmask[chunk_cluster[q]]) {   // a leaf: same positions in the other buffer
+    for (int32_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
+      x2[i] = x[i];
+      y2[i] = y[i];
+      z2[i] = z[i];
+      perm2[i] = perm[i];
+    }
+    return;
+  }
   if (threadIdx.x < 8) {
     running[threadIdx.x] = 0;
     base[threadIdx.x] = chunk_base[(int64_t)q * 8 + threadIdx.x];
@@ -502,33 +517,41 @@ int build_tree(Tree& T, const double* coords, int32_t n, const std::vector<int32
 
   T.level_start.assign({0, nroots});
   T.nroots = nroots;
+  // per-level scratch, grown with the level (nl clusters, tc particle chunks)
+  uint8_t* splitmask = nullptr;
+  double* mid = nullptr;
+  int32_t *nchunks = nullptr, *chunk_off = nullptr, *chunk_cluster = nullptr, *chunk_start = nullptr,
+          *counts = nullptr, *chunk_base = nullptr, *child_cnt = nullptr, *nch = nullptr,
+          *child_off = nullptr;
+  size_t c_sm = 0, c_mid = 0, c_nq = 0, c_qo = 0, c_qc = 0, c_qs = 0, c_cnt = 0, c_cb = 0, c_cc = 0,
+         c_nch = 0, c_co = 0;
+  int32_t* tot2 = nullptr;   // [0] chunks of the level, [1] clusters that split
+  BL_TRY(dalloc_n(&tot2, 2, s));
+  // Particles of a cluster that stays a leaf are copied into the other buffer
+  // at its level, so both buffers hold them from then on and later levels only
+  // touch the clusters they split.
   for (int lvl = 0;; ++lvl) {
     int32_t ls = T.level_start[lvl], le = T.level_start[lvl + 1], nl = le - ls;
-    uint8_t* splitmask = nullptr;
-    double* mid = nullptr;
-    int32_t *nchunks = nullptr, *chunk_off = nullptr;
-    BL_TRY(dalloc_n(&splitmask, nl, s));
-    BL_TRY(dalloc_n(&mid, (size_t)nl * 3, s));
-    BL_TRY(dalloc_n(&nchunks, nl, s));
-    BL_TRY(dalloc_n(&chunk_off, nl, s));
+    BL_TRY(dgrow(&splitmask, &c_sm, (size_t)nl, 0, s));
+    BL_TRY(dgrow(&mid, &c_mid, (size_t)nl * 3, 0, s));
+    BL_TRY(dgrow(&nchunks, &c_nq, (size_t)nl, 0, s));
+    BL_TRY(dgrow(&chunk_off, &c_qo, (size_t)nl, 0, s));
+    BL_CUDA(cudaMemsetAsync(tot2 + 1, 0, sizeof(int32_t), s));
     k_tree_decide<<<nblk(nl, 128), 128, 0, s>>>(ls, nl, T.begin, T.end, T.box, max_leaf, splitmask,
-                                                mid, nchunks, T.first_child, T.nchild);
+                                                mid, nchunks, T.first_child, T.nchild, tot2 + 1);
     BL_LAUNCHED(cnt.launches);
-    int32_t tc = 0;
-    BL_TRY(scan_exclusive(nchunks, chunk_off, nl, &tc, s, cnt));
-    if (tc == 0) {
-      dfree(splitmask, s); dfree(mid, s); dfree(nchunks, s); dfree(chunk_off, s);
-      break;
-    }
-    int32_t *chunk_cluster = nullptr, *chunk_start = nullptr, *counts = nullptr,
-            *chunk_base = nullptr, *child_cnt = nullptr, *nch = nullptr, *child_off = nullptr;
-    BL_TRY(dalloc_n(&chunk_cluster, tc, s));
-    BL_TRY(dalloc_n(&chunk_start, tc, s));
-    BL_TRY(dalloc_n(&counts, (size_t)tc * 8, s));
-    BL_TRY(dalloc_n(&chunk_base, (size_t)tc * 8, s));
-    BL_TRY(dalloc_n(&child_cnt, (size_t)nl * 8, s));
-    BL_TRY(dalloc_n(&nch, nl, s));
-    BL_TRY(dalloc_n(&child_off, nl, s));
+    BL_TRY(scan_exclusive_dev(nchunks, chunk_off, nl, tot2, s, cnt));
+    int32_t h2[2];
+    BL_TRY(read_device(tot2, h2, sizeof(h2), s));
+    const int32_t tc = h2[0];
+    if (h2[1] == 0) break;   // no cluster of this level splits
+    BL_TRY(dgrow(&chunk_cluster, &c_qc, (size_t)tc, 0, s));
+    BL_TRY(dgrow(&chunk_start, &c_qs, (size_t)tc, 0, s));
+    BL_TRY(dgrow(&counts, &c_cnt, (size_t)tc * 8, 0, s));
+    BL_TRY(dgrow(&chunk_base, &c_cb, (size_t)tc * 8, 0, s));
+    BL_TRY(dgrow(&child_cnt, &c_cc, (size_t)nl * 8, 0, s));
+    BL_TRY(dgrow(&nch, &c_nch, (size_t)nl, 0, s));
+    BL_TRY(dgrow(&child_off, &c_co, (size_t)nl, 0, s));
     k_tree_chunks<<<nblk(tc, 256), 256, 0, s>>>(nl, ls, chunk_off, tc, T.begin, chunk_cluster,
                                                 chunk_start);
     BL_LAUNCHED(cnt.launches);
@@ -545,11 +568,7 @@ int build_tree(Tree& T, const double* coords, int32_t n, const std::vector<int32
                                                   T.begin, T.end, T.parent, T.level, T.first_child,
                                                   T.nchild, T.problem);
     BL_LAUNCHED(cnt.launches);
-    BL_CUDA(cudaMemcpyAsync(x2, T.x, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
-    BL_CUDA(cudaMemcpyAsync(y2, T.y, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
-    BL_CUDA(cudaMemcpyAsync(z2, T.z, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
-    BL_CUDA(cudaMemcpyAsync(perm2, T.perm, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
-    k_tree_scatter<<<tc, kTreeThreads, 0, s>>>(ls, chunk_cluster, chunk_start, T.end, code,
+    k_tree_scatter<<<tc, kTreeThreads, 0, s>>>(ls, chunk_cluster, chunk_start, T.end, splitmask, code,
                                                chunk_base, T.x, T.y, T.z, T.perm, x2, y2, z2, perm2);
     BL_LAUNCHED(cnt.launches);
     { double* t = T.x; T.x = x2; x2 = t; }
@@ -558,10 +577,10 @@ int build_tree(Tree& T, const double* coords, int32_t n, const std::vector<int32
     { int32_t* t = T.perm; T.perm = perm2; perm2 = t; }
     BL_TRY(cluster_boxes(T, le, nc, n, s, cnt));
     T.level_start.push_back(le + nc);
-    dfree(splitmask, s); dfree(mid, s); dfree(nchunks, s); dfree(chunk_off, s);
-    dfree(chunk_cluster, s); dfree(chunk_start, s); dfree(counts, s); dfree(chunk_base, s);
-    dfree(child_cnt, s); dfree(nch, s); dfree(child_off, s);
   }
+  dfree(splitmask, s); dfree(mid, s); dfree(nchunks, s); dfree(chunk_off, s);
+  dfree(chunk_cluster, s); dfree(chunk_start, s); dfree(counts, s); dfree(chunk_base, s);
+  dfree(child_cnt, s); dfree(nch, s); dfree(child_off, s); dfree(tot2, s);
   dfree(x2, s); dfree(y2, s); dfree(z2, s); dfree(perm2, s); dfree(code, s);
 
   T.nclusters = T.level_start.back();
