@@ -118,6 +118,7 @@ def test_device_direct_sum_matches_oracle():
     ("all_identical", np.full((3, 700), 0.25)),
     ("flat_plane", None),
     ("duplicated_pairs", None),
+    ("signed_zeros", None),
 ])
 def test_degenerate_inputs(name, pts):
     rng = np.random.default_rng(11)
@@ -135,6 +136,21 @@ def test_degenerate_inputs(name, pts):
         tgt[2] = 0.0
         src = tgt
         q = rng.uniform(-1, 1, 3000)
+        kw = dict(n=4, theta=0.7, N0=40, M0=40)
+    elif name == "signed_zeros":
+        # root box [-1, 1]^3, so the first midpoints are exactly 0; a fifth of
+        # the coordinates are -0.0 or +0.0, which FP64 compares as equal (the
+        # tree's integer keys must too)
+        tgt = rng.uniform(-1, 1, (3, 2000))
+        tgt[:, :6] = [[-1, 1, 0, 0, 0, 0], [0, 0, -1, 1, 0, 0], [0, 0, 0, 0, -1, 1]]
+        zero = rng.random((3, 2000)) < 0.2
+        neg = rng.random((3, 2000)) < 0.5
+        zero[:, :6] = False
+        tgt[zero & neg] = -0.0
+        tgt[zero & ~neg] = 0.0
+        assert np.signbit(tgt[zero & neg]).all()
+        src = tgt
+        q = rng.uniform(-1, 1, 2000)
         kw = dict(n=4, theta=0.7, N0=40, M0=40)
     else:
         base = rng.uniform(-1, 1, (3, 1500))
@@ -188,6 +204,16 @@ def test_invalid_inputs_on_device():
     with pytest.raises(B.BLDTTError) as e:
         B.Plan(to_dev(tgt), to_dev(src), to_dev(qb), n=3, N0=20, M0=20)
     assert e.value.status == 1
+    # a bad source coordinate, found by the source-tree build (second stream)
+    bad_src = src.copy()
+    bad_src[2, 400] = -np.inf
+    with pytest.raises(B.BLDTTError) as e:
+        B.Plan(to_dev(tgt), to_dev(bad_src), to_dev(q), n=3, N0=20, M0=20)
+    assert e.value.status == 1
+    # the library stays usable after the errors
+    phi, plan = run_gpu(tgt, src.copy(), q, n=3, theta=0.7, N0=20, M0=20, precision=B.FP64)
+    plan.close()
+    assert np.all(np.isfinite(phi))
 
 
 def test_plain_fp64_workload_full_size():
