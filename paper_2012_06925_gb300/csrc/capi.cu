@@ -124,14 +124,14 @@ float fp32_parameter(int kernel, double kappa) {
 // built on a second stream by a helper thread while this thread builds the
 // target tree (each build synchronises with the host once per level, so one
 // thread would serialise the two).  The stream of the call then waits for both.
-static int build_two_trees(bldtt_plan* p, const double* targets, const double* sources, int* bad,
+static int build_two_trees(bldtt_plan* p, const double* targets, const double* sources,
                            cudaStream_t s) {
   cudaStream_t s2 = nullptr;
   cudaEvent_t go = nullptr, done = nullptr;
   BL_CUDA(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
   BL_CUDA(cudaEventCreateWithFlags(&go, cudaEventDisableTiming));
   BL_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
-  BL_CUDA(cudaEventRecord(go, s));   // the inputs and the flag, as of this call
+  BL_CUDA(cudaEventRecord(go, s));   // the inputs, as of this call
   BL_CUDA(cudaStreamWaitEvent(s2, go, 0));
   Counters c2;
   int rc2 = BLDTT_OK;
@@ -143,11 +143,11 @@ static int build_two_trees(bldtt_plan* p, const double* targets, const double* s
       err2 = "cudaSetDevice failed in the source-tree thread";
       return;
     }
-    rc2 = build_tree(p->st, sources, (int32_t)p->N, p->s_off, p->N0, p->n, bad, s2, c2);
+    rc2 = build_tree(p->st, sources, (int32_t)p->N, p->s_off, p->N0, p->n, s2, c2);
     if (rc2 == BLDTT_OK) rc2 = morton_order_leaves(p->st, p->N0, s2, c2);
     if (rc2 != BLDTT_OK) err2 = last_error();
   });
-  int rc1 = build_tree(p->tt, targets, (int32_t)p->M, p->t_off, p->M0, p->n, bad, s, p->setup_counter);
+  int rc1 = build_tree(p->tt, targets, (int32_t)p->M, p->t_off, p->M0, p->n, s, p->setup_counter);
   if (rc1 == BLDTT_OK) rc1 = morton_order_leaves(p->tt, p->M0, s, p->setup_counter);
   worker.join();
   p->setup_counter.launches += c2.launches;
@@ -191,30 +191,32 @@ int setup_impl(bldtt_plan* p, const double* targets, const double* sources, cons
   BL_TRY(dalloc_n(&bad, 1, s));
   BL_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
   BL_CUDA(cudaEventRecord(p->ev[0], s));
-  // Targets that are the sources, with the same leaf size and problem
-  // offsets, give two identical trees (the build is deterministic): build one
-  // and let the source tree alias it.
-  p->shared_tree = targets == sources && p->M == p->N && p->M0 == p->N0 && p->t_off == p->s_off;
-  if (p->shared_tree) {
-    BL_TRY(build_tree(p->tt, targets, (int32_t)p->M, p->t_off, p->M0, p->n, bad, s,
-                      p->setup_counter));
-    BL_TRY(morton_order_leaves(p->tt, p->M0, s, p->setup_counter));
-    p->st = p->tt;
-  } else {
-    BL_TRY(build_two_trees(p, targets, sources, bad, s));
-  }
-  BL_TRY(dalloc_n(&p->q_tree, p->N, s));
-  BL_TRY(permute_charges(p, charges, s));
-  BL_TRY(check_finite(p->q_tree, p->N, bad, s, p->setup_counter));
-  BL_CUDA(cudaEventRecord(p->ev[1], s));
+  // Reject non-finite input before any tree is built: a box of infinite
+  // extent would be split without end.
+  BL_TRY(check_finite(targets, 3 * p->M, bad, s, p->setup_counter));
+  if (sources != targets) BL_TRY(check_finite(sources, 3 * p->N, bad, s, p->setup_counter));
+  BL_TRY(check_finite(charges, p->N, bad, s, p->setup_counter));
   int h_bad = 0;
-  BL_CUDA(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
-  BL_CUDA(cudaStreamSynchronize(s));
+  BL_TRY(read_device(bad, &h_bad, sizeof(int), s));
   dfree(bad, s);
   if (h_bad) {
     set_error("a target, source or charge value is not finite");
     return BLDTT_EINVAL;
   }
+  // Targets that are the sources, with the same leaf size and problem
+  // offsets, give two identical trees (the build is deterministic): build one
+  // and let the source tree alias it.
+  p->shared_tree = targets == sources && p->M == p->N && p->M0 == p->N0 && p->t_off == p->s_off;
+  if (p->shared_tree) {
+    BL_TRY(build_tree(p->tt, targets, (int32_t)p->M, p->t_off, p->M0, p->n, s, p->setup_counter));
+    BL_TRY(morton_order_leaves(p->tt, p->M0, s, p->setup_counter));
+    p->st = p->tt;
+  } else {
+    BL_TRY(build_two_trees(p, targets, sources, s));
+  }
+  BL_TRY(dalloc_n(&p->q_tree, p->N, s));
+  BL_TRY(permute_charges(p, charges, s));
+  BL_CUDA(cudaEventRecord(p->ev[1], s));
   BL_TRY(setup_degrees(p, s));
   BL_TRY(build_lists(p, s));
   BL_TRY(build_work_items(p, s));

@@ -322,8 +322,9 @@ int check_finite(const double* v, int64_t n, int* bad_dev, cudaStream_t s, Count
 
 // ---- trees (tree.cu) ----
 // roots: host offsets (nroots + 1 entries) of the problems' particle ranges.
+// The coordinates must be finite (the set-up checks them first).
 int build_tree(Tree& T, const double* coords_user, int32_t n, const std::vector<int32_t>& roots,
-               int32_t max_leaf, int degree, int* bad_dev, cudaStream_t s, Counters& c);
+               int32_t max_leaf, int degree, cudaStream_t s, Counters& c);
 // Reorder the particles inside every leaf along a Morton curve of the leaf's box.
 int morton_order_leaves(Tree& T, int32_t max_leaf, cudaStream_t s, Counters& c);
 void free_tree(Tree& T, cudaStream_t s);

@@ -480,8 +480,13 @@ static int grow_clusters(Tree& T, size_t need, size_t keep, cudaStream_t s) {
 }
 
 
+// Levels past this many mean a cluster that the midpoint rule cannot
+// separate (e.g. more than max_leaf points on two adjacent doubles whose
+// midpoint rounds to the lower one); the build stops with an error.
+constexpr int kMaxTreeLevels = 2048;
+
 int build_tree(Tree& T, const double* coords, int32_t n, const std::vector<int32_t>& roots,
-               int32_t max_leaf, int degree, int* bad_dev, cudaStream_t s, Counters& cnt) {
+               int32_t max_leaf, int degree, cudaStream_t s, Counters& cnt) {
   T.n = n;
   double *x2 = nullptr, *y2 = nullptr, *z2 = nullptr;
   int32_t* perm2 = nullptr;
@@ -507,9 +512,6 @@ int build_tree(Tree& T, const double* coords, int32_t n, const std::vector<int32
     k_tree_roots<<<nblk(nroots, 128), 128, 0, s>>>(nroots, d_roots, T.begin, T.end, T.parent,
                                                    T.level, T.problem);
     BL_LAUNCHED(cnt.launches);
-    BL_TRY(check_finite(T.x, n, bad_dev, s, cnt));
-    BL_TRY(check_finite(T.y, n, bad_dev, s, cnt));
-    BL_TRY(check_finite(T.z, n, bad_dev, s, cnt));
     // root boxes: the minimal bounding box of each problem's particles (Sec. 2.3)
     BL_TRY(cluster_boxes(T, 0, nroots, n, s, cnt));
     dfree(d_roots, s);
@@ -530,7 +532,14 @@ int build_tree(Tree& T, const double* coords, int32_t n, const std::vector<int32
   // Particles of a cluster that stays a leaf are copied into the other buffer
   // at its level, so both buffers hold them from then on and later levels only
   // touch the clusters they split.
+  int status = BLDTT_OK;
   for (int lvl = 0;; ++lvl) {
+    if (lvl >= kMaxTreeLevels) {   // only clusters that no midpoint split separates get here
+      set_error("tree deeper than %d levels: some cluster is not separated by its midpoints",
+                kMaxTreeLevels);
+      status = BLDTT_EINTERNAL;
+      break;
+    }
     int32_t ls = T.level_start[lvl], le = T.level_start[lvl + 1], nl = le - ls;
     BL_TRY(dgrow(&splitmask, &c_sm, (size_t)nl, 0, s));
     BL_TRY(dgrow(&mid, &c_mid, (size_t)nl * 3, 0, s));
@@ -581,6 +590,10 @@ int build_tree(Tree& T, const double* coords, int32_t n, const std::vector<int32
   dfree(splitmask, s); dfree(mid, s); dfree(nchunks, s); dfree(chunk_off, s);
   dfree(chunk_cluster, s); dfree(chunk_start, s); dfree(counts, s); dfree(chunk_base, s);
   dfree(child_cnt, s); dfree(nch, s); dfree(child_off, s); dfree(tot2, s);
+  if (status != BLDTT_OK) {
+    dfree(x2, s); dfree(y2, s); dfree(z2, s); dfree(perm2, s); dfree(code, s);
+    return status;
+  }
   dfree(x2, s); dfree(y2, s); dfree(z2, s); dfree(perm2, s); dfree(code, s);
 
   T.nclusters = T.level_start.back();

@@ -30,7 +30,7 @@ def _rank(rank, world, port, times, out):
 @pytest.mark.parametrize("times", [(120.0, 80.0), (50.0, 50.0), (10.0, 400.0)])
 def test_slowest_rank_times_the_job(times):
     world = 2
-    manager = mp.Manager()
+    manager = mp.get_context("spawn").Manager()   # no fork of a threaded process
     out = manager.dict()
     mp.spawn(_rank, args=(world, _free_port(), list(times), out), nprocs=world, join=True)
     worst = max(times)
