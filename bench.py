@@ -246,12 +246,33 @@ def code_hash(*paths):
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()
 
 
-INTERACT_SOURCES = ("interact.cu", "internal.cuh")   # the kernel and its constants
+def _kernel_header_code(path):
+    """The parts of the shared header that the interaction kernel compiles
+    with: its constants and its device helper functions."""
+    keep, in_fn = [], False
+    with open(path) as f:
+        for line in f:
+            code = line.split("//", 1)[0].rstrip()
+            if code.lstrip().startswith("constexpr"):
+                keep.append(code.strip())
+            if "__device__" in code:
+                in_fn = True
+            if in_fn:
+                if code.strip():
+                    keep.append(code.strip())
+                if code == "}":
+                    in_fn = False
+    return "\n".join(keep)
 
 
 def interact_code_hash():
+    """sha256 of the interaction kernel's code: interact.cu (code lines) and
+    the constants and device helpers of internal.cuh."""
+    import hashlib
     csrc = os.path.join(ROOT, "paper_2012_06925_gb300", "csrc")
-    return code_hash(*(os.path.join(csrc, f) for f in INTERACT_SOURCES))
+    h = hashlib.sha256(code_hash(os.path.join(csrc, "interact.cu")).encode())
+    h.update(_kernel_header_code(os.path.join(csrc, "internal.cuh")).encode())
+    return h.hexdigest()
 
 
 def interact_traffic():
