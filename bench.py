@@ -759,7 +759,8 @@ def run_gpu_learned(args):
                                                                   "downward", "compute")}},
         "speedup_vs_fixed_rule": fixed_ms / total_ms,
         "selector": {"train_seconds": t_train, "pairs": report["pairs"], "loss": report["loss"],
-                     "log10_pair_budget": report["log_eps"], "degrees": list(sel.degrees)},
+                     "log10_pair_budget": report["log_eps"], "separation_cap": report["sep_cap"],
+                     "degrees": list(sel.degrees)},
         "phases_ms": {k: st["ms_" + k] for k in ("tree", "lists", "upward", "interact", "downward",
                                                   "compute")},
         "interactions": {"PP": st["interactions"][0], "PC": st["interactions"][1],

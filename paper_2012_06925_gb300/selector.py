@@ -9,9 +9,10 @@ theta (the pairs a traversal actually meets near its accept/reject
 boundary), their features and FP64 error labels come from the library's
 kernels (bldtt_pair_features, bldtt_pair_errors), and the network is trained
 by the library's forward/backward/Adam kernels (bldtt_mlp_gradients,
-bldtt_mlp_adam).  The per-pair budget is then calibrated on a separate
-problem against the FP64 direct sum so that the whole potential meets a
-global relative-l2 budget.  This module only orchestrates those calls.
+bldtt_mlp_adam).  The per-pair budget and a cap on the separation feature
+are then calibrated on a separate problem against the FP64 direct sum so that
+the whole potential meets a global relative-l2 budget.  This module only
+orchestrates those calls.
 """
 from __future__ import annotations
 
@@ -154,31 +155,50 @@ def sampled_error(points, charges, phi, sample_idx, kernel=B.COULOMB, kappa=0.0,
     return float(np.sqrt(np.sum((got - ref) ** 2) / np.sum(ref ** 2)))
 
 
+SEP = 4                      # index of the separation feature (r_t + r_s)/R
+
+
 def calibrate(params, lo, hi, points, charges, budget=1e-6, degrees=DEGREES, leaf=2000, theta=0.7,
-              candidates=(-5.0, -5.5, -6.0, -6.5, -7.0, -7.5, -8.0), safety=0.5, samples=2000,
+              candidates=(-5.0, -5.25, -5.5, -5.75, -6.0, -6.25, -6.5, -7.0, -7.5, -8.0),
+              sep_caps=(0.8, 0.85, 0.9, 0.95), safety=0.5, samples=2000,
               kernel=B.COULOMB, kappa=0.0, seed=0, precision=B.FP32_BULK):
-    """The loosest per-pair log10 budget whose whole-potential error on this
-    problem stays below safety * budget (FP64 direct sum on sampled targets).
-    Returns (log_eps, table of (log_eps, error, evaluations))."""
+    """The per-pair log10 budget and the cap on the separation feature that
+    do the least work while the whole-potential error on this problem stays
+    below safety * budget (FP64 direct sum on sampled targets).  A pair whose
+    separation ratio exceeds the cap falls outside the selector's box and
+    takes the fixed rule, which for such pairs means descending: the pairs
+    near the MAC boundary are the ones whose errors the network extrapolates
+    worst (without a cap the whole-potential error jumps by four decades
+    between two neighbouring budgets).
+    Returns (log_eps, sep_cap, table of (log_eps, error, evaluations) at the
+    chosen cap, grid of (sep_cap, log_eps, error, evaluations))."""
     import torch
     rng = np.random.default_rng(seed)
     idx = rng.choice(points.shape[1], size=min(samples, points.shape[1]), replace=False)
     dt = torch.from_numpy(np.ascontiguousarray(points)).cuda()
     dq = torch.from_numpy(np.ascontiguousarray(charges)).cuda()
-    table = []
-    chosen = None
-    for le in sorted(candidates, reverse=True):
-        sel = B.Selector(degrees, params, lo, hi, log10_budget=le)
-        with B.Plan.learned(dt, dt, dq, sel, kernel=kernel, kappa=kappa, theta=theta, N0=leaf, M0=leaf,
-                            precision=precision) as plan:
-            phi = plan.compute().cpu().numpy()
-            plan.check_error()
-            ev = sum(plan.stats()["interactions"])
-        e = sampled_error(points, charges, phi, idx, kernel, kappa)
-        table.append((le, e, ev))
-        if chosen is None and e <= safety * budget:
-            chosen = le
-    return (chosen if chosen is not None else min(candidates)), table
+    grid = []
+    best = None
+    for cap in sep_caps:
+        h = np.array(hi, dtype=np.float32)
+        h[SEP] = min(h[SEP], np.float32(cap))
+        for le in sorted(candidates, reverse=True):
+            sel = B.Selector(degrees, params, lo, h, log10_budget=le)
+            with B.Plan.learned(dt, dt, dq, sel, kernel=kernel, kappa=kappa, theta=theta, N0=leaf,
+                                M0=leaf, precision=precision) as plan:
+                phi = plan.compute().cpu().numpy()
+                plan.check_error()
+                ev = sum(plan.stats()["interactions"])
+            e = sampled_error(points, charges, phi, idx, kernel, kappa)
+            grid.append((cap, le, e, ev))
+            if e <= safety * budget:
+                if best is None or ev < best[3]:
+                    best = (cap, le, e, ev)
+                break   # tighter budgets at this cap only cost more
+    if best is None:   # nothing met the budget: the tightest candidate at the tightest cap
+        best = (min(sep_caps), min(candidates), float("nan"), float("nan"))
+    table = [(le, e, ev) for cap, le, e, ev in grid if cap == best[0]]
+    return best[1], best[0], table, grid
 
 
 def training_problems(kind_sizes=(("uniform", 400_000), ("uniform", 150_000), ("plummer", 300_000)),
@@ -208,11 +228,14 @@ def train_selector(budget=1e-6, degrees=DEGREES, leaf=2000, theta=0.7, kernel=B.
     if calib is None:
         calib = W.make_problem("uniform", 200_000, seed=seed + 200)[::2]
     cp, cq = calib
-    log_eps, table = calibrate(params, lo, hi, cp, cq, budget, degrees, leaf, theta, kernel=kernel,
-                               kappa=kappa, seed=seed)
+    log_eps, cap, table, grid = calibrate(params, lo, hi, cp, cq, budget, degrees, leaf, theta,
+                                          kernel=kernel, kappa=kappa, seed=seed)
+    hi = hi.copy()
+    hi[SEP] = min(hi[SEP], np.float32(cap))
     t3 = time.time()
     report = dict(pairs=len(data), loss=loss, label_seconds=t1 - t0, train_seconds=t2 - t1,
-                  calibrate_seconds=t3 - t2, log_eps=log_eps, calibration=table)
+                  calibrate_seconds=t3 - t2, log_eps=log_eps, sep_cap=cap, calibration=table,
+                  calibration_grid=grid)
     if log:
         log(report)
     return B.Selector(degrees, params, lo, hi, log10_budget=log_eps), report

@@ -27,9 +27,21 @@ def test_training_converges(trained):
     sel, report = trained
     assert report["pairs"] > 10_000
     assert report["loss"] < 1.0                      # mean squared error in decades^2
-    # a looser per-pair budget buys less work and a larger error
-    table = sorted(report["calibration"])
-    assert table[-1][2] < table[0][2] and table[-1][1] > table[0][1]
+    # at every separation cap, a looser per-pair budget buys less work and a
+    # larger error (the calibration walks each cap from the loosest budget
+    # down to the first that meets the target)
+    grid = report["calibration_grid"]
+    caps = sorted({g[0] for g in grid})
+    assert report["sep_cap"] in caps
+    walked = 0
+    for cap in caps:
+        rows = sorted((le, e, ev) for c, le, e, ev in grid if c == cap)
+        if len(rows) >= 2:
+            walked += 1
+            assert rows[-1][2] < rows[0][2] and rows[-1][1] > rows[0][1]
+    assert walked >= 1
+    # the capped selector reads pairs beyond the cap as outside its box
+    assert sel.hi[4] <= report["sep_cap"]
 
 
 def test_learned_selector_beats_the_fixed_rule(trained):
