@@ -168,6 +168,22 @@ struct SelParams {
   int net;   // 0: no network (MAC fallback everywhere)
 };
 
+// Per-warp scratch of k_select: the MLP's activations, then the inputs and
+// outputs of the warp's 32 pairs.
+constexpr int kSelOutMax = 3 * kMaxDegrees;
+constexpr int kSelWarpFloats = 2 * kHidden + 32 * 8 + 32 * kSelOutMax;
+
+__host__ __device__ inline size_t select_smem_bytes(int nout) {
+  size_t w = (size_t)sel_weight_count(nout) * sizeof(__nv_bfloat16);
+  w = (w + 15) / 16 * 16;
+  return w + (size_t)sel_bias_count(nout) * sizeof(float) +
+         (size_t)kSelWarps * kSelWarpFloats * sizeof(float);
+}
+
+// A warp takes 32 pairs at a time: each lane computes its pair's features (the
+// FP64 divisions and square root run on all lanes at once), the warp runs the
+// network for every pair inside the box in turn, and each lane decides its own
+// pair.  Same arithmetic as one pair per warp.
 __global__ void k_select(const int2* __restrict__ pairs, int32_t F, PairTrees T, SelParams sp,
                          const __nv_bfloat16* __restrict__ gw, const float* __restrict__ gb,
                          int16_t* __restrict__ choice) {
@@ -178,33 +194,41 @@ __global__ void k_select(const int2* __restrict__ pairs, int32_t F, PairTrees T,
   float* swarp = sb + sel_bias_count(sp.nout);
   if (sp.net) load_net(gw, gb, sp.nout, sw, sb);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* act = swarp + warp * (2 * kHidden + 8 + 32);
-  float* x = act + 2 * kHidden;
-  float* ys = x + 8;
+  float* act = swarp + warp * kSelWarpFloats;
+  float* xs = act + 2 * kHidden;      // [32][8]
+  float* ys = xs + 32 * 8;            // [32][kSelOutMax]
   const NetSmem net{sw, sb, sp.nout};
-  for (int64_t i = (int64_t)blockIdx.x * kSelWarps + warp; i < F; i += (int64_t)gridDim.x * kSelWarps) {
-    const int t = pairs[i].x, s = pairs[i].y;
+  const int64_t stride = (int64_t)gridDim.x * kSelWarps * 32;
+  for (int64_t base = ((int64_t)blockIdx.x * kSelWarps + warp) * 32; base < F; base += stride) {
+    const int64_t i = base + lane;
     int state = 0;   // 0 no approximation, 1 fallback, 2 network
-    if (lane == 0) {
+    int t = 0, s = 0;
+    if (i < F) {
+      t = pairs[i].x;
+      s = pairs[i].y;
       double f[kFeatures];
       if (pair_features(T, t, s, sp.kappa, f)) {
         state = sp.net ? 2 : 1;
         for (int d = 0; d < kFeatures; ++d) {
-          x[d] = bf16r(__double2float_rn(f[d]));
-          if (x[d] < sp.lo[d] || x[d] > sp.hi[d]) state = 1;
+          const float xd = bf16r(__double2float_rn(f[d]));
+          xs[lane * 8 + d] = xd;
+          if (xd < sp.lo[d] || xd > sp.hi[d]) state = 1;
         }
       }
     }
-    state = __shfl_sync(0xffffffffu, state, 0);
     __syncwarp();
-    if (state == 2) {
-      const float y = mlp_forward_warp(net, x, act, nullptr);
-      if (lane < sp.nout) ys[lane] = y;
+    unsigned todo = __ballot_sync(0xffffffffu, state == 2);
+    while (todo) {
+      const int j = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const float y = mlp_forward_warp(net, xs + j * 8, act, nullptr);
+      if (lane < sp.nout) ys[j * kSelOutMax + lane] = y;
       __syncwarp();
     }
-    if (lane == 0) {
+    if (i < F) {
       int16_t c = state == 0 ? kChoiceNoApprox : kChoiceFallback;
       if (state == 2) {
+        const float* y = ys + lane * kSelOutMax;
         const int64_t ct = T.te[t] - T.tb[t], cs = T.se[s] - T.sb[s];
         int best = -1;
         int64_t best_cost = 0;
@@ -212,7 +236,7 @@ __global__ void k_select(const int2* __restrict__ pairs, int32_t F, PairTrees T,
           const int64_t np = sp.np[di];
           const int64_t cost[3] = {ct * np, np * cs, np * np};
           for (int ty = 0; ty < 3; ++ty)
-            if (ys[3 * di + ty] <= sp.log_eps && (best < 0 || cost[ty] < best_cost)) {
+            if (y[3 * di + ty] <= sp.log_eps && (best < 0 || cost[ty] < best_cost)) {
               best = 1 + 3 * di + ty;
               best_cost = cost[ty];
             }
@@ -244,9 +268,9 @@ int select_pairs(bldtt_plan* p, const int2* pairs, int32_t F, int16_t* choice, c
   sp.log_eps = p->sel_log_eps;
   sp.kappa = p->kappa;
   sp.net = p->selector_net ? 1 : 0;
-  const size_t sm = net_smem_bytes(p->sel_nout);
+  const size_t sm = select_smem_bytes(p->sel_nout);
   BL_CUDA(cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  unsigned g = nblk(F, kSelWarps);
+  unsigned g = nblk(F, kSelWarps * 32);
   if (g > 4096) g = 4096;
   k_select<<<g, 32 * kSelWarps, sm, s>>>(pairs, F, pair_trees(p), sp,
                                           reinterpret_cast<const __nv_bfloat16*>(p->sel_w), p->sel_b,
