@@ -6,6 +6,7 @@ potentials FP64 to rel-l2 1e-12 and max-norm 1e-10, FP32_BULK to rel-l2 1e-6
 and max-norm 1e-5 (FP32 evaluation error, derived in the design notes)."""
 import numpy as np
 import pytest
+import torch
 
 import oracle as O
 from paper_2012_06925_gb300 import binding as B
@@ -233,3 +234,32 @@ def test_plain_fp64_workload_full_size():
     err = rel_l2(direct, phi)
     assert err == pytest.approx(rel_l2(direct, ref.phi), rel=1e-6)
     assert err < 1e-4
+
+
+def test_plans_release_their_memory():
+    """Set-ups and destroys in a loop (shared and separate trees, a batch, a
+    learned plan's degree set) leave the device's free memory where it was:
+    every plan's pool, pinned slots and arrays go with it."""
+    tgt, src, q = W.make_problem("uniform", 60_000, 40_000, seed=17, sources_kind="plummer")
+    dt, ds, dq = to_dev(tgt), to_dev(src), to_dev(q)
+    dq_t = to_dev(W.make_problem("uniform", 60_000, seed=17)[2])
+    torch.cuda.synchronize()
+
+    def cycle():
+        for prec in (B.FP64, B.FP32_BULK):
+            with B.Plan(dt, dt, dq_t, n=5, theta=0.7, N0=200, M0=200, precision=prec) as p:
+                p.compute()
+            with B.Plan(dt, ds, dq, n=5, theta=0.7, N0=200, M0=200, precision=prec) as p:
+                p.compute()
+        off = [0, 30_000, 60_000]
+        with B.Plan.batch(dt, off, dt, off, dq_t, [B.COULOMB, B.YUKAWA], [0.0, 0.5], n=4, N0=200,
+                          M0=200) as p:
+            p.compute()
+        torch.cuda.synchronize()
+
+    cycle()                                   # first use: library state, module loading
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(5):
+        cycle()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert abs(free1 - free0) < 64 << 20, (free0, free1)
