@@ -177,25 +177,38 @@ def calibrate(params, lo, hi, points, charges, budget=1e-6, degrees=DEGREES, lea
     idx = rng.choice(points.shape[1], size=min(samples, points.shape[1]), replace=False)
     dt = torch.from_numpy(np.ascontiguousarray(points)).cuda()
     dq = torch.from_numpy(np.ascontiguousarray(charges)).cuda()
+
+    def measure(cap, le):
+        h = np.array(hi, dtype=np.float32)
+        h[SEP] = min(h[SEP], np.float32(cap))
+        sel = B.Selector(degrees, params, lo, h, log10_budget=le)
+        with B.Plan.learned(dt, dt, dq, sel, kernel=kernel, kappa=kappa, theta=theta, N0=leaf,
+                            M0=leaf, precision=precision) as plan:
+            phi = plan.compute().cpu().numpy()
+            plan.check_error()
+            ev = sum(plan.stats()["interactions"])
+        return sampled_error(points, charges, phi, idx, kernel, kappa), ev
+
+    return choose_calibration(measure, sep_caps, candidates, safety * budget)
+
+
+def choose_calibration(measure, sep_caps, candidates, target):
+    """The calibration walk: at each cap, budgets from the loosest down to the
+    first whose error (measure(cap, log_eps) -> (error, evaluations)) is at most
+    `target`; among those, the one with the fewest evaluations.  If none meets
+    the target, the tightest budget at the tightest cap.  Returns (log_eps,
+    sep_cap, table at the chosen cap, grid)."""
     grid = []
     best = None
     for cap in sep_caps:
-        h = np.array(hi, dtype=np.float32)
-        h[SEP] = min(h[SEP], np.float32(cap))
         for le in sorted(candidates, reverse=True):
-            sel = B.Selector(degrees, params, lo, h, log10_budget=le)
-            with B.Plan.learned(dt, dt, dq, sel, kernel=kernel, kappa=kappa, theta=theta, N0=leaf,
-                                M0=leaf, precision=precision) as plan:
-                phi = plan.compute().cpu().numpy()
-                plan.check_error()
-                ev = sum(plan.stats()["interactions"])
-            e = sampled_error(points, charges, phi, idx, kernel, kappa)
+            e, ev = measure(cap, le)
             grid.append((cap, le, e, ev))
-            if e <= safety * budget:
+            if e <= target:
                 if best is None or ev < best[3]:
                     best = (cap, le, e, ev)
                 break   # tighter budgets at this cap only cost more
-    if best is None:   # nothing met the budget: the tightest candidate at the tightest cap
+    if best is None:
         best = (min(sep_caps), min(candidates), float("nan"), float("nan"))
     table = [(le, e, ev) for cap, le, e, ev in grid if cap == best[0]]
     return best[1], best[0], table, grid
