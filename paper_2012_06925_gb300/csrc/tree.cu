@@ -647,20 +647,46 @@ __device__ __forceinline__ uint32_t spread10(uint32_t v) {
   return v;
 }
 
-// 10-bit cell of a coordinate in [lo, lo + 1024 / scale): an ordering key
-// only, so FP32 suffices (scale = 0 for a zero-width box).
-__device__ __forceinline__ uint32_t quantize10(double v, float lo, float scale) {
+// Cell of a coordinate in [lo, lo + cells / scale), 0..cells-1: an ordering
+// key only, so FP32 suffices (scale = 0 for a zero-width box).
+__device__ __forceinline__ uint32_t quantize(double v, float lo, float scale, int cells) {
   const int q = (int)(__fsub_rn((float)v, lo) * scale);
-  return (uint32_t)(q < 0 ? 0 : (q > 1023 ? 1023 : q));
+  return (uint32_t)(q < 0 ? 0 : (q >= cells ? cells - 1 : q));
 }
 
+// Sort keys: the Morton code of the point's cell above its position in the
+// leaf (unique keys, ties by position).  32-bit keys (7 bits per dimension,
+// 11 position bits) for leaves of up to 2048 points, 64-bit keys (10 bits per
+// dimension) above: the sort is bound by shared-memory traffic.
+template <typename Key>
+struct MortonKey;
+template <>
+struct MortonKey<uint32_t> {
+  static constexpr int kBits = 7, kMaxPoints = 2048;
+  __device__ static uint32_t make(uint32_t code, int i) { return (code << 11) | (uint32_t)i; }
+  __device__ static int index(uint32_t k) { return (int)(k & 0x7ffu); }
+  __device__ static uint32_t none() { return ~0u; }
+};
+template <>
+struct MortonKey<unsigned long long> {
+  static constexpr int kBits = 10, kMaxPoints = 1 << 30;
+  __device__ static unsigned long long make(uint32_t code, int i) {
+    return ((unsigned long long)code << 32) | (unsigned)i;
+  }
+  __device__ static int index(unsigned long long k) { return (int)(k & 0xffffffffu); }
+  __device__ static unsigned long long none() { return ~0ull; }
+};
+
+template <typename Key>
 __global__ void __launch_bounds__(kMortonThreads) k_leaf_morton(
     const int32_t* __restrict__ leaf_ids, const int32_t* __restrict__ begin,
     const int32_t* __restrict__ end, const double* __restrict__ box, const double* __restrict__ x,
     const double* __restrict__ y, const double* __restrict__ z, const int32_t* __restrict__ perm,
     double* __restrict__ x2, double* __restrict__ y2, double* __restrict__ z2,
     int32_t* __restrict__ perm2, int cap) {
-  extern __shared__ unsigned long long key[];   // [cap], cap a power of two
+  using MK = MortonKey<Key>;
+  extern __shared__ __align__(16) unsigned char kraw[];
+  Key* key = reinterpret_cast<Key*>(kraw);   // [cap], cap a power of two
   const int c = leaf_ids[blockIdx.x];
   const int32_t b = begin[c];
   const int m = end[c] - b;
@@ -676,20 +702,21 @@ __global__ void __launch_bounds__(kMortonThreads) k_leaf_morton(
   int n2 = 1;
   while (n2 < m) n2 <<= 1;
   const double* bx = box + (int64_t)c * 6;
+  constexpr int kCells = 1 << MK::kBits;
   float lo[3], sc[3];
   for (int d = 0; d < 3; ++d) {
     lo[d] = (float)bx[d];
     const float e = (float)bx[3 + d] - lo[d];
-    sc[d] = e > 0.f ? 1024.f / e : 0.f;
+    sc[d] = e > 0.f ? (float)kCells / e : 0.f;
   }
   for (int i = threadIdx.x; i < n2; i += blockDim.x) {
     if (i < m) {
-      uint32_t code = (spread10(quantize10(x[b + i], lo[0], sc[0])) << 2) |
-                      (spread10(quantize10(y[b + i], lo[1], sc[1])) << 1) |
-                      spread10(quantize10(z[b + i], lo[2], sc[2]));
-      key[i] = ((unsigned long long)code << 32) | (unsigned)i;   // unique: ties by position
+      const uint32_t code = (spread10(quantize(x[b + i], lo[0], sc[0], kCells)) << 2) |
+                            (spread10(quantize(y[b + i], lo[1], sc[1], kCells)) << 1) |
+                            spread10(quantize(z[b + i], lo[2], sc[2], kCells));
+      key[i] = MK::make(code, i);
     } else {
-      key[i] = ~0ull;
+      key[i] = MK::none();
     }
   }
   __syncthreads();
@@ -698,7 +725,7 @@ __global__ void __launch_bounds__(kMortonThreads) k_leaf_morton(
       for (int t = threadIdx.x; t < (n2 >> 1); t += blockDim.x) {   // one compare-exchange each
         const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));          // lower index of pair t
         const int ixj = i | j;
-        const unsigned long long a = key[i], bb = key[ixj];
+        const Key a = key[i], bb = key[ixj];
         const bool up = (i & k) == 0;
         if ((a > bb) == up) {
           key[i] = bb;
@@ -709,7 +736,7 @@ __global__ void __launch_bounds__(kMortonThreads) k_leaf_morton(
     }
   }
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    int src = b + (int)(key[i] & 0xffffffffu);
+    const int src = b + MK::index(key[i]);
     x2[b + i] = x[src];
     y2[b + i] = y[src];
     z2[b + i] = z[src];
@@ -728,10 +755,19 @@ int morton_order_leaves(Tree& T, int32_t max_leaf, cudaStream_t s, Counters& cnt
   // keys of the largest sorted leaf (leaves hold at most max_leaf particles)
   int n2max = 2;
   while (n2max < max_leaf && n2max < kMortonMax) n2max <<= 1;
-  const size_t smem = sizeof(unsigned long long) * (size_t)n2max;
-  BL_CUDA(cudaFuncSetAttribute(k_leaf_morton, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_leaf_morton<<<T.nleaves, kMortonThreads, smem, s>>>(T.leaf_ids, T.begin, T.end, T.box, T.x, T.y,
-                                                        T.z, T.perm, x2, y2, z2, perm2, n2max);
+  if (n2max <= MortonKey<uint32_t>::kMaxPoints) {
+    const size_t smem = sizeof(uint32_t) * (size_t)n2max;
+    BL_CUDA(cudaFuncSetAttribute(k_leaf_morton<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    k_leaf_morton<uint32_t><<<T.nleaves, kMortonThreads, smem, s>>>(
+        T.leaf_ids, T.begin, T.end, T.box, T.x, T.y, T.z, T.perm, x2, y2, z2, perm2, n2max);
+  } else {
+    const size_t smem = sizeof(unsigned long long) * (size_t)n2max;
+    BL_CUDA(cudaFuncSetAttribute(k_leaf_morton<unsigned long long>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_leaf_morton<unsigned long long><<<T.nleaves, kMortonThreads, smem, s>>>(
+        T.leaf_ids, T.begin, T.end, T.box, T.x, T.y, T.z, T.perm, x2, y2, z2, perm2, n2max);
+  }
   BL_LAUNCHED(cnt.launches);
   std::swap(T.x, x2);
   std::swap(T.y, y2);
