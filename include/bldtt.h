@@ -323,8 +323,9 @@ int bldtt_compute_graph(bldtt_plan* plan, double* phi, void* cuda_stream);
  * for each kernel type of the plan: runs bldtt_compute once (phi, device M
  * float64, receives its potentials), then times each kernel type's
  * persistent launch three times per layout instantiated for that kernel
- * (Coulomb: 4 warps x 2 targets at 6 or 8 CTAs/SM, 2 warps x 4 targets;
- * other kernels: 4 warps x 2 targets) with CUDA events and keeps the fastest
+ * (Coulomb: 4 warps x 2 targets at 6 CTAs/SM with a 3-stage ring or at 5
+ * CTAs/SM with a 4-stage ring, 2 warps x 4 targets; other kernels: 4 warps x 2
+ * targets, 3 stages) with CUDA events and keeps the fastest
  * in the plan.  Results do not depend on the layout (bit for bit).  *chosen
  * (may be NULL) receives the layout picked for the lowest kernel id of the
  * plan.  Synchronous.  Errors: EINVAL, ECUDA, ETIMEOUT.

@@ -276,7 +276,7 @@ struct bldtt_plan {
     int layout, grid, threads;        // consumer layout and launch shape
   };
   std::vector<Segment> segments;
-  int interact_layout = 0;            // requested layout: 0 = 4 warps x 2 targets, 1 = 2 x 4, 2 = 4 x 2 at 8 CTAs/SM
+  int interact_layout = 0;            // requested layout: 0 = 4 warps x 2 targets, 1 = 2 x 4, 2 = 4 x 2 at 5 CTAs/SM, 4 stages
   float4* chunk_frame = nullptr;      // [pool chunks][kChunkInfo]: frame centre + count, extents + tau
   float4* item_box = nullptr;         // FP32_BULK: [items][kItemGroups][2] target group boxes (lo, hi)
   float* pool_res = nullptr;          // FP32_BULK: frame residuals of the pool's particles (pair records)
