@@ -343,6 +343,18 @@ int bldtt_autotune(bldtt_plan* plan, double* phi, void* cuda_stream, int* chosen
  */
 int bldtt_pipe_rates(double* out, void* cuda_stream);
 
+/*
+ * bldtt_wait_probe - failure detection without a fault: one CTA waits, with
+ * the interaction kernel's bounded-wait pattern (mbarrier try_wait until the
+ * %globaltimer passes the limit, then the error flag is raised and the kernel
+ * returns), on an mbarrier that nothing ever arrives on.  limit_ns in
+ * [1000, 1e9].  Returns BLDTT_ETIMEOUT when the wait gave up as designed (the
+ * expected outcome) and leaves the context usable; EINTERNAL if the wait
+ * completed (it cannot), EINVAL for a limit out of range, ENOMEM, ECUDA.
+ * Synchronous on cuda_stream.  No counterpart in the paper.
+ */
+int bldtt_wait_probe(int64_t limit_ns, void* cuda_stream);
+
 /* Synchronise the plan's last stream and report a device-side error flag
  * (ETIMEOUT from a bounded wait, EINTERNAL from a bounds check). */
 int bldtt_check_error(bldtt_plan* plan);

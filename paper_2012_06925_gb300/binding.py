@@ -29,7 +29,7 @@ EXPORTED = (
     "bldtt_export_proxy_potentials", "bldtt_direct_sum", "bldtt_solve_host",
     "bldtt_bounding_box_noalloc", "bldtt_selector_param_count", "bldtt_setup_learned",
     "bldtt_list_classes", "bldtt_mlp_forward", "bldtt_mlp_gradients", "bldtt_mlp_adam",
-    "bldtt_pair_features", "bldtt_pair_errors", "bldtt_pipe_rates",
+    "bldtt_pair_features", "bldtt_pair_errors", "bldtt_pipe_rates", "bldtt_wait_probe",
 )
 
 
@@ -126,6 +126,7 @@ def load_library(path: str = LIB_PATH):
         "bldtt_pair_features": (i32, [vp, i64, vp, vp, vp]),
         "bldtt_pair_errors": (i32, [vp, i64, vp, i32, i32, ctypes.POINTER(ctypes.c_int), vp, vp]),
         "bldtt_pipe_rates": (i32, [P_dbl, vp]),
+        "bldtt_wait_probe": (i32, [i64, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -467,6 +468,12 @@ def pipe_rates(stream=None) -> dict:
     out = np.zeros(5, dtype=np.float64)
     _check(load_library().bldtt_pipe_rates(_np_ptr(out, ctypes.c_double), _stream_ptr(stream)))
     return dict(ffma=out[0], ffma2_lanes=out[1], mufu_rsqrt=out[2], mufu_ex2=out[3], dfma=out[4])
+
+
+def wait_probe(limit_ns: int, stream=None) -> int:
+    """Run the bounded-wait probe (bldtt_wait_probe) and return its status
+    without raising: BLDTT_ETIMEOUT (4) is the expected outcome."""
+    return int(load_library().bldtt_wait_probe(int(limit_ns), _stream_ptr(stream)))
 
 
 def direct_sum(targets, sources, charges, kernel=COULOMB, kappa=0.0, phi=None, stream=None):

@@ -50,6 +50,13 @@ def test_status_strings(lib):
     assert B.status_string(12345) == "BLDTT_UNKNOWN_STATUS"
 
 
+def test_wait_probe_rejects_limits_out_of_range(lib):
+    # validated before any CUDA call
+    assert B.wait_probe(999) == 1
+    assert B.wait_probe(1_000_000_001) == 1
+    assert "limit_ns" in lib.bldtt_last_error().decode()
+
+
 DUMMY = ctypes.c_void_p(0x1000)   # never dereferenced: validation fails first
 GOOD = dict(kernel=0, kappa=0.0, n=4, theta=0.7, N0=10, M0=10, precision=1)
 

@@ -269,3 +269,15 @@ def test_plans_release_their_memory():
         cycle()
     free1 = torch.cuda.mem_get_info()[0]
     assert abs(free1 - free0) < 64 << 20, (free0, free1)
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """Failure detection without a fault: a wait on an mbarrier that nothing
+    arrives on gives up after its limit with BLDTT_ETIMEOUT, and the device
+    keeps computing correctly afterwards."""
+    assert B.wait_probe(2_000_000) == 4          # BLDTT_ETIMEOUT, after 2 ms
+    assert "gave up" in B.load_library().bldtt_last_error().decode()
+    tgt, src, q = W.make_problem("uniform", 3000, seed=23)
+    phi, plan = run_gpu(tgt, src, q, n=4, theta=0.0, N0=100, M0=100, precision=B.FP64)
+    plan.close()
+    assert rel_l2(O.direct_sum(tgt, src, q), phi) <= 1e-13
