@@ -51,9 +51,9 @@ def test_status_strings(lib):
 
 
 def test_wait_probe_rejects_limits_out_of_range(lib):
-    # validated before any CUDA call
-    assert B.wait_probe(999) == 1
-    assert B.wait_probe(1_000_000_001) == 1
+    # validated before any CUDA call (null stream: no device needed)
+    assert lib.bldtt_wait_probe(999, None) == 1
+    assert lib.bldtt_wait_probe(1_000_000_001, None) == 1
     assert "limit_ns" in lib.bldtt_last_error().decode()
 
 
