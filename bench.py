@@ -110,34 +110,46 @@ kw = dict(kernel=cfg["kernel"], kappa=cfg["kappa"], n=cfg["n"], theta=cfg["theta
           N0=cfg["N0"], M0=cfg["M0"])
 t0 = time.perf_counter()
 samp = O.SampledBLDTT(tgt, tgt, q, **kw)
-t1 = time.perf_counter()
-leaf = samp.tt.leaves()[%(leaf)d]
-pos = np.arange(samp.tt.begin[leaf], samp.tt.end[leaf])[:%(count)d]
-idx = samp.tt.perm[pos]
-phi = samp.potentials(idx)
-t2 = time.perf_counter()
-print(json.dumps(dict(setup_s=t1 - t0, sample_s=t2 - t1, sample=int(idx.size), M=int(cfg["M"]))))
+setup_s = time.perf_counter() - t0
+leaves = samp.tt.leaves()
+for k in %(leaves)r:
+    leaf = leaves[k %% len(leaves)]
+    idx = samp.tt.perm[np.arange(samp.tt.begin[leaf], samp.tt.end[leaf])]
+    t1 = time.perf_counter()
+    samp.potentials(idx)
+    print(json.dumps(dict(setup_s=setup_s, sample_s=time.perf_counter() - t1,
+                          sample=int(idx.size), M=int(cfg["M"]))), flush=True)
 """
 
 
-def oracle_rate(leaf=0, count=400):
-    """Time the oracle single-threaded on one target leaf's first `count`
-    targets; the trees/lists/upward pass are charged pro rata (sample/M)."""
+def oracle_rates(leaves):
+    """Time the oracle single-threaded on whole target leaves (one rate per
+    entry of `leaves`, leaf indices in tree order).  The trees, the traversal
+    and the upward pass are built once, for all M particles, and charged to
+    each leaf pro rata (its targets / M): per target the oracle then sums the
+    PP/PC entries of the target's cluster chain and interpolates the chain's
+    CP/CC proxy potentials, which a whole leaf shares."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ORACLE_SNIPPET % dict(root=ROOT, wl=WORKLOAD, leaf=leaf, count=count)
+    code = ORACLE_SNIPPET % dict(root=ROOT, wl=WORKLOAD, leaves=list(leaves))
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                       timeout=900)
+                       timeout=1800)
     if r.returncode != 0:
         raise RuntimeError("oracle timing failed:\n" + r.stderr[-2000:])
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    t = d["sample_s"] + d["setup_s"] * d["sample"] / d["M"]
-    return dict(value=d["sample"] / t, unit=UNIT, cores=1, kind="oracle",
-                sample=(f"{d['sample']} targets of one target leaf of the {WORKLOAD} workload "
-                        f"(FP64 numpy oracle, one thread): per-target PP/PC along the cluster chain "
-                        f"plus that chain's CP/CC proxy potentials ({d['sample_s']:.1f} s); trees, "
-                        f"traversal and upward pass for all 1e6 particles ({d['setup_s']:.1f} s) "
-                        f"charged pro rata"),
-                seconds=d["sample_s"] + d["setup_s"])
+    out = []
+    for ln in r.stdout.strip().splitlines():
+        d = json.loads(ln)
+        t = d["sample_s"] + d["setup_s"] * d["sample"] / d["M"]
+        out.append(dict(value=d["sample"] / t, unit=UNIT, cores=1, kind="oracle",
+                        sample=(f"one whole target leaf ({d['sample']} targets) of the {WORKLOAD} "
+                                f"workload (FP64 numpy oracle, one thread): per-target PP/PC along "
+                                f"the cluster chain plus the chain's CP/CC proxy potentials "
+                                f"({d['sample_s']:.2f} s); trees, traversal and upward pass for "
+                                f"all {d['M']:.0e} particles ({d['setup_s']:.1f} s, once) charged "
+                                f"pro rata"),
+                        seconds=t))
+    if len(out) != len(leaves):
+        raise RuntimeError("oracle timing printed %d of %d leaves" % (len(out), len(leaves)))
+    return out
 
 
 def run_reference(args):
@@ -147,11 +159,8 @@ def run_reference(args):
     from paper_2012_06925_gb300 import workloads as W
     cfg = dict(W.CONFIGS[WORKLOAD])
     cfg["name"] = WORKLOAD
-    rates = []
-    for i in range(args.warmup + args.steps):
-        r = oracle_rate(leaf=i % 7, count=150)
-        if i >= args.warmup:
-            rates.append(r)
+    # one leaf per step (a different leaf each step), the oracle's set-up once
+    rates = oracle_rates(range(args.warmup + args.steps))[args.warmup:]
     value = statistics.median([r["value"] for r in rates])
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -457,7 +466,7 @@ def run_gpu(args):
     cpu = None
     if world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD:
         try:
-            cb = oracle_rate(leaf=0, count=2000)
+            cb = oracle_rates([0])[0]
             cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
         except Exception as exc:   # reported, not fatal
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
