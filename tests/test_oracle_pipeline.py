@@ -7,6 +7,7 @@ degree 2 for which every approximation is exact.  The approximate checks use
 the paper's own error figures (tests/golden/paper_errors.json).
 """
 import json
+import math
 import os
 
 import numpy as np
@@ -184,3 +185,13 @@ def test_cc_pp_only_variant():
         for t, s in abl.lists[typ]:
             cover[abl.ttree.begin[t]:abl.ttree.end[t], abl.stree.begin[s]:abl.stree.end[s]] += 1
     assert cover.min() == 1 and cover.max() == 1
+
+
+def test_coulomb_and_yukawa_closed_form_values():
+    """Values fixed by arithmetic alone: |(3, 4, 0)| = 5, so 1/r = 0.2; with
+    kappa = ln 2, exp(-kappa r)/r is 1/2 at r = 1 and 1/8 at r = 2 (Sec. 4.6)."""
+    g = O.kernel_values(O.COULOMB, 0.0, np.array([3.0]), np.array([4.0]), np.array([0.0]))
+    assert abs(g[0] - 0.2) <= 1e-16
+    y = O.kernel_values(O.YUKAWA, math.log(2.0), np.array([1.0, 0.0]), np.array([0.0, -2.0]),
+                        np.zeros(2))
+    assert abs(y[0] - 0.5) <= 1e-15 and abs(y[1] - 0.125) <= 1e-15

@@ -91,3 +91,100 @@ def test_swapped_downward_operands_are_caught(monkeypatch):
         return np.einsum("ai,bj,ck,abc->ijk", D2, D1, D3, phit_par)
     monkeypatch.setattr(B, "parent_to_child", swapped)
     assert _poly_exact_error() > 1e-8
+
+
+# ---- Alg. 2's decision points, against the hand-worked lists -------------
+
+def _dtt_example(name):
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "dtt_examples.json")
+    with open(path) as f:
+        ex = {e["name"]: e for e in json.load(f)["examples"]}[name]
+    tt = B.build_tree(np.array(ex["targets"], dtype=np.float64), ex["M0"])
+    st = B.build_tree(np.array(ex["sources"], dtype=np.float64), ex["N0"])
+    return ex, tt, st
+
+
+def _lists_match(ex, tt, st):
+    lists = B.dual_tree_traversal(tt, st, ex["n"], ex["theta"])
+    return all(sorted(map(list, lists[k])) == sorted(ex["lists"][nm])
+               for k, nm in enumerate(B.TYPE_NAMES))
+
+
+def test_non_strict_mac_is_caught(monkeypatch):
+    ex, tt, st = _dtt_example("mac_tie_is_not_separated")
+    assert _lists_match(ex, tt, st)
+    def non_strict(tt_, t, st_, s, theta):
+        ct, cs = tt_.center(t), st_.center(s)
+        R = float(np.sqrt(sum((a - b) ** 2 for a, b in zip(ct, cs))))
+        return tt_.radius(t) + st_.radius(s) <= theta * R
+    monkeypatch.setattr(B, "well_separated", non_strict)
+    assert not _lists_match(ex, tt, st)
+
+
+@pytest.mark.parametrize("name", ["eight_points_against_n_p_eight_is_pp",
+                                  "nine_sources_against_eight_targets_is_pc",
+                                  "nine_targets_against_eight_sources_is_cp"])
+def test_non_strict_type_threshold_is_caught(monkeypatch, name):
+    """|C| >= n_p in place of |C| > n_p (planted by counting one particle more
+    after the trees are built)."""
+    ex, tt, st = _dtt_example(name)
+    assert _lists_match(ex, tt, st)
+    orig = B.Tree.count
+    monkeypatch.setattr(B.Tree, "count", lambda self, c: orig(self, c) + 1)
+    assert not _lists_match(ex, tt, st)
+
+
+def test_splitting_the_target_on_equal_counts_is_caught():
+    """Split the target iff |C_s| <= |C_t| (planted: the target tree reports
+    one particle more, which only changes the equal-count decision here)."""
+    ex, tt, st = _dtt_example("equal_counts_split_the_source")
+    assert _lists_match(ex, tt, st)
+    orig = tt.count
+    tt.count = lambda c: orig(c) + 1
+    assert not _lists_match(ex, tt, st)
+
+
+# ---- kernels, interactions and the upward pass ------------------------------
+
+def test_flipped_yukawa_exponent_is_caught(monkeypatch):
+    orig = B.kernel_values
+    monkeypatch.setattr(B, "kernel_values",
+                        lambda kernel, kappa, dx, dy, dz: orig(kernel, -kappa if kernel == B.YUKAWA
+                                                               else kappa, dx, dy, dz))
+    # one unit charge at distance 1, kappa = ln 2: exp(-ln 2)/1 = 1/2 (the closed-form pin)
+    got = B.direct_sum(np.zeros((3, 1)), np.array([[1.0], [0.0], [0.0]]), np.array([1.0]),
+                       B.YUKAWA, np.log(2.0))[0]
+    assert abs(got - 0.5) > 0.1     # exp(+ln 2)/1 = 2
+
+
+@pytest.mark.parametrize("term", ["interact_pc", "interact_cp"])
+def test_dropped_pc_or_cp_term_is_caught(monkeypatch, term):
+    tgt, src, q = W.make_problem("uniform", 1200, 1100, seed=6, sources_kind="plummer")
+    res = O.bldtt(tgt, src, q, kernel=O.TEST_POLY, n=2, theta=0.7, N0=15, M0=15)
+    assert len(res.lists[B.PC if term == "interact_pc" else B.CP]) > 0
+    orig = getattr(B, term)
+    monkeypatch.setattr(B, term, lambda *a: np.zeros_like(orig(*a)))
+    assert _poly_exact_error() > 1e-6
+
+
+def test_mixed_up_dimension_in_upward_leaf_is_caught(monkeypatch):
+    """Eq. (9) with the y factor evaluated at x: the first moments in y no
+    longer match the particles'."""
+    _, src, q = W.make_problem("plummer", 10, 1500, seed=4, sources_kind="plummer")
+    st = B.build_tree(src, 40)
+    ys, qs = src[:, st.perm], q[st.perm]
+    orig = B.tensor_basis
+    monkeypatch.setattr(B, "tensor_basis",
+                        lambda tree, c, n, px, py, pz: orig(tree, c, n, px, px, pz))
+    n = 3
+    with np.errstate(all="ignore"):    # x far outside a leaf's y interval may overflow
+        qhat = B.upward_pass(st, n, ys, qs)
+        worst = 0.0
+        for c in st.leaves():
+            b, e = st.begin[c], st.end[c]
+            _, gy, _ = B.proxy_grid(st, c, n)
+            diff = abs((gy * qhat[c].ravel()).sum() - (ys[1, b:e] * qs[b:e]).sum())
+            worst = max(worst, diff if np.isfinite(diff) else np.inf)
+    assert worst > 1e-6

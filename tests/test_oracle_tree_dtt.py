@@ -135,3 +135,19 @@ def test_theta_zero_gives_only_leaf_pp():
     assert len(lists[O.PC]) == len(lists[O.CP]) == len(lists[O.CC]) == 0
     leaves = tt.leaves()
     assert len(lists[O.PP]) == len(leaves) ** 2
+
+
+def _dtt_examples():
+    with open(os.path.join(os.path.dirname(GOLDEN), "dtt_examples.json")) as f:
+        return json.load(f)["examples"]
+
+
+@pytest.mark.parametrize("ex", _dtt_examples(), ids=lambda e: e["name"])
+def test_dtt_hand_worked_examples(ex):
+    """Alg. 2 at its decision points (MAC tie, type thresholds at |C| = n_p,
+    equal counts), against lists worked out by hand."""
+    tt = O.build_tree(np.array(ex["targets"], dtype=np.float64), ex["M0"])
+    st = O.build_tree(np.array(ex["sources"], dtype=np.float64), ex["N0"])
+    lists = O.dual_tree_traversal(tt, st, ex["n"], ex["theta"])
+    for typ, name in enumerate(O.TYPE_NAMES):
+        assert sorted(map(list, lists[typ])) == sorted(ex["lists"][name]), name
