@@ -160,3 +160,17 @@ def test_training_entry_points_reject_bad_arguments(lib):
     assert lib.bldtt_pair_errors(None, 1, DUMMY, 64, 2, deg, DUMMY, None) == 1
     assert lib.bldtt_pair_features(None, 1, DUMMY, DUMMY, None) == 1
     assert lib.bldtt_list_classes(None, None, None, None) == 1
+
+
+def test_binding_refuses_host_tensors(lib):
+    """No CPU fallback: the binding hands only device pointers to the library
+    and refuses host, non-FP64 or wrongly shaped tensors before any CUDA call."""
+    import torch
+    pts = torch.zeros(3, 10, dtype=torch.float64)
+    q = torch.zeros(10, dtype=torch.float64)
+    with pytest.raises(TypeError):
+        B.Plan(pts, pts, q)
+    with pytest.raises(TypeError):
+        B.Plan(pts.float(), pts.float(), q.float())
+    with pytest.raises(ValueError):
+        B.Plan(pts.t(), pts.t(), q)
