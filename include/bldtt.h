@@ -112,7 +112,9 @@ typedef struct bldtt_stats {
  *  sources   device, 3*N float64, SoA.
  *  N         number of sources, 1 <= N < 2^31.
  *  charges   device, N float64 (input order of the sources).
- *  kernel    enum bldtt_kernel; kappa >= 0 is used by BLDTT_YUKAWA only.
+ *  kernel    enum bldtt_kernel.
+ *  kappa     parameter of BLDTT_YUKAWA, BLDTT_OSCILLATORY and BLDTT_REG_COULOMB:
+ *            finite and >= 0 (else EINVAL); ignored by the other kernels.
  *  n         interpolation degree, 1 <= n <= 16; proxies per cluster n_p=(n+1)^3.
  *  theta     MAC parameter, theta >= 0 (theta = 0 gives only PP, i.e. the direct sum).
  *  N0, M0    maximum particles per source / target leaf, >= 1.
