@@ -117,12 +117,3 @@ def test_graph_replay_and_autotune(probs):
         assert layout in (0, 1, 2)                   # layouts instantiated for Coulomb
         assert np.array_equal(plan.compute().cpu().numpy(), ref)
         plan.check_error()
-
-
-def test_batched_workload_generator_shape():
-    probs = W.batched_problems(count=16, seed=4, nmin=1e3, nmax=1e4)
-    sizes = [p["points"].shape[1] for p in probs]
-    assert all(1000 <= m <= 10000 for m in sizes)
-    assert {p["kernel"] for p in probs} <= {B.COULOMB, B.YUKAWA}
-    radii = [np.linalg.norm(p["points"], axis=0) for p in probs[1::2]]
-    assert all(np.allclose(r, 1.0) for r in radii)     # odd problems on the unit sphere
