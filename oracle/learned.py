@@ -330,19 +330,6 @@ def bldtt_entries(targets, sources, charges, tt, st, entries, degrees, kernel=O.
     return out
 
 
-def entry_counts(tt, st, entries, degrees):
-    """Kernel evaluations of the entries (the cost the selector minimises)."""
-    total = 0
-    for c, t, s in entries:
-        if c == 0:
-            total += tt.count(t) * st.count(s)
-            continue
-        i, typ = divmod(c - 1, 3)
-        npd = n_p(degrees[i])
-        total += (tt.count(t) * npd, npd * st.count(s), npd * npd)[typ]
-    return total
-
-
 # --------------------------------------------------------------------------
 # Training labels: the error each option makes on one pair
 # --------------------------------------------------------------------------

@@ -183,3 +183,55 @@ def test_pair_errors_polynomial_exact_and_falling_with_degree():
         assert err[0, typ] > err[1, typ] > err[2, typ] > err[3, typ]
     # CC interpolates on both sides: never much better than the one-sided forms
     assert np.all(err[:, 2] >= 0.5 * np.maximum(err[:, 0], err[:, 1]))
+
+
+# --------------------------------------------------------------------------
+# Pair features against hand-worked values
+# --------------------------------------------------------------------------
+
+def _feature_examples():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "pair_features_examples.json")
+    with open(path) as f:
+        return json.load(f)["examples"]
+
+
+def _cluster_points(spec):
+    """lo, hi and m - 2 copies of the box centre (one particle when m = 1)."""
+    lo, hi, m = np.array(spec["lo"], float), np.array(spec["hi"], float), spec["m"]
+    if m == 1:
+        assert np.array_equal(lo, hi)
+        return lo[:, None].copy()
+    mid = (lo + hi) * 0.5
+    return np.concatenate([lo[:, None], hi[:, None], np.repeat(mid[:, None], m - 2, axis=1)],
+                          axis=1)
+
+
+def _fraction(text):
+    from fractions import Fraction
+    return float(Fraction(text))
+
+
+def pair_feature_mismatches(features_fn):
+    """Names of the hand-worked examples whose features features_fn gets
+    wrong (bit for bit: every expected value is a correctly rounded quotient
+    of exact operands)."""
+    bad = []
+    for ex in _feature_examples():
+        tpts, spts = _cluster_points(ex["target"]), _cluster_points(ex["source"])
+        tt, st = O.build_tree(tpts, ex["target"]["m"]), O.build_tree(spts, ex["source"]["m"])
+        assert tt.num_clusters == 1 and st.num_clusters == 1
+        assert list(tt.lo[0]) == ex["target"]["lo"] and list(st.hi[0]) == ex["source"]["hi"]
+        got = features_fn(tt, 0, st, 0, ex["kappa"])
+        want = ex["features"]
+        if want is None:
+            if got is not None:
+                bad.append(ex["name"])
+        elif got is None or not np.array_equal(np.asarray(got), [_fraction(v) for v in want]):
+            bad.append(ex["name"])
+    return bad
+
+
+def test_pair_features_hand_worked():
+    assert pair_feature_mismatches(L.pair_features) == []

@@ -188,3 +188,79 @@ def test_mixed_up_dimension_in_upward_leaf_is_caught(monkeypatch):
             diff = abs((gy * qhat[c].ravel()).sum() - (ys[1, b:e] * qs[b:e]).sum())
             worst = max(worst, diff if np.isfinite(diff) else np.inf)
     assert worst > 1e-6
+
+
+# ---- learned-selector features and the interaction counts -------------------
+
+def _mutant_features(mistake):
+    """pair_features with one planted mistake."""
+    from oracle import learned as Lm
+
+    def f(tt, t, st, s, kappa):
+        out = Lm.pair_features(tt, t, st, s, kappa)
+        if mistake == "non_strict_separation":
+            ct, cs = np.array(tt.center(t)), np.array(st.center(s))
+            R = float(np.sqrt(((ct - cs) ** 2).sum()))
+            if out is None and R > 0 and (tt.radius(t) + st.radius(s)) / R <= 1.0:
+                kr = kappa * R
+                return np.array([Lm.plog2(tt.count(t)) / 16, Lm.plog2(st.count(s)) / 16,
+                                 tt.radius(t) / R, st.radius(s) / R,
+                                 (tt.radius(t) + st.radius(s)) / R, kr / (1 + kr)])
+            return out
+        if out is None:
+            return None
+        out = out.copy()
+        if mistake == "swapped_radii":
+            out[2], out[3] = out[3], out[2]
+        elif mistake == "source_count_twice":
+            out[0] = out[1]
+        elif mistake == "kappa_feature_without_r":
+            ct, cs = np.array(tt.center(t)), np.array(st.center(s))
+            R = float(np.sqrt(((ct - cs) ** 2).sum()))
+            out[5] = kappa / (1.0 + kappa * R)
+        return out
+    return f
+
+
+@pytest.mark.parametrize("mistake", ["swapped_radii", "source_count_twice",
+                                     "kappa_feature_without_r", "non_strict_separation"])
+def test_pair_feature_mistakes_are_caught(mistake):
+    from test_oracle_learned import pair_feature_mismatches
+    from oracle import learned as Lm
+    assert pair_feature_mismatches(Lm.pair_features) == []
+    assert pair_feature_mismatches(_mutant_features(mistake)) != []
+
+
+_counts = B.interaction_counts
+
+
+def _counts_pc_by_source(tt, st, lists, n):
+    pp, pc, cp, cc = _counts(tt, st, lists, n)
+    n_p = (n + 1) ** 3
+    return pp, sum(n_p * st.count(s) for t, s in lists[B.PC]), cp, cc
+
+
+def _counts_cp_by_target(tt, st, lists, n):
+    pp, pc, cp, cc = _counts(tt, st, lists, n)
+    n_p = (n + 1) ** 3
+    return pp, pc, sum(tt.count(t) * n_p for t, s in lists[B.CP]), cc
+
+
+def _counts_cc_by_particles(tt, st, lists, n):
+    pp, pc, cp, cc = _counts(tt, st, lists, n)
+    return pp, pc, cp, sum(tt.count(t) * st.count(s) for t, s in lists[B.CC])
+
+
+@pytest.mark.parametrize("mutant", [_counts_pc_by_source, _counts_cp_by_target,
+                                    _counts_cc_by_particles])
+def test_interaction_count_mistakes_are_caught(monkeypatch, mutant):
+    """PC counted as n_p |C_s|, CP as |C_t| n_p or CC as |C_t||C_s| fails the
+    hand-worked counts and the instrumented evaluation count."""
+    from test_oracle_tree_dtt import (_dtt_examples, evaluations_performed,
+                                      interaction_count_mismatches)
+    assert any(interaction_count_mismatches(ex, mutant) for ex in _dtt_examples())
+    monkeypatch.setattr(B, "interaction_counts", mutant)
+    tgt, src, q = W.make_problem("uniform", 1000, 1200, seed=12, sources_kind="plummer")
+    performed, counts = evaluations_performed(monkeypatch, tgt, src, q, n=2, theta=0.7,
+                                              N0=30, M0=30)
+    assert performed != sum(counts)

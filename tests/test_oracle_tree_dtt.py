@@ -151,3 +151,53 @@ def test_dtt_hand_worked_examples(ex):
     lists = O.dual_tree_traversal(tt, st, ex["n"], ex["theta"])
     for typ, name in enumerate(O.TYPE_NAMES):
         assert sorted(map(list, lists[typ])) == sorted(ex["lists"][name]), name
+
+
+@pytest.mark.parametrize("ex", _dtt_examples(), ids=lambda e: e["name"])
+def test_interaction_counts_hand_worked(ex):
+    """Kernel evaluations per list type (PP |C_t||C_s|, PC |C_t| n_p, CP
+    n_p |C_s|, CC n_p^2 per entry; Eqs. (6), (8), (12), (15)) against the
+    counts worked out by hand for the Alg. 2 examples."""
+    assert interaction_count_mismatches(ex, O.interaction_counts) == []
+
+
+def interaction_count_mismatches(ex, counts_fn):
+    tt = O.build_tree(np.array(ex["targets"], dtype=np.float64), ex["M0"])
+    st = O.build_tree(np.array(ex["sources"], dtype=np.float64), ex["N0"])
+    lists = O.dual_tree_traversal(tt, st, ex["n"], ex["theta"])
+    got = counts_fn(tt, st, lists, ex["n"])
+    return [(name, got[k], ex["counts"][name]) for k, name in enumerate(O.TYPE_NAMES)
+            if got[k] != ex["counts"][name]]
+
+
+def evaluations_performed(monkeypatch, t, s, q, **kw):
+    """Runs the oracle BLDTT with its kernel evaluator instrumented and
+    returns (counted evaluations, the counts the result reports).  Only the
+    interaction sums evaluate G, so the instrumented total is the number of
+    kernel evaluations the four sums really make."""
+    from oracle import bldtt_oracle as Bo
+    seen = [0]
+    orig = Bo.kernel_values
+
+    def counting(kernel, kappa, dx, dy, dz):
+        seen[0] += np.asarray(dx).size
+        return orig(kernel, kappa, dx, dy, dz)
+
+    monkeypatch.setattr(Bo, "kernel_values", counting)
+    res = Bo.bldtt(t, s, q, **kw)
+    return seen[0], res.counts
+
+
+@pytest.mark.parametrize("theta,n,leaf", [(0.0, 2, 30), (0.7, 2, 30), (0.8, 1, 12)])
+def test_interaction_counts_equal_evaluations_performed(monkeypatch, theta, n, leaf):
+    """Brute force: the reported counts sum to the evaluations the oracle's
+    interaction sums perform, on unequal target and source sets where all
+    four list types occur (theta = 0: only PP, M N evaluations)."""
+    t, s, q = W.make_problem("uniform", 1000, 1200, seed=12, sources_kind="plummer")
+    performed, counts = evaluations_performed(monkeypatch, t, s, q, n=n, theta=theta,
+                                              N0=leaf, M0=leaf)
+    assert performed == sum(counts)
+    if theta == 0.0:
+        assert counts[0] == t.shape[1] * s.shape[1] and sum(counts[1:]) == 0
+    else:
+        assert all(c > 0 for c in counts), counts
