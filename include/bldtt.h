@@ -90,16 +90,20 @@ typedef struct bldtt_stats {
     double interactions[4];             /* kernel evaluations per type, as defined by
                                            Eqs. (6), (8), (12), (15): |C_t||C_s|,
                                            |C_t| n_p, n_p |C_s|, n_p^2 per entry */
-    double executed_evaluations;        /* evaluations the interaction kernel performs:
-                                           every target slot of a 256-target tile meets
-                                           every real source (idle slots of partial tiles
-                                           included) */
+    double executed_evaluations;        /* evaluations the interaction kernel performs
+                                           in its default layout: every 32-target row group
+                                           holding a real target meets every real source
+                                           (the idle rows of such a group included) */
     int64_t work_items;                 /* target tiles drained by the interaction kernel */
     int32_t interact_grid;              /* CTAs of the persistent interaction kernel */
     int32_t interact_threads;           /* threads per CTA of that kernel */
     float ms_tree, ms_lists;            /* last bldtt_setup: trees; traversal + work lists */
     float ms_upward, ms_interact, ms_downward, ms_compute;   /* last bldtt_compute */
     int64_t launches_setup, launches_compute;                /* kernels launched */
+    double computed_evaluations;        /* evaluations (as interactions[]) of the work
+                                           items the last compute ran: all of them after
+                                           bldtt_compute, one shard's after
+                                           bldtt_compute_shard */
 } bldtt_stats_t;
 
 /*
@@ -310,6 +314,49 @@ int bldtt_set_charges(bldtt_plan* plan, const double* charges, void* cuda_stream
 int bldtt_compute(bldtt_plan* plan, double* phi, void* cuda_stream);
 
 /*
+ * bldtt_compute_shard - the compute phase for one shard of the target leaves,
+ * for one process per GPU (no counterpart in the paper, whose distributed
+ * runs partition both particle sets and exchange locally essential trees,
+ * Sec. 3.2; here the sources stay whole on every GPU).  Every rank sets up the
+ * same plan (set-up is deterministic), and rank `shard` of `nshards` calls
+ * this instead of bldtt_compute: it runs the whole upward pass, the PP/PC
+ * work items of its leaves, the CP/CC work items of every target cluster above
+ * or at its leaves (shared ancestors are computed by every rank that needs
+ * them, with the same result), and the downward pass, and writes phi only at
+ * its own targets; every other entry of phi is left untouched.  The leaves, in
+ * tree order, are split into nshards contiguous ranges of equal cost
+ * (bldtt_partition_leaves; a leaf costs its particle items' kernel
+ * evaluations plus, for every cluster on its path to the root, that cluster's
+ * proxy-item evaluations divided among the leaves under it).  The union of
+ * the shards' outputs equals bldtt_compute's phi bit for bit, so ranks that
+ * zero-fill phi, compute their shard and sum phi over ranks (or gather their
+ * entries) get the one-GPU result.
+ *
+ *  shard, nshards  0 <= shard < nshards; nshards = 1 is bldtt_compute.
+ *  phi             device, M float64, input order; only the shard's targets
+ *                  are written.
+ *
+ * The first call for a given nshards synchronises the stream once (costs to
+ * the host); the shard's work list is kept in the plan until another shard is
+ * computed.  Otherwise asynchronous on cuda_stream.  Errors: EINVAL, ENOMEM,
+ * ECUDA, ETIMEOUT (reported by the next synchronising call).
+ */
+int bldtt_compute_shard(bldtt_plan* plan, int shard, int nshards, double* phi, void* cuda_stream);
+
+/*
+ * bldtt_partition_leaves - host-only: split nleaves leaves, in order, with
+ * costs leaf_cost (host, >= 0, finite) into nshards contiguous ranges of
+ * nearly equal total cost.  leaf_begin (host, nshards + 1 int32) receives the
+ * first leaf of each range and nleaves last; the k-th boundary is the leaf
+ * boundary nearest to k/nshards of the total cost (never before the previous
+ * one), so ranges may be empty when there are fewer leaves than shards; if
+ * every cost is zero the ranges hold equal numbers of leaves.
+ * Deterministic; no device work.  Errors: EINVAL.
+ */
+int bldtt_partition_leaves(const double* leaf_cost, int32_t nleaves, int32_t nshards,
+                           int32_t* leaf_begin);
+
+/*
  * bldtt_compute_graph - bldtt_compute through a CUDA graph.  The first call
  * (and any call with a different phi pointer) captures the whole compute
  * phase on cuda_stream into a graph and instantiates it; every call then
@@ -333,17 +380,6 @@ int bldtt_compute_graph(bldtt_plan* plan, double* phi, void* cuda_stream);
  * plan.  Synchronous.  Errors: EINVAL, ECUDA, ETIMEOUT.
  */
 int bldtt_autotune(bldtt_plan* plan, double* phi, void* cuda_stream, int* chosen);
-
-/*
- * bldtt_pipe_rates - measured throughput of the pipes the interaction kernel
- * uses, for the roofline's issue ceilings (no counterpart in the paper): one
- * CTA of 1024 threads per SM runs independent chains of one operation and the
- * SM's cycle counter times it.  out (host, 5 doubles) receives operations
- * (lanes) per clock per SM of: FP32 FMA, packed FP32x2 FMA (counted per
- * lane, two per instruction), MUFU rsqrt, MUFU exp2, FP64 FMA (median CTA).
- * Synchronous on cuda_stream.  Errors: EINVAL (NULL out), ENOMEM, ECUDA.
- */
-int bldtt_pipe_rates(double* out, void* cuda_stream);
 
 /*
  * bldtt_wait_probe - failure detection without a fault: one CTA waits, with
@@ -452,14 +488,21 @@ int bldtt_solve_host(const double* targets, int64_t M, const double* sources, in
  *  n          1 <= n < 2^31 (larger sizes are rejected with EINVAL).
  *  box        device, 6 float64 written: lo x, lo y, lo z, hi x, hi y, hi z.
  *  nonfinite  device int or NULL; set to 1 if any coordinate is NaN or
- *             infinite (those values are left out of the box), else 0.
+ *             infinite (those values are left out of the box; a dimension
+ *             with no finite value gets lo = +inf, hi = -inf), else 0.
+ *
+ * Minima and maxima are taken on the same order-preserving integer keys as
+ * bldtt_setup, so the box equals the setup's root box bit for bit (-0.0 and
+ * +0.0 compare equal and come back as +0.0).
  *
  * The first call on a device (with that device current) looks up the
  * array's device address with cudaGetSymbolAddress; make that first call
- * before any stream capture.  All calls share the array and every call
- * rewrites the slots it reads, but calls that overlap on the GPU race on it:
- * serialise them (one stream, or events).  Asynchronous on cuda_stream.
- * Errors: EINVAL, ECUDA.
+ * before any stream capture (a first call during capture returns EINVAL).
+ * Later calls outside capture look the address up again, so a context
+ * re-created by cudaDeviceReset gets the array's new address.  All calls
+ * share the array and every call rewrites the slots it reads, but calls that
+ * overlap on the GPU race on it: serialise them (one stream, or events).
+ * Asynchronous on cuda_stream.  Errors: EINVAL, ECUDA.
  */
 int bldtt_bounding_box_noalloc(const double* points, int64_t n, double* box, int* nonfinite,
                                void* cuda_stream);

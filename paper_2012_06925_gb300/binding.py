@@ -29,7 +29,8 @@ EXPORTED = (
     "bldtt_export_proxy_potentials", "bldtt_direct_sum", "bldtt_solve_host",
     "bldtt_bounding_box_noalloc", "bldtt_selector_param_count", "bldtt_setup_learned",
     "bldtt_list_classes", "bldtt_mlp_forward", "bldtt_mlp_gradients", "bldtt_mlp_adam",
-    "bldtt_pair_features", "bldtt_pair_errors", "bldtt_pipe_rates", "bldtt_wait_probe",
+    "bldtt_pair_features", "bldtt_pair_errors", "bldtt_wait_probe", "bldtt_compute_shard",
+    "bldtt_partition_leaves",
 )
 
 
@@ -65,6 +66,7 @@ class Stats(ctypes.Structure):
         ("ms_upward", ctypes.c_float), ("ms_interact", ctypes.c_float),
         ("ms_downward", ctypes.c_float), ("ms_compute", ctypes.c_float),
         ("launches_setup", ctypes.c_int64), ("launches_compute", ctypes.c_int64),
+        ("computed_evaluations", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -125,8 +127,9 @@ def load_library(path: str = LIB_PATH):
         "bldtt_mlp_adam": (i32, [vp, vp, vp, vp, i64, i32, ctypes.c_float, vp]),
         "bldtt_pair_features": (i32, [vp, i64, vp, vp, vp]),
         "bldtt_pair_errors": (i32, [vp, i64, vp, i32, i32, ctypes.POINTER(ctypes.c_int), vp, vp]),
-        "bldtt_pipe_rates": (i32, [P_dbl, vp]),
         "bldtt_wait_probe": (i32, [i64, vp]),
+        "bldtt_compute_shard": (i32, [vp, i32, i32, vp, vp]),
+        "bldtt_partition_leaves": (i32, [P_dbl, ctypes.c_int32, ctypes.c_int32, P_i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -269,6 +272,13 @@ class Plan:
         if phi is None:
             phi = torch.empty(self.M, dtype=torch.float64, device="cuda")
         _check(load_library().bldtt_compute(self._handle(), _dptr(phi, self.M), _stream_ptr(stream)))
+        return phi
+
+    def compute_shard(self, shard: int, nshards: int, phi, stream=None):
+        """The compute phase of one shard of the target leaves
+        (bldtt_compute_shard): writes phi at that shard's targets only."""
+        _check(load_library().bldtt_compute_shard(self._handle(), int(shard), int(nshards),
+                                                  _dptr(phi, self.M), _stream_ptr(stream)))
         return phi
 
     def set_charges(self, charges, stream=None):
@@ -462,12 +472,14 @@ def pair_errors(plan, pairs, degrees, samples=64, stream=None):
     return out
 
 
-def pipe_rates(stream=None) -> dict:
-    """Measured operations per clock per SM of the FP32 FMA pipe (scalar and
-    packed, per lane), MUFU rsqrt and exp2, and FP64 FMA (bldtt_pipe_rates)."""
-    out = np.zeros(5, dtype=np.float64)
-    _check(load_library().bldtt_pipe_rates(_np_ptr(out, ctypes.c_double), _stream_ptr(stream)))
-    return dict(ffma=out[0], ffma2_lanes=out[1], mufu_rsqrt=out[2], mufu_ex2=out[3], dfma=out[4])
+def partition_leaves(leaf_cost, nshards: int):
+    """Contiguous ranges of leaves of nearly equal cost (bldtt_partition_leaves,
+    host only): returns the nshards + 1 range boundaries."""
+    cost = np.ascontiguousarray(leaf_cost, dtype=np.float64)
+    out = np.zeros(int(nshards) + 1, dtype=np.int32)
+    _check(load_library().bldtt_partition_leaves(_np_ptr(cost, ctypes.c_double), cost.size,
+                                                 int(nshards), _np_ptr(out, ctypes.c_int32)))
+    return out
 
 
 def wait_probe(limit_ns: int, stream=None) -> int:

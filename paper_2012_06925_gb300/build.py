@@ -2,7 +2,8 @@
 
 Each translation unit is compiled in parallel, then linked into a shared
 library next to this file.  A stamp of the sources and flags skips rebuilds
-when nothing changed.
+when nothing changed.  build_pipes() builds the benchmark's separate
+pipe-throughput library (libbldtt_pipes.so) from csrc_bench/.
 """
 from __future__ import annotations
 
@@ -20,7 +21,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libbldtt.so")
 
 SOURCES = ["prims.cu", "tree.cu", "dtt.cu", "passes.cu", "interact.cu", "direct.cu", "capi.cu",
-           "noalloc.cu", "learned.cu", "pipes.cu"]
+           "noalloc.cu", "learned.cu", "waitprobe.cu", "shard.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
                  "--expt-relaxed-constexpr", f"-I{INCLUDE}"]
@@ -82,6 +83,36 @@ def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
     with open(stamp_path, "w") as f:
         f.write(stamp)
     return LIB_PATH
+
+
+PIPES_SRC = os.path.join(HERE, "csrc_bench", "pipes.cu")
+PIPES_LIB = os.path.join(HERE, "libbldtt_pipes.so")
+
+
+def build_pipes(force: bool = False) -> str:
+    """Compile the pipe microbenchmark used by bench.py (not part of
+    libbldtt.so); returns the library's path."""
+    h = hashlib.sha256()
+    with open(PIPES_SRC, "rb") as f:
+        h.update(f.read())
+    h.update(" ".join(ARCH).encode())
+    stamp = h.hexdigest()
+    stamp_path = os.path.join(BUILD_DIR, "pipes.stamp")
+    if not force and os.path.exists(PIPES_LIB) and os.path.exists(stamp_path):
+        with open(stamp_path) as f:
+            if f.read().strip() == stamp:
+                return PIPES_LIB
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    tmp = PIPES_LIB + ".tmp"
+    cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+           PIPES_SRC, "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on csrc_bench/pipes.cu:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PIPES_LIB)
+    with open(stamp_path, "w") as f:
+        f.write(stamp)
+    return PIPES_LIB
 
 
 if __name__ == "__main__":

@@ -15,10 +15,6 @@ const char* last_error();
 int configure_pass_kernels();
 }  // namespace bldtt
 
-namespace {
-int compute_body(bldtt_plan* p, double* phi, cudaStream_t s);
-}
-
 using namespace bldtt;
 
 namespace {
@@ -86,6 +82,10 @@ void release(bldtt_plan* p) {
   dfree_ptr(p->chunk_frame, s);
   dfree_ptr(p->pool_res, s);
   dfree_ptr(p->item_box, s);
+  dfree_ptr(p->eval_part, s);
+  dfree_ptr(p->eval_prox, s);
+  dfree_ptr(p->sh_items, s);
+  dfree_ptr(p->sh_item_box, s);
   dfree_ptr(p->qhat, s);
   dfree_ptr(p->phit, s);
   dfree_ptr(p->phi_near, s);
@@ -429,6 +429,15 @@ static int setup_common(bldtt_plan** plan, const double* targets, const int64_t*
   std::sort(p->kernels_present.begin(), p->kernels_present.end());
   p->kernels_present.erase(std::unique(p->kernels_present.begin(), p->kernels_present.end()),
                            p->kernels_present.end());
+  {
+    const auto& kp = p->kernels_present;
+    const bool both = std::count(kp.begin(), kp.end(), (int)BLDTT_COULOMB) &&
+                      std::count(kp.begin(), kp.end(), (int)BLDTT_YUKAWA);
+    p->segment_kernels.clear();
+    if (both) p->segment_kernels.push_back(kKernCoulombYukawa);
+    for (int k : kp)
+      if (!both || (k != BLDTT_COULOMB && k != BLDTT_YUKAWA)) p->segment_kernels.push_back(k);
+  }
   p->kernel = kernels[0];
   p->kappa = p->prob_kappa_h[0];
   p->variant = variant;
@@ -577,6 +586,7 @@ int bldtt_compute(bldtt_plan* p, double* phi, void* cuda_stream) {
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   p->stream = s;
   p->compute_counter.launches = 0;
+  p->computed_evals = p->interactions[0] + p->interactions[1] + p->interactions[2] + p->interactions[3];
   return compute_body(p, phi, s);
 }
 
@@ -591,6 +601,7 @@ int bldtt_compute_graph(bldtt_plan* p, double* phi, void* cuda_stream) {
     return BLDTT_EINVAL;
   }
   p->stream = s;
+  p->computed_evals = p->interactions[0] + p->interactions[1] + p->interactions[2] + p->interactions[3];
   if (!p->graph_exec || p->graph_phi != phi) {
     if (p->graph_exec) {
       cudaGraphExecDestroy(p->graph_exec);
@@ -632,6 +643,7 @@ int bldtt_autotune(bldtt_plan* p, double* phi, void* cuda_stream, int* chosen) {
   // One full compute stages the pool; then every segment's launch is timed
   // alone for each layout (a launch only overwrites its own items' outputs).
   p->compute_counter.launches = 0;
+  p->computed_evals = p->interactions[0] + p->interactions[1] + p->interactions[2] + p->interactions[3];
   BL_TRY(compute_body(p, phi, s));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   BL_CUDA(cudaEventCreate(&e0));
@@ -679,7 +691,7 @@ int bldtt_autotune(bldtt_plan* p, double* phi, void* cuda_stream, int* chosen) {
 
 }  // extern "C"
 
-namespace {
+namespace bldtt {
 int compute_body(bldtt_plan* p, double* phi, cudaStream_t s) {
   BL_CUDA(cudaEventRecord(p->ev[0], s));
   for (int i = 0; i < p->deg.n; ++i)
@@ -695,7 +707,7 @@ int compute_body(bldtt_plan* p, double* phi, cudaStream_t s) {
   p->have_compute_events = true;
   return BLDTT_OK;
 }
-}  // namespace
+}  // namespace bldtt
 
 extern "C" {
 
@@ -738,6 +750,7 @@ int bldtt_stats(bldtt_plan* p, bldtt_stats_t* out) {
   }
   out->launches_setup = p->setup_counter.launches;
   out->launches_compute = p->compute_counter.launches;
+  out->computed_evaluations = p->computed_evals;
   return device_error(p);
 }
 

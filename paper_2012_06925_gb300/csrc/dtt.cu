@@ -336,6 +336,11 @@ __device__ __forceinline__ void class_work(const ListView& L, const int32_t* s_b
   }
 }
 
+// Target rows the interaction kernel evaluates for m targets cut into tiles of
+// kTile: every 32-row group holding a real target (the consumer warps of the
+// default layout skip empty groups; a group's idle rows are evaluated).
+__device__ __forceinline__ int64_t executed_rows(int64_t m) { return (m + 31) / 32 * 32; }
+
 // Items of target cluster c: tiles of its particles (a leaf: PP and PC of every
 // degree, on the leaf and on each ancestor), and tiles of its proxy points of
 // degree i (CP and CC of degree i on the cluster itself).  cost_prox is
@@ -345,7 +350,8 @@ __global__ void k_item_count(int32_t nct, ListView L, const int32_t* __restrict_
                              const int32_t* __restrict__ end, const int32_t* __restrict__ s_begin,
                              const int32_t* __restrict__ s_end, int32_t* __restrict__ nitems,
                              int64_t* __restrict__ cost_part, int64_t* __restrict__ cost_prox,
-                             unsigned long long* __restrict__ executed) {
+                             unsigned long long* __restrict__ executed,
+                             int64_t* __restrict__ eval_part, int64_t* __restrict__ eval_prox) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nct) return;
   int64_t cp = 0, sp = 0;
@@ -357,7 +363,9 @@ __global__ void k_item_count(int32_t nct, ListView L, const int32_t* __restrict_
     }
   const int32_t tp = cp > 0 ? (end[c] - begin[c] + kTile - 1) / kTile : 0;
   int32_t items = tp;
-  unsigned long long ex = (unsigned long long)tp * kTile * sp;
+  unsigned long long ex = cp > 0 ? (unsigned long long)executed_rows(end[c] - begin[c]) * sp : 0ull;
+  eval_part[c] = cp > 0 ? (int64_t)(end[c] - begin[c]) * sp : 0;   // real evaluations (no padding)
+  int64_t evq = 0;
   for (int i = 0; i < L.deg.n; ++i) {   // CP + CC of degree i on the cluster itself
     int64_t cq = 0, sq = 0;
     class_work(L, s_begin, s_end, class_of(BLDTT_CP, i), true, i, c, sq, cq);
@@ -365,8 +373,10 @@ __global__ void k_item_count(int32_t nct, ListView L, const int32_t* __restrict_
     const int32_t tq = cq > 0 ? (L.deg.np[i] + kTile - 1) / kTile : 0;
     items += tq;
     cost_prox[(int64_t)c * kMaxDegrees + i] = cq;
-    ex += (unsigned long long)tq * kTile * sq;
+    if (cq > 0) ex += (unsigned long long)executed_rows(L.deg.np[i]) * sq;
+    if (cq > 0) evq += (int64_t)L.deg.np[i] * sq;
   }
+  eval_prox[c] = evq;
   nitems[c] = items;
   cost_part[c] = cp;
   // evaluations the kernel performs: every target slot of every tile meets every real source
@@ -393,7 +403,9 @@ __global__ void k_item_fill(int32_t nct, const int32_t* __restrict__ off,
   uint32_t seg = 0;
   const int kern = prob_kernel[problem[c]];
   for (int i = 0; i < segmap.n; ++i)
-    if (segmap.kernel[i] == kern) seg = (uint32_t)i;
+    if (segmap.kernel[i] == kern ||
+        (segmap.kernel[i] == kKernCoulombYukawa && (kern == BLDTT_COULOMB || kern == BLDTT_YUKAWA)))
+      seg = (uint32_t)i;
   if (cost_part[c] > 0) {
     uint32_t k = (seg << 24) | (kKeyMax - (uint32_t)min((int64_t)kKeyMax, cost_part[c]));
     for (int32_t r = begin[c]; r < end[c]; r += kTile) {
@@ -520,9 +532,13 @@ int build_work_items(bldtt_plan* p, cudaStream_t s) {
   unsigned long long* executed = nullptr;
   BL_TRY(dalloc_n(&executed, 1, s));
   BL_CUDA(cudaMemsetAsync(executed, 0, sizeof(unsigned long long), s));
+  dfree_ptr(p->eval_part, s);
+  dfree_ptr(p->eval_prox, s);
+  BL_TRY(dalloc_n(&p->eval_part, nct, s));
+  BL_TRY(dalloc_n(&p->eval_prox, nct, s));
   k_item_count<<<nblk(nct, 128), 128, 0, s>>>(nct, L, tt.parent, tt.nchild, tt.begin, tt.end,
                                               st.begin, st.end, nitems, cost_part, cost_prox,
-                                              executed);
+                                              executed, p->eval_part, p->eval_prox);
   BL_LAUNCHED(cnt.launches);
   int32_t ni = 0;
   BL_TRY(scan_exclusive(nitems, off, nct, &ni, s, cnt));
@@ -535,8 +551,8 @@ int build_work_items(bldtt_plan* p, cudaStream_t s) {
   BL_TRY(dalloc_n(&vals, ni, s));
   BL_TRY(dalloc_n(&p->items, ni, s));
   SegmentMap segmap{};
-  segmap.n = (int)p->kernels_present.size();
-  for (int i = 0; i < segmap.n; ++i) segmap.kernel[i] = p->kernels_present[i];
+  segmap.n = (int)p->segment_kernels.size();
+  for (int i = 0; i < segmap.n; ++i) segmap.kernel[i] = p->segment_kernels[i];
   k_item_fill<<<nblk(nct, 128), 128, 0, s>>>(nct, off, cost_part, cost_prox, tt.begin, tt.end,
                                              tt.problem, p->prob_kernel, segmap, p->deg, items, keys,
                                              vals);

@@ -84,6 +84,7 @@ struct InteractView {
   const int32_t* t_problem;    // target cluster -> problem
   const float* prob_prm;       // FP32 kernel parameter (see pair_f32)
   const double* prob_kappa;
+  const int* prob_kernel;      // kernel of each problem (read per item by the fused launch)
 };
 
 struct StageMeta {
@@ -731,7 +732,7 @@ __device__ __forceinline__ void eval_chunk_f64(const void* buf, int count, const
 }
 
 template <bool F32, int KERN, int NCW, int K, int MINB, int STAGES>
-__global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_interact(InteractView v) {
+__global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_interact(const __grid_constant__ InteractView v) {
   static_assert(NCW * 32 * K == kTile, "a CTA covers exactly one work-item tile");
   constexpr int kConsumers = NCW * 32;
   using Vec = typename std::conditional<F32, float4, double4>::type;
@@ -770,8 +771,10 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_interact(InteractView 
   const TargetSplit ts{s_th + ct, s_tl + ct, kConsumers};
   double acc[K];
   bool warp_full = true;
+  bool warp_active = true;
   float prm = 0.f;              // its FP32 parameter
   double kappa = 0.0;           // its FP64 parameter
+  bool yukawa = KERN == BLDTT_YUKAWA;   // the fused Coulomb/Yukawa launch: this item's kernel
   for (uint32_t it = 0;; ++it) {
     const int s = (int)(it % STAGES);
     if (!mbar_wait(&full[s], (it / STAGES) & 1u, v.err)) return;
@@ -787,8 +790,11 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_interact(InteractView 
       const int pid = v.t_problem[item.x];
       prm = v.prob_prm[pid];
       kappa = v.prob_kappa[pid];
+      if (KERN == kKernCoulombYukawa) yukawa = v.prob_kernel[pid] == BLDTT_YUKAWA;
       // does any row of this warp's last target slot hold a real target?
       warp_full = (K - 1) * kConsumers + (warp * 32) < item.z;
+      // does any row of its first slot?  (if not, the warp only keeps the ring going)
+      warp_active = warp * 32 < item.z;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         acc[k] = 0.0;
@@ -805,7 +811,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_interact(InteractView 
       }
     }
     const int count = smeta[s].count;
-    if (F32) {
+    if (!warp_active) {
+      // no real target in this warp's rows: nothing to evaluate
+    } else if (F32) {
       f2_t x2[K][3];
       const f2_t* c2 = smeta[s].c2;
 #pragma unroll
@@ -822,12 +830,22 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_interact(InteractView 
         for (int k = 0; k < K; ++k) slot |= ((gm >> (k * NCW + warp)) & 1u) << k;
       }
       float a[K];
-      eval_chunk_f32<KERN, K>(sbuf[s], sres[s], count, x2, ts, c2, ext, slot, warp_full, prm, a);
+      if (KERN != kKernCoulombYukawa)
+        eval_chunk_f32<KERN, K>(sbuf[s], sres[s], count, x2, ts, c2, ext, slot, warp_full, prm, a);
+      else if (yukawa)
+        eval_chunk_f32<BLDTT_YUKAWA, K>(sbuf[s], sres[s], count, x2, ts, c2, ext, slot, warp_full, prm, a);
+      else
+        eval_chunk_f32<BLDTT_COULOMB, K>(sbuf[s], sres[s], count, x2, ts, c2, ext, slot, warp_full, prm, a);
 #pragma unroll
       for (int k = 0; k < K; ++k) acc[k] += (double)a[k];
     } else {
       double a[K];
-      eval_chunk_f64<KERN, K>(sbuf[s], count, X, kappa, a);
+      if (KERN != kKernCoulombYukawa)
+        eval_chunk_f64<KERN, K>(sbuf[s], count, X, kappa, a);
+      else if (yukawa)
+        eval_chunk_f64<BLDTT_YUKAWA, K>(sbuf[s], count, X, kappa, a);
+      else
+        eval_chunk_f64<BLDTT_COULOMB, K>(sbuf[s], count, X, kappa, a);
 #pragma unroll
       for (int k = 0; k < K; ++k) acc[k] += a[k];
     }
@@ -847,7 +865,7 @@ static const Layout kLayouts[] = {{4, 2, 6, 3}, {2, 4, 6, 3}, {4, 2, 5, 4}};
 
 template <bool F32, int KERN>
 static const void* kernel_for(int layout) {
-  if constexpr (KERN == BLDTT_COULOMB) {
+  if constexpr (KERN == BLDTT_COULOMB || KERN == kKernCoulombYukawa) {
     if (layout == 1) return reinterpret_cast<const void*>(&k_interact<F32, KERN, 2, 4, 6, 3>);
     if (layout == 2) return reinterpret_cast<const void*>(&k_interact<F32, KERN, 4, 2, 5, 4>);
   }
@@ -857,7 +875,7 @@ static const void* kernel_for(int layout) {
 // Layouts instantiated for a kernel (the autotuner tries these).
 int layouts_available(int kernel, int* out) {
   out[0] = 0;
-  if (kernel != BLDTT_COULOMB) return 1;
+  if (kernel != BLDTT_COULOMB && kernel != kKernCoulombYukawa) return 1;
   out[1] = 1;
   out[2] = 2;
   return 3;
@@ -867,6 +885,8 @@ static const void* select_kernel(int kernel, bool f32, int layout) {
   switch (kernel) {
     case BLDTT_COULOMB: return f32 ? kernel_for<true, BLDTT_COULOMB>(layout) : kernel_for<false, BLDTT_COULOMB>(layout);
     case BLDTT_YUKAWA: return f32 ? kernel_for<true, BLDTT_YUKAWA>(layout) : kernel_for<false, BLDTT_YUKAWA>(layout);
+    case kKernCoulombYukawa:
+      return f32 ? kernel_for<true, kKernCoulombYukawa>(layout) : kernel_for<false, kKernCoulombYukawa>(layout);
     case BLDTT_OSCILLATORY: return f32 ? kernel_for<true, BLDTT_OSCILLATORY>(layout) : kernel_for<false, BLDTT_OSCILLATORY>(layout);
     case BLDTT_REG_COULOMB: return f32 ? kernel_for<true, BLDTT_REG_COULOMB>(layout) : kernel_for<false, BLDTT_REG_COULOMB>(layout);
     default: return f32 ? kernel_for<true, BLDTT_TEST_POLY>(layout) : kernel_for<false, BLDTT_TEST_POLY>(layout);
@@ -924,6 +944,7 @@ static InteractView make_view(const bldtt_plan* p) {
   v.t_problem = tt.problem;
   v.prob_prm = p->prob_prm;
   v.prob_kappa = p->prob_kappa;
+  v.prob_kernel = p->prob_kernel;
   return v;
 }
 

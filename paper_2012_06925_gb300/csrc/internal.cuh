@@ -33,6 +33,9 @@ constexpr int kTile = 256;                     // targets per work item of the i
 constexpr int kChunkInfo = 2;                  // float4 per pool chunk description
 constexpr int kItemGroups = kTile / 32;        // 32-row target groups per work item
 constexpr int kMaxDegrees = 8;                 // interpolation degrees of one plan
+// Segment kernel id of a persistent launch that drains the Coulomb and the
+// Yukawa problems of a batch together (the kernel is chosen per work item).
+constexpr int kKernCoulombYukawa = 1000;
 constexpr int kMaxClasses = 1 + 3 * kMaxDegrees;
 constexpr int kHidden = 64;                    // selector network width
 constexpr int kFeatures = 6;                   // selector network inputs
@@ -220,6 +223,9 @@ struct bldtt_plan {
   double* prob_kappa = nullptr;       // device [nprob]
   float* prob_prm = nullptr;          // device [nprob] FP32 form of the parameter
   std::vector<int> kernels_present;   // distinct kernel ids of the batch, ascending
+  // Kernel id of each persistent interaction launch: one per kernel present,
+  // except that Coulomb and Yukawa problems share one (kKernCoulombYukawa).
+  std::vector<int> segment_kernels;
   cudaStream_t stream = nullptr;      // stream of the last call (for synchronisation)
 
   bldtt::Tree tt, st;                 // target and source trees
@@ -277,6 +283,26 @@ struct bldtt_plan {
   };
   std::vector<Segment> segments;
   int interact_layout = 0;            // requested layout: 0 = 4 warps x 2 targets, 1 = 2 x 4, 2 = 4 x 2 at 5 CTAs/SM, 4 stages
+  // Real kernel evaluations per target cluster: its particle items (leaves)
+  // and its proxy items (all degrees); the costs behind target-leaf sharding.
+  int64_t* eval_part = nullptr;       // [Ct]
+  int64_t* eval_prox = nullptr;       // [Ct]
+  // Target-leaf sharding (bldtt_compute_shard): the leaf-order ranges of the
+  // last partition, and the work items of the last shard computed.
+  int32_t shard_parts = 0;            // shards of the cached partition (0: none)
+  std::vector<int32_t> shard_begin;   // [shard_parts + 1] first leaf (leaf order) of each shard
+  int32_t shard_cached = -1;          // shard whose items are below
+  std::vector<int64_t> h_eval_part, h_eval_prox;     // host copies for the shard's count
+  std::vector<int32_t> h_leaf_first, h_leaf_last;
+  double sh_evals = 0.0;              // evaluations of the cached shard's items
+  double computed_evals = 0.0;        // evaluations of the last compute's items
+  int4* sh_items = nullptr;
+  float4* sh_item_box = nullptr;
+  int32_t sh_nitems = 0;
+  std::vector<Segment> sh_segments;
+  // Leaves (leaf order) the downward leaf pass writes: [down_lo, down_hi);
+  // down_hi < 0 means all leaves.
+  int32_t down_lo = 0, down_hi = -1;
   float4* chunk_frame = nullptr;      // [pool chunks][kChunkInfo]: frame centre + count, extents + tau
   float4* item_box = nullptr;         // FP32_BULK: [items][kItemGroups][2] target group boxes (lo, hi)
   float* pool_res = nullptr;          // FP32_BULK: frame residuals of the pool's particles (pair records)
@@ -348,6 +374,11 @@ int layouts_available(int kernel, int* out);
 int interaction_grids(bldtt_plan* p);                 // launch shape of every segment
 int run_segment(bldtt_plan* p, int seg, cudaStream_t s);
 int run_interactions(bldtt_plan* p, cudaStream_t s);
+
+// ---- compute phase (capi.cu) ----
+// Upward pass, pool, interactions of the plan's current work items, downward
+// pass (leaves [down_lo, down_hi) only).
+int compute_body(bldtt_plan* p, double* phi, cudaStream_t s);
 
 // ---- learned selector (learned.cu) ----
 // Class decision of every frontier pair (class >= 0, kChoiceNoApprox, or

@@ -884,11 +884,16 @@ int downward_pass(bldtt_plan* p, double* phi_user, cudaStream_t s) {
   const int P = p->P, np = p->np;
   const int stride = 3 * P + ((3 * P) % 2 == 0 ? 1 : 0);
   const size_t tz = (size_t)kDownThreads * (P | 1);
+  // Leaves written: all, or the leaf-order range of one shard.
+  const int32_t leaf_lo = p->down_hi < 0 ? 0 : p->down_lo;
+  const int32_t nleaves = (p->down_hi < 0 ? T.nleaves : p->down_hi) - leaf_lo;
+  if (nleaves <= 0) return BLDTT_OK;
+  const int32_t* leaf_ids = T.leaf_ids + leaf_lo;
   if (p->precision == BLDTT_FP32_BULK && P >= kFixedPMin && P <= kFixedPMax) {
     switch (P) {
 #define BL_DOWN_LEAF(PP)                                                                      \
   case PP:                                                                                    \
-    k_down_leaf_f32<PP><<<dim3(T.nleaves, kDownF32Split), kDownF32Threads, 0, s>>>(T.leaf_ids, T.begin, T.end, T.x, \
+    k_down_leaf_f32<PP><<<dim3(nleaves, kDownF32Split), kDownF32Threads, 0, s>>>(leaf_ids, T.begin, T.end, T.x, \
                                                               T.y, T.z, T.perm, T.nodes,      \
                                                               p->phit, p->phi_near, phi_user); \
     break;
@@ -899,13 +904,13 @@ int downward_pass(bldtt_plan* p, double* phi_user, cudaStream_t s) {
   } else if (p->precision == BLDTT_FP32_BULK) {
     size_t bytes = sizeof(double) * (3 * P + (size_t)kDownThreads * stride) + sizeof(float) * (np + tz) +
                    sizeof(float) * 6 * kMaxP;
-    k_down_leaf<true><<<T.nleaves, kDownThreads, bytes, s>>>(T.leaf_ids, T.begin, T.end, T.x, T.y,
+    k_down_leaf<true><<<nleaves, kDownThreads, bytes, s>>>(leaf_ids, T.begin, T.end, T.x, T.y,
                                                               T.z, T.perm, T.nodes, p->n, p->phit,
                                                               p->phi_near, phi_user);
   } else {
     size_t bytes = sizeof(double) * (3 * P + (size_t)kDownThreads * stride + np + tz) +
                    sizeof(float) * 6 * kMaxP;
-    k_down_leaf<false><<<T.nleaves, kDownThreads, bytes, s>>>(T.leaf_ids, T.begin, T.end, T.x, T.y,
+    k_down_leaf<false><<<nleaves, kDownThreads, bytes, s>>>(leaf_ids, T.begin, T.end, T.x, T.y,
                                                                T.z, T.perm, T.nodes, p->n, p->phit,
                                                                p->phi_near, phi_user);
   }

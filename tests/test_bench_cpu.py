@@ -94,6 +94,8 @@ def test_reference_arm_prints_the_contract_line(bench):
     assert d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 0
     assert d["config"]["workload"].startswith("uniform_n1e6")
     assert d["value"] > 0 and d["cpu_baseline"]["value"] == d["value"]
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle"
+    assert d["cpu_baseline"]["cores"] == bench.host_cores()   # one oracle process per host core
+    assert f"{bench.host_cores()} whole target leaves" in d["cpu_baseline"]["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}

@@ -39,8 +39,27 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, name), name
 
 
-def test_stats_struct_size_matches_header(lib):
-    assert ctypes.sizeof(B.Stats) == 168
+def test_stats_struct_size_matches_header(lib, tmp_path):
+    """The binding's Stats layout has the size and field offsets that a C
+    compiler gives bldtt_stats_t from include/bldtt.h."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [name for name, _ in B.Stats._fields_]
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "bldtt.h"\nint main(void){'
+                   'printf("%zu", sizeof(bldtt_stats_t));'
+                   + "".join(f'printf(" %zu", offsetof(bldtt_stats_t, {f}));' for f in fields)
+                   + 'return 0;}\n')
+    exe = tmp_path / "sz"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, f"-I{inc}", str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    assert got[0] == ctypes.sizeof(B.Stats)
+    assert got[1:] == [getattr(B.Stats, f).offset for f in fields]
 
 
 def test_status_strings(lib):

@@ -57,30 +57,31 @@ def test_sampled_fp64_potentials(full):
     assert O.max_norm_error(ref, got) <= 1e-10
 
 
-# Max-norm bound of FP32_BULK at this size, from the arithmetic: a source in a
-# 256-point chunk frame of half-size rho ~ 6e-2 (Morton-ordered leaves of ~2000
-# points, leaf side 1/4) is rounded to ~u*rho absolute per coordinate, u = 2^-24,
-# so a pair at distance r carries a relative error ~2*u*rho/r.  Targets within
-# tau = 0.3|e| ~ 3e-2 of a particle chunk's box (|e| its half-diagonal) take the
-# frame residuals and are back at a few u, so every uncompensated term has
-# r >= tau and a relative error <= 2*u*rho/tau ~ 2.4e-7.  A target's error is
-# then at most 2.4e-7 * sum_j |q_j|/r_ij ~ 2.4e-7 * 5e5 (all signs aligned, 1E6
-# charges of mean modulus 1/2 at mean 1/r ~ 1), against max|phi| ~ 6e3 from the
-# closest pair (r ~ 1.6e-4): ~2e-5 of max|phi| in the worst alignment.  The bound
-# keeps a factor 2.5 over that.  The metric itself is the rel-l2 error (<= 1e-6).
-FP32_MAX_FULL = 5e-5
+# Max-norm of FP32_BULK against FP64, relative to max|phi|: the same 1e-5 as
+# on the small parity cases (the tolerance proposed for the metric beside its
+# rel-l2 budget of 1e-6).  Why it holds at this size: every term whose pair
+# distance r is below tau = 0.3|e| of a particle chunk (|e| its
+# half-diagonal, ~0.1 here) takes the frame residuals and is back at a few u
+# (u = 2^-24); the rest carry a relative error <= 2 u rho/tau ~ 2.4e-7 each
+# (rho ~ 6e-2 the chunk's half size), and these errors have random signs, so
+# a target's error grows like the square root of its ~1e5 near-field terms,
+# not like their sum.  The measured value is printed.
+FP32_MAX_FULL = 1e-5
 
 
 def test_fp32_bulk_against_fp64_and_direct(full):
     err = O.relative_l2_error(full["phi64"], full["phi32"])
+    mx = O.max_norm_error(full["phi64"], full["phi32"])
+    print(f"uniform_n1e6: FP32 vs FP64 rel-l2 {err:.3e}, max-norm {mx:.3e}")
     assert err <= 1e-6
-    assert O.max_norm_error(full["phi64"], full["phi32"]) <= FP32_MAX_FULL
+    assert mx <= FP32_MAX_FULL
     rng = np.random.default_rng(7)
     idx = np.sort(rng.choice(full["tgt"].shape[1], size=2000, replace=False))
     ts = to_dev(full["tgt"][:, idx])
     direct = B.direct_sum(ts, full["dt"], full["dq"]).cpu().numpy()
     e64 = O.relative_l2_error(direct, full["phi64"][idx])
     e32 = O.relative_l2_error(direct, full["phi32"][idx])
+    print(f"uniform_n1e6 vs direct sum (2000 targets): FP64 {e64:.3e}, FP32 {e32:.3e}")
     # Sec. 4.1 reports 3.67E-8 at this size; FP32 evaluation adds at most ~1E-6.
     assert 3e-9 <= e64 <= 3e-7
     assert e32 <= e64 + 1e-6

@@ -63,3 +63,55 @@ def test_learned_selector_beats_the_fixed_rule(trained):
     (e_fix, w_fix, _), (e_learn, w_learn, _) = out["fixed"], out["learned"]
     assert e_fix <= 1e-6 and e_learn <= 1e-6
     assert w_learn <= 0.8 * w_fix, (w_learn, w_fix)
+
+
+def _timed_step(make_plan, flush, reps=3):
+    """Set-up + compute timed with CUDA events (median of reps after one
+    warm-up, L2 flushed before each); returns (phi numpy, step ms, interaction
+    ms, evaluations)."""
+    steps, inter = [], []
+    for r in range(reps + 1):
+        flush.fill_(float(r))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan = make_plan()
+        phi = plan.compute()
+        e1.record()
+        st = plan.stats()                       # synchronises
+        plan.check_error()
+        plan.close()
+        if r > 0:
+            steps.append(e0.elapsed_time(e1))
+            inter.append(st["ms_interact"])
+    return phi.cpu().numpy(), float(np.median(steps)), float(np.median(inter)), sum(st["interactions"])
+
+
+def test_learned_selector_at_1e7_with_the_1e8_protocol(trained):
+    """The 1E8 workload's protocol at 1E7 (the largest size the test budget
+    allows): uniform points with that workload's seed, Coulomb, leaves 2000,
+    FP32 bulk; the trained selector against the fixed rule n = 8, theta = 0.7;
+    errors against the FP64 direct sum on 1E4 seeded sampled targets.  Both
+    must meet 1e-6, and the selector must save interaction time (CUDA events),
+    not only evaluations."""
+    sel, _ = trained
+    t, _, q = W.make_problem("uniform", 10_000_000, seed=5)
+    dt, dq = torch.from_numpy(t).cuda(), torch.from_numpy(q).cuda()
+    idx = np.sort(np.random.default_rng(77).choice(t.shape[1], 10_000, replace=False))
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    base = dict(theta=0.7, N0=2000, M0=2000, precision=B.FP32_BULK)
+    runs = {
+        "fixed": lambda: B.Plan(dt, dt, dq, n=8, **base),
+        "learned": lambda: B.Plan.learned(dt, dt, dq, sel, **base),
+    }
+    out = {}
+    for name, make in runs.items():
+        phi, ms_step, ms_int, evals = _timed_step(make, flush)
+        out[name] = (S.sampled_error(t, q, phi, idx), ms_step, ms_int, evals)
+    for name, (err, ms_step, ms_int, evals) in out.items():
+        print(f"1E7 {name}: error {err:.3e}, step {ms_step:.1f} ms, interaction {ms_int:.1f} ms, "
+              f"{evals:.3e} evaluations")
+    (e_fix, s_fix, i_fix, w_fix), (e_learn, s_learn, i_learn, w_learn) = out["fixed"], out["learned"]
+    assert e_fix <= 1e-6 and e_learn <= 1e-6
+    assert w_learn <= 0.8 * w_fix, (w_learn, w_fix)
+    assert i_learn <= 0.8 * i_fix, (i_learn, i_fix)          # interaction time
+    assert s_learn <= 0.85 * s_fix, (s_learn, s_fix)         # whole step, set-up included
