@@ -368,18 +368,33 @@ int bldtt_partition_leaves(const double* leaf_cost, int32_t nleaves, int32_t nsh
 int bldtt_compute_graph(bldtt_plan* plan, double* phi, void* cuda_stream);
 
 /*
- * bldtt_autotune - pick the fastest consumer layout of the interaction kernel
- * for each kernel type of the plan: runs bldtt_compute once (phi, device M
- * float64, receives its potentials), then times each kernel type's
- * persistent launch three times per layout instantiated for that kernel
- * (Coulomb: 4 warps x 2 targets at 6 CTAs/SM with a 3-stage ring or at 5
- * CTAs/SM with a 4-stage ring, 2 warps x 4 targets; other kernels: 4 warps x 2
- * targets, 3 stages) with CUDA events and keeps the fastest
- * in the plan.  Results do not depend on the layout (bit for bit).  *chosen
- * (may be NULL) receives the layout picked for the lowest kernel id of the
- * plan.  Synchronous.  Errors: EINVAL, ECUDA, ETIMEOUT.
+ * bldtt_autotune - pick the fastest launch shape of the interaction kernel
+ * for each persistent launch of the plan: runs bldtt_compute once (phi,
+ * device M float64, receives its potentials), then times each launch three
+ * times per layout instantiated for its kernel with CUDA events and keeps the
+ * fastest in the plan.  A layout fixes the CTA's tile of 256 targets (consumer
+ * warps x targets per thread: 4 x 2 or 2 x 4), the CTAs per SM the registers
+ * are sized for (6 or 5), the depth of the shared-memory ring of source
+ * chunks (3 or 4 stages) and whether warps whose rows hold no real target
+ * skip their work: layouts 0 = 4x2, 6 CTAs, 3 stages; 1 = 2x4, 6 CTAs, 3
+ * stages; 2 = 4x2, 5 CTAs, 4 stages; 3-5 = the same with skipping (Coulomb
+ * and the shared Coulomb/Yukawa launch; other kernels: layouts 0 and 3).
+ * Results do not depend on the layout (bit for bit).  *chosen (may be NULL)
+ * receives the layout picked for the plan's first launch; the searched table
+ * is kept for bldtt_autotune_table.  Synchronous.  Errors: EINVAL, ECUDA,
+ * ETIMEOUT.
  */
 int bldtt_autotune(bldtt_plan* plan, double* phi, void* cuda_stream, int* chosen);
+
+/*
+ * bldtt_autotune_table - the table the last bldtt_autotune searched: for each
+ * of its *rows entries (at most capacity are written; *rows receives the
+ * total), the launch index, the kernel id of that launch (1000: Coulomb and
+ * Yukawa items in one launch), the layout and its best time in ms.  Host
+ * arrays.  Errors: EINVAL (no autotune yet, or NULL arguments).
+ */
+int bldtt_autotune_table(const bldtt_plan* plan, int capacity, int* rows, int* launch, int* kernel,
+                         int* layout, float* ms);
 
 /*
  * bldtt_wait_probe - failure detection without a fault: one CTA waits, with

@@ -30,7 +30,7 @@ EXPORTED = (
     "bldtt_bounding_box_noalloc", "bldtt_selector_param_count", "bldtt_setup_learned",
     "bldtt_list_classes", "bldtt_mlp_forward", "bldtt_mlp_gradients", "bldtt_mlp_adam",
     "bldtt_pair_features", "bldtt_pair_errors", "bldtt_wait_probe", "bldtt_compute_shard",
-    "bldtt_partition_leaves",
+    "bldtt_partition_leaves", "bldtt_autotune_table",
 )
 
 
@@ -130,6 +130,9 @@ def load_library(path: str = LIB_PATH):
         "bldtt_wait_probe": (i32, [i64, vp]),
         "bldtt_compute_shard": (i32, [vp, i32, i32, vp, vp]),
         "bldtt_partition_leaves": (i32, [P_dbl, ctypes.c_int32, ctypes.c_int32, P_i32]),
+        "bldtt_autotune_table": (i32, [vp, i32, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_float)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -266,6 +269,17 @@ class Plan:
         _check(load_library().bldtt_autotune(self._handle(), _dptr(phi, self.M), _stream_ptr(stream),
                                              ctypes.byref(chosen)))
         return chosen.value
+
+    def autotune_table(self):
+        """The last autotune's searched table: (launch, kernel, layout, ms) rows."""
+        lib = load_library()
+        rows = ctypes.c_int(0)
+        _check(lib.bldtt_autotune_table(self._handle(), 0, ctypes.byref(rows), None, None, None, None))
+        n = rows.value
+        ints = [(ctypes.c_int * max(n, 1))() for _ in range(3)]
+        ms = (ctypes.c_float * max(n, 1))()
+        _check(lib.bldtt_autotune_table(self._handle(), n, ctypes.byref(rows), *ints, ms))
+        return [(ints[0][i], ints[1][i], ints[2][i], ms[i]) for i in range(n)]
 
     def compute(self, phi=None, stream=None):
         import torch

@@ -229,13 +229,17 @@ int setup_impl(bldtt_plan* p, const double* targets, const double* sources, cons
   BL_TRY(dalloc_n(&p->phi_near, (size_t)p->M, s));
   BL_TRY(dalloc_n(&p->item_counter, p->segments.size() > 0 ? p->segments.size() : 1, s));
   BL_TRY(build_chunk_frames(p, s));
-  p->interact_layout = 0;
+  // Default layout: warps of empty rows skip their work when that saves at
+  // least 2 % of the evaluations (many items smaller than a tile).
+  const bool skip = p->skip_saved_evaluations > 0.02 * p->executed_noskip;
+  p->executed_evaluations = skip ? p->executed_skip : p->executed_noskip;
+  p->interact_layout = skip ? kLayoutSkip : 0;
   if (const char* lay = std::getenv("BLDTT_INTERACT_LAYOUT")) {
     int l = std::atoi(lay);
-    p->interact_layout = (l >= 0 && l < 3) ? l : 0;
+    p->interact_layout = (l >= 0 && l < kMaxLayouts) ? l : 0;
   }
   for (auto& seg : p->segments) {      // the requested layout where it is instantiated
-    int cand[3];
+    int cand[kMaxLayouts];
     const int nc = layouts_available(seg.kernel, cand);
     seg.layout = 0;
     for (int i = 0; i < nc; ++i)
@@ -649,9 +653,11 @@ int bldtt_autotune(bldtt_plan* p, double* phi, void* cuda_stream, int* chosen) {
   BL_CUDA(cudaEventCreate(&e0));
   BL_CUDA(cudaEventCreate(&e1));
   int rc = BLDTT_OK;
+  p->tune_table.clear();
+  p->tuned = false;
   for (size_t g = 0; g < p->segments.size() && rc == BLDTT_OK; ++g) {
     auto& seg = p->segments[g];
-    int cand[3];
+    int cand[kMaxLayouts];
     const int ncand = layouts_available(seg.kernel, cand);
     float best = -1.f;
     int best_layout = seg.layout;
@@ -670,6 +676,7 @@ int bldtt_autotune(bldtt_plan* p, double* phi, void* cuda_stream, int* chosen) {
         cudaEventElapsedTime(&ms, e0, e1);
         if (rep == 1 || (rep > 1 && ms < t)) t = ms;
       }
+      if (rc == BLDTT_OK) p->tune_table.push_back({(int)g, seg.kernel, cand[i], t});
       if (rc == BLDTT_OK && (best < 0.f || t < best)) {
         best = t;
         best_layout = cand[i];
@@ -686,6 +693,27 @@ int bldtt_autotune(bldtt_plan* p, double* phi, void* cuda_stream, int* chosen) {
     p->graph_exec = nullptr;
   }
   if (chosen) *chosen = p->segments.empty() ? 0 : p->segments[0].layout;
+  p->tuned = true;
+  return BLDTT_OK;
+}
+
+int bldtt_autotune_table(const bldtt_plan* p, int capacity, int* rows, int* launch, int* kernel,
+                         int* layout, float* ms) {
+  if (!p || !rows || capacity < 0 || (capacity > 0 && (!launch || !kernel || !layout || !ms))) {
+    set_error("autotune_table: plan, rows and (for capacity > 0) the four arrays must be non-NULL");
+    return BLDTT_EINVAL;
+  }
+  if (!p->tuned) {
+    set_error("autotune_table: the plan has not been autotuned");
+    return BLDTT_EINVAL;
+  }
+  *rows = (int)p->tune_table.size();
+  for (int i = 0; i < *rows && i < capacity; ++i) {
+    launch[i] = p->tune_table[i].launch;
+    kernel[i] = p->tune_table[i].kernel;
+    layout[i] = p->tune_table[i].layout;
+    ms[i] = p->tune_table[i].ms;
+  }
   return BLDTT_OK;
 }
 

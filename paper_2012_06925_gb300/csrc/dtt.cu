@@ -336,10 +336,16 @@ __device__ __forceinline__ void class_work(const ListView& L, const int32_t* s_b
   }
 }
 
-// Target rows the interaction kernel evaluates for m targets cut into tiles of
-// kTile: every 32-row group holding a real target (the consumer warps of the
-// default layout skip empty groups; a group's idle rows are evaluated).
-__device__ __forceinline__ int64_t executed_rows(int64_t m) { return (m + 31) / 32 * 32; }
+// Target rows the interaction kernel evaluates in its default consumer layout
+// (4 warps x 2 rows of 32) for m targets cut into tiles of kTile: with idle
+// warps skipping, every 32-row group that holds a real target (its idle rows
+// included); without, a partial tile of at most 128 targets costs all four
+// warps' first rows.
+__device__ __forceinline__ int64_t executed_rows_skip(int64_t m) { return (m + 31) / 32 * 32; }
+__device__ __forceinline__ int64_t executed_rows_noskip(int64_t m) {
+  const int64_t r = m % kTile;
+  return m - r + (r == 0 ? 0 : (r <= kTile / 2 ? kTile / 2 : (r + 31) / 32 * 32));
+}
 
 // Items of target cluster c: tiles of its particles (a leaf: PP and PC of every
 // degree, on the leaf and on each ancestor), and tiles of its proxy points of
@@ -350,7 +356,7 @@ __global__ void k_item_count(int32_t nct, ListView L, const int32_t* __restrict_
                              const int32_t* __restrict__ end, const int32_t* __restrict__ s_begin,
                              const int32_t* __restrict__ s_end, int32_t* __restrict__ nitems,
                              int64_t* __restrict__ cost_part, int64_t* __restrict__ cost_prox,
-                             unsigned long long* __restrict__ executed,
+                             unsigned long long* __restrict__ executed,   // [2]: skip, no skip
                              int64_t* __restrict__ eval_part, int64_t* __restrict__ eval_prox) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nct) return;
@@ -363,7 +369,8 @@ __global__ void k_item_count(int32_t nct, ListView L, const int32_t* __restrict_
     }
   const int32_t tp = cp > 0 ? (end[c] - begin[c] + kTile - 1) / kTile : 0;
   int32_t items = tp;
-  unsigned long long ex = cp > 0 ? (unsigned long long)executed_rows(end[c] - begin[c]) * sp : 0ull;
+  unsigned long long ex = cp > 0 ? (unsigned long long)executed_rows_skip(end[c] - begin[c]) * sp : 0ull;
+  unsigned long long ex_ns = cp > 0 ? (unsigned long long)executed_rows_noskip(end[c] - begin[c]) * sp : 0ull;
   eval_part[c] = cp > 0 ? (int64_t)(end[c] - begin[c]) * sp : 0;   // real evaluations (no padding)
   int64_t evq = 0;
   for (int i = 0; i < L.deg.n; ++i) {   // CP + CC of degree i on the cluster itself
@@ -373,7 +380,10 @@ __global__ void k_item_count(int32_t nct, ListView L, const int32_t* __restrict_
     const int32_t tq = cq > 0 ? (L.deg.np[i] + kTile - 1) / kTile : 0;
     items += tq;
     cost_prox[(int64_t)c * kMaxDegrees + i] = cq;
-    if (cq > 0) ex += (unsigned long long)executed_rows(L.deg.np[i]) * sq;
+    if (cq > 0) {
+      ex += (unsigned long long)executed_rows_skip(L.deg.np[i]) * sq;
+      ex_ns += (unsigned long long)executed_rows_noskip(L.deg.np[i]) * sq;
+    }
     if (cq > 0) evq += (int64_t)L.deg.np[i] * sq;
   }
   eval_prox[c] = evq;
@@ -381,10 +391,13 @@ __global__ void k_item_count(int32_t nct, ListView L, const int32_t* __restrict_
   cost_part[c] = cp;
   // evaluations the kernel performs: every target slot of every tile meets every real source
   if (ex) atomicAdd(executed, ex);
+  if (ex_ns) atomicAdd(executed + 1, ex_ns);
 }
 
 // Sort key of an item: the segment (kernel group) of its problem in the high
-// bits, then decreasing cost.
+// bits, then (in the shared Coulomb/Yukawa launch) its kernel, then decreasing
+// cost.  Kernel-major order keeps one kernel's code hot on all SMs at a time:
+// items of the two kernels interleaved by cost ran 44 % slower.
 struct SegmentMap {
   int n;
   int kernel[8];
@@ -401,13 +414,16 @@ __global__ void k_item_fill(int32_t nct, const int32_t* __restrict__ off,
   int32_t o = off[c];
   const uint32_t kKeyMax = (1u << 24) - 1u;
   uint32_t seg = 0;
+  uint32_t sub = 0;          // the shared Coulomb/Yukawa launch: Coulomb items first
   const int kern = prob_kernel[problem[c]];
   for (int i = 0; i < segmap.n; ++i)
     if (segmap.kernel[i] == kern ||
-        (segmap.kernel[i] == kKernCoulombYukawa && (kern == BLDTT_COULOMB || kern == BLDTT_YUKAWA)))
+        (segmap.kernel[i] == kKernCoulombYukawa && (kern == BLDTT_COULOMB || kern == BLDTT_YUKAWA))) {
       seg = (uint32_t)i;
+      sub = segmap.kernel[i] == kKernCoulombYukawa && kern == BLDTT_YUKAWA ? 1u : 0u;
+    }
   if (cost_part[c] > 0) {
-    uint32_t k = (seg << 24) | (kKeyMax - (uint32_t)min((int64_t)kKeyMax, cost_part[c]));
+    uint32_t k = (seg << 25) | (sub << 24) | (kKeyMax - (uint32_t)min((int64_t)kKeyMax, cost_part[c]));
     for (int32_t r = begin[c]; r < end[c]; r += kTile) {
       items[o] = make_int4(c, r, min(kTile, end[c] - r), kItemParticles);
       keys[o] = k;
@@ -419,7 +435,7 @@ __global__ void k_item_fill(int32_t nct, const int32_t* __restrict__ off,
     const int64_t cq = cost_prox[(int64_t)c * kMaxDegrees + i];
     if (cq <= 0) continue;
     const int32_t np = deg.np[i];
-    uint32_t k = (seg << 24) | (kKeyMax - (uint32_t)min((int64_t)kKeyMax, cq));
+    uint32_t k = (seg << 25) | (sub << 24) | (kKeyMax - (uint32_t)min((int64_t)kKeyMax, cq));
     for (int32_t r = 0; r < np; r += kTile) {
       items[o] = make_int4(c, r, min(kTile, np - r), kItemProxies + i);
       keys[o] = k;
@@ -433,8 +449,8 @@ __global__ void k_item_fill(int32_t nct, const int32_t* __restrict__ off,
 __global__ void k_segment_starts(const uint32_t* __restrict__ keys, int32_t n, int32_t* __restrict__ first) {
   const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const uint32_t sg = keys[i] >> 24;
-  if (i == 0 || (keys[i - 1] >> 24) != sg) first[sg] = i;
+  const uint32_t sg = keys[i] >> 25;
+  if (i == 0 || (keys[i - 1] >> 25) != sg) first[sg] = i;
 }
 
 __global__ void k_gather_items(const int4* __restrict__ src, const int32_t* __restrict__ idx,
@@ -530,8 +546,8 @@ int build_work_items(bldtt_plan* p, cudaStream_t s) {
   BL_TRY(dalloc_n(&cost_part, nct, s));
   BL_TRY(dalloc_n(&cost_prox, (size_t)nct * kMaxDegrees, s));
   unsigned long long* executed = nullptr;
-  BL_TRY(dalloc_n(&executed, 1, s));
-  BL_CUDA(cudaMemsetAsync(executed, 0, sizeof(unsigned long long), s));
+  BL_TRY(dalloc_n(&executed, 2, s));
+  BL_CUDA(cudaMemsetAsync(executed, 0, 2 * sizeof(unsigned long long), s));
   dfree_ptr(p->eval_part, s);
   dfree_ptr(p->eval_prox, s);
   BL_TRY(dalloc_n(&p->eval_part, nct, s));
@@ -561,7 +577,7 @@ int build_work_items(bldtt_plan* p, cudaStream_t s) {
   // each persistent launch's tail is short.
   int seg_bits = 0;
   while ((1 << seg_bits) < segmap.n) ++seg_bits;
-  BL_TRY(radix_sort_pairs(keys, vals, ni, 24 + seg_bits, s, cnt));
+  BL_TRY(radix_sort_pairs(keys, vals, ni, 25 + seg_bits, s, cnt));
   int32_t* seg_first = nullptr;
   BL_TRY(dalloc_n(&seg_first, 8, s));
   BL_CUDA(cudaMemsetAsync(seg_first, 0xff, 8 * sizeof(int32_t), s));
@@ -582,10 +598,13 @@ int build_work_items(bldtt_plan* p, cudaStream_t s) {
                                                                     p->deg, p->item_box);
     BL_LAUNCHED(cnt.launches);
   }
-  unsigned long long h_exec = 0;
+  unsigned long long h_exec[2] = {0, 0};
   BL_TRY(read_device(seg_first, h_first, sizeof(h_first), s));
-  BL_TRY(read_device(executed, &h_exec, sizeof(h_exec), s));
-  p->executed_evaluations = (double)h_exec;
+  BL_TRY(read_device(executed, h_exec, sizeof(h_exec), s));
+  p->executed_skip = (double)h_exec[0];
+  p->executed_noskip = (double)h_exec[1];
+  p->skip_saved_evaluations = p->executed_noskip - p->executed_skip;
+  p->executed_evaluations = p->executed_noskip;
   dfree(seg_first, s);
   p->segments.clear();
   for (int i = 0; i < segmap.n; ++i) {

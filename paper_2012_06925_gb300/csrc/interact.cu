@@ -731,7 +731,7 @@ __device__ __forceinline__ void eval_chunk_f64(const void* buf, int count, const
   }
 }
 
-template <bool F32, int KERN, int NCW, int K, int MINB, int STAGES>
+template <bool F32, int KERN, int NCW, int K, int MINB, int STAGES, bool SKIP>
 __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_interact(const __grid_constant__ InteractView v) {
   static_assert(NCW * 32 * K == kTile, "a CTA covers exactly one work-item tile");
   constexpr int kConsumers = NCW * 32;
@@ -793,8 +793,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_interact(const __grid_
       if (KERN == kKernCoulombYukawa) yukawa = v.prob_kernel[pid] == BLDTT_YUKAWA;
       // does any row of this warp's last target slot hold a real target?
       warp_full = (K - 1) * kConsumers + (warp * 32) < item.z;
-      // does any row of its first slot?  (if not, the warp only keeps the ring going)
-      warp_active = warp * 32 < item.z;
+      // does any row of its first slot?  (if not, the warp only keeps the ring
+      // going; layouts for plans with many small items skip such warps' work)
+      if (SKIP) warp_active = warp * 32 < item.z;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         acc[k] = 0.0;
@@ -811,9 +812,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_interact(const __grid_
       }
     }
     const int count = smeta[s].count;
-    if (!warp_active) {
+    if (SKIP && !warp_active) {
       // no real target in this warp's rows: nothing to evaluate
-    } else if (F32) {
+    } else if constexpr (F32) {
       f2_t x2[K][3];
       const f2_t* c2 = smeta[s].c2;
 #pragma unroll
@@ -855,31 +856,46 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_interact(const __grid_
 }
 
 // Consumer layouts the kernel is instantiated for: NCW warps x K targets, the
-// CTAs per SM the register allocation is sized for, and the depth of the
+// CTAs per SM the register allocation is sized for, the depth of the
 // shared-memory ring (3 stages let six CTAs share an SM; 4 stages at five
-// CTAs hide the producer's list walks better on short items).
+// CTAs hide the producer's list walks better on short items), and whether
+// warps whose rows hold no real target skip their work (worth it when many
+// items are smaller than a tile; a cost of about 1 % otherwise).  Layouts
+// kLayoutSkip + i are layout i with skipping.
 struct Layout {
   int ncw, k, minb, stages;
 };
-static const Layout kLayouts[] = {{4, 2, 6, 3}, {2, 4, 6, 3}, {4, 2, 5, 4}};
+static const Layout kLayouts[kLayoutSkip] = {{4, 2, 6, 3}, {2, 4, 6, 3}, {4, 2, 5, 4}};
+
+template <bool F32, int KERN, bool SKIP>
+static const void* kernel_for_skip(int base) {
+  if constexpr (KERN == BLDTT_COULOMB || KERN == kKernCoulombYukawa) {
+    if (base == 1) return reinterpret_cast<const void*>(&k_interact<F32, KERN, 2, 4, 6, 3, SKIP>);
+    if (base == 2) return reinterpret_cast<const void*>(&k_interact<F32, KERN, 4, 2, 5, 4, SKIP>);
+  }
+  return reinterpret_cast<const void*>(&k_interact<F32, KERN, 4, 2, 6, 3, SKIP>);
+}
 
 template <bool F32, int KERN>
 static const void* kernel_for(int layout) {
-  if constexpr (KERN == BLDTT_COULOMB || KERN == kKernCoulombYukawa) {
-    if (layout == 1) return reinterpret_cast<const void*>(&k_interact<F32, KERN, 2, 4, 6, 3>);
-    if (layout == 2) return reinterpret_cast<const void*>(&k_interact<F32, KERN, 4, 2, 5, 4>);
+  if constexpr (F32) {
+    if (layout >= kLayoutSkip) return kernel_for_skip<F32, KERN, true>(layout - kLayoutSkip);
   }
-  return reinterpret_cast<const void*>(&k_interact<F32, KERN, 4, 2, 6, 3>);
+  // FP64: the skipping instances are not built (the FP64 path's cost is its
+  // arithmetic, not idle rows); a skipping layout runs its base layout.
+  return kernel_for_skip<F32, KERN, false>(layout % kLayoutSkip);
 }
 
 // Layouts instantiated for a kernel (the autotuner tries these).
 int layouts_available(int kernel, int* out) {
-  out[0] = 0;
-  if (kernel != BLDTT_COULOMB && kernel != kKernCoulombYukawa) return 1;
-  out[1] = 1;
-  out[2] = 2;
-  return 3;
+  const int nbase = (kernel == BLDTT_COULOMB || kernel == kKernCoulombYukawa) ? kLayoutSkip : 1;
+  int n = 0;
+  for (int i = 0; i < nbase; ++i) out[n++] = i;
+  for (int i = 0; i < nbase; ++i) out[n++] = kLayoutSkip + i;
+  return n;
 }
+
+int layout_threads(int layout) { return (kLayouts[layout % kLayoutSkip].ncw + 1) * 32; }
 
 static const void* select_kernel(int kernel, bool f32, int layout) {
   switch (kernel) {
@@ -902,7 +918,7 @@ int interaction_grids(bldtt_plan* p) {
   const bool f32 = p->precision == BLDTT_FP32_BULK;
   for (auto& seg : p->segments) {
     int per_sm = 0;
-    seg.threads = (kLayouts[seg.layout].ncw + 1) * 32;
+    seg.threads = layout_threads(seg.layout);
     BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &per_sm, select_kernel(seg.kernel, f32, seg.layout), seg.threads, 0));
     if (per_sm < 1) per_sm = 1;

@@ -36,6 +36,10 @@ constexpr int kMaxDegrees = 8;                 // interpolation degrees of one p
 // Segment kernel id of a persistent launch that drains the Coulomb and the
 // Yukawa problems of a batch together (the kernel is chosen per work item).
 constexpr int kKernCoulombYukawa = 1000;
+// Interaction-kernel layouts: kLayoutSkip base layouts, and the same again
+// (ids kLayoutSkip..2*kLayoutSkip-1) with idle warps skipping their work.
+constexpr int kLayoutSkip = 3;
+constexpr int kMaxLayouts = 2 * kLayoutSkip;
 constexpr int kMaxClasses = 1 + 3 * kMaxDegrees;
 constexpr int kHidden = 64;                    // selector network width
 constexpr int kFeatures = 6;                   // selector network inputs
@@ -274,6 +278,9 @@ struct bldtt_plan {
   int32_t nitems = 0;
   int32_t* item_counter = nullptr;    // one per segment
   double executed_evaluations = 0.0;
+  // Evaluations the interaction kernel performs with and without idle warps
+  // skipping their work (rows of 32-target groups holding no real target).
+  double executed_skip = 0.0, executed_noskip = 0.0, skip_saved_evaluations = 0.0;
   // Items are grouped by the kernel of their problem; each group is one
   // persistent launch of the interaction kernel specialised for that kernel.
   struct Segment {
@@ -282,7 +289,13 @@ struct bldtt_plan {
     int layout, grid, threads;        // consumer layout and launch shape
   };
   std::vector<Segment> segments;
-  int interact_layout = 0;            // requested layout: 0 = 4 warps x 2 targets, 1 = 2 x 4, 2 = 4 x 2 at 5 CTAs/SM, 4 stages
+  struct TuneRow {
+    int launch, kernel, layout;
+    float ms;
+  };
+  std::vector<TuneRow> tune_table;    // what the last bldtt_autotune searched
+  bool tuned = false;
+  int interact_layout = 0;            // requested layout: 0 = 4 warps x 2 targets, 1 = 2 x 4, 2 = 4 x 2 at 5 CTAs/SM, 4 stages; +kLayoutSkip: idle warps skip
   // Real kernel evaluations per target cluster: its particle items (leaves)
   // and its proxy items (all degrees); the costs behind target-leaf sharding.
   int64_t* eval_part = nullptr;       // [Ct]

@@ -193,3 +193,8 @@ def test_binding_refuses_host_tensors(lib):
         B.Plan(pts.float(), pts.float(), q.float())
     with pytest.raises(ValueError):
         B.Plan(pts.t(), pts.t(), q)
+
+
+def test_autotune_table_rejects_null_arguments(lib):
+    rows = ctypes.c_int(0)
+    assert lib.bldtt_autotune_table(None, 0, ctypes.byref(rows), None, None, None, None) == 1

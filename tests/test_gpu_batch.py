@@ -1,5 +1,6 @@
 """Batched problems (bldtt_setup_batch): one plan, one persistent interaction
-launch per kernel type and one CUDA graph for many independent problems.
+launch for the Coulomb and Yukawa problems together (one more per other
+kernel) and one CUDA graph for many independent problems.
 
 Each problem of the batch must equal the oracle's BLDTT of that problem alone
 (trees, lists and potentials), and the batched potentials must equal, bit for
@@ -114,6 +115,10 @@ def test_graph_replay_and_autotune(probs):
                 stream.synchronize()
                 assert np.array_equal(phi.cpu().numpy(), ref)
         layout = plan.autotune(phi)
-        assert layout in (0, 1, 2)                   # layouts instantiated for Coulomb
+        assert layout in range(6)                    # layouts instantiated for Coulomb
+        table = plan.autotune_table()                # (launch, kernel, layout, ms) per tried layout
+        first = [r for r in table if r[0] == 0]
+        assert sorted(r[2] for r in first) == list(range(6))
+        assert min(first, key=lambda r: r[3])[2] == layout
         assert np.array_equal(plan.compute().cpu().numpy(), ref)
         plan.check_error()
