@@ -405,11 +405,15 @@ def run_gpu(args):
         if dist is not None:
             dist.barrier()
 
+    st_engines = [None, None]
+
     def step(precision, phi):
         """Set-up and compute of the whole problem: one GPU computes it all;
         with N ranks each computes its shard of the target leaves and the
         shards' potentials are gathered (the job's one exchange)."""
         plan = B.Plan(dt, ds, dq, precision=precision, stream=stream, **kw)
+        if precision == B.FP32_BULK:
+            st_engines[:] = [plan.pass_engine_used(0), plan.pass_engine_used(1)]
         if dist is None:
             plan.compute(phi, stream=stream)
         else:
@@ -614,6 +618,8 @@ def run_gpu(args):
                      "mufu_ceiling_frac": ceilings["mufu_frac"],
                      "ceilings": ceilings},
         "passes_roofline": passes,
+        "pass_engines": {"upward": "tensor" if st_engines[0] == 1 else "simt",
+                         "downward": "tensor" if st_engines[1] == 1 else "simt"},
         "fp64_plain": fp64,
         "speedup_vs_fp64": value / fp64["value"] if fp64 else None,
         "e2e": e2e, "gpu_launches": launches, "clocks": csum, "cpu_baseline": cpu,

@@ -76,6 +76,12 @@ enum bldtt_precision {
  * particles and by PP otherwise (no PC or CP). */
 enum bldtt_variant { BLDTT_VARIANT_FULL = 0, BLDTT_VARIANT_CC_PP_ONLY = 1 };
 
+/* Engines of the FP32_BULK leaf contractions (Eq. (9) of the upward pass and
+ * Eq. (21) of the downward pass): SIMT FP32 arithmetic, or the tensor cores
+ * (tcgen05 MMA on TF32 operands split in two parts, accumulators in tensor
+ * memory), see bldtt_set_pass_engine. */
+enum bldtt_pass_engine { BLDTT_PASS_SIMT = 0, BLDTT_PASS_TENSOR = 1 };
+
 /* Interaction types (Sec. 2.4), used to index the list arrays below. */
 enum bldtt_interaction { BLDTT_PP = 0, BLDTT_PC = 1, BLDTT_CP = 2, BLDTT_CC = 3 };
 
@@ -385,6 +391,30 @@ int bldtt_compute_graph(bldtt_plan* plan, double* phi, void* cuda_stream);
  * ETIMEOUT.
  */
 int bldtt_autotune(bldtt_plan* plan, double* phi, void* cuda_stream, int* chosen);
+
+/*
+ * bldtt_set_pass_engine - the engines of the plan's FP32_BULK leaf
+ * contractions for the following computes: `upward` for Eq. (9) (leaf proxy
+ * charges, Sec. 2.5), `downward` for Eq. (21) (leaf proxy potentials to the
+ * particles, Sec. 2.7), each BLDTT_PASS_SIMT or BLDTT_PASS_TENSOR.  The
+ * tensor engine runs each as one dense product on the tensor cores: upward,
+ * the P^2 x m Khatri-Rao matrix of (L_k2 q)(L_k3) times the m x P matrix of
+ * L_k1 per leaf of m particles, in chunks of 32 particles folded by TwoSum;
+ * downward, the 128 x P matrix of L_k1 of 128 particles times the P x P^2
+ * proxy potentials, then the k2, k3 sums per particle in FP32 (the k2 sum
+ * compensated).  Operands are TF32 pairs (three products per term, relative
+ * error about 2^-22 per product, FP32 accumulation).  Grids of 2..11 points
+ * (P^2 <= 121); other grids, and FP64 plans, keep the SIMT kernels.  A new
+ * plan starts with the upward pass on SIMT and the downward pass on the tensor
+ * cores, the faster engine of each measured on a GB300 (1E6 and 1E7 uniform
+ * points, n = 8).  A captured graph of the plan is dropped.  Errors: EINVAL.
+ */
+int bldtt_set_pass_engine(bldtt_plan* plan, int upward, int downward);
+
+/* The engine the plan's upward (which = 0) or downward (which = 1) leaf
+ * contraction runs on: BLDTT_PASS_TENSOR only when chosen and applicable,
+ * else BLDTT_PASS_SIMT; -1 for a NULL plan or another `which`. */
+int bldtt_pass_engine_used(const bldtt_plan* plan, int which);
 
 /*
  * bldtt_autotune_table - the table the last bldtt_autotune searched: for each

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "libbldtt.so")
 COULOMB, YUKAWA, OSCILLATORY, REG_COULOMB, TEST_POLY = 0, 1, 2, 3, 99
 VARIANT_FULL, VARIANT_CC_PP_ONLY = 0, 1
 FP64, FP32_BULK = 0, 1
+PASS_SIMT, PASS_TENSOR = 0, 1
 PP, PC, CP, CC = 0, 1, 2, 3
 
 EXPORTED = (
@@ -30,7 +31,8 @@ EXPORTED = (
     "bldtt_bounding_box_noalloc", "bldtt_selector_param_count", "bldtt_setup_learned",
     "bldtt_list_classes", "bldtt_mlp_forward", "bldtt_mlp_gradients", "bldtt_mlp_adam",
     "bldtt_pair_features", "bldtt_pair_errors", "bldtt_wait_probe", "bldtt_compute_shard",
-    "bldtt_partition_leaves", "bldtt_autotune_table",
+    "bldtt_partition_leaves", "bldtt_autotune_table", "bldtt_set_pass_engine",
+    "bldtt_pass_engine_used",
 )
 
 
@@ -130,6 +132,8 @@ def load_library(path: str = LIB_PATH):
         "bldtt_wait_probe": (i32, [i64, vp]),
         "bldtt_compute_shard": (i32, [vp, i32, i32, vp, vp]),
         "bldtt_partition_leaves": (i32, [P_dbl, ctypes.c_int32, ctypes.c_int32, P_i32]),
+        "bldtt_set_pass_engine": (i32, [vp, i32, i32]),
+        "bldtt_pass_engine_used": (i32, [vp, i32]),
         "bldtt_autotune_table": (i32, [vp, i32, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_float)]),
@@ -269,6 +273,15 @@ class Plan:
         _check(load_library().bldtt_autotune(self._handle(), _dptr(phi, self.M), _stream_ptr(stream),
                                              ctypes.byref(chosen)))
         return chosen.value
+
+    def set_pass_engine(self, upward: int, downward: int):
+        """Leaf contractions of the upward and downward passes on SIMT
+        (PASS_SIMT) or on the tensor cores (PASS_TENSOR)."""
+        _check(load_library().bldtt_set_pass_engine(self._handle(), int(upward), int(downward)))
+
+    def pass_engine_used(self, which: int) -> int:
+        """Engine of the upward (0) or downward (1) leaf contraction."""
+        return int(load_library().bldtt_pass_engine_used(self._handle(), int(which)))
 
     def autotune_table(self):
         """The last autotune's searched table: (launch, kernel, layout, ms) rows."""

@@ -21,7 +21,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libbldtt.so")
 
 SOURCES = ["prims.cu", "tree.cu", "dtt.cu", "passes.cu", "interact.cu", "direct.cu", "capi.cu",
-           "noalloc.cu", "learned.cu", "waitprobe.cu", "shard.cu"]
+           "noalloc.cu", "learned.cu", "waitprobe.cu", "shard.cu", "passes_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
                  "--expt-relaxed-constexpr", f"-I{INCLUDE}"]

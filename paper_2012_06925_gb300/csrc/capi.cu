@@ -13,6 +13,7 @@
 namespace bldtt {
 const char* last_error();
 int configure_pass_kernels();
+int configure_tc_kernels();
 }  // namespace bldtt
 
 using namespace bldtt;
@@ -170,6 +171,7 @@ int setup_impl(bldtt_plan* p, const double* targets, const double* sources, cons
   cudaStream_t s = p->stream;
   BL_CUDA(cudaGetDevice(&p->device));
   BL_TRY(configure_pass_kernels());
+  BL_TRY(configure_tc_kernels());
   for (auto& e : p->ev) BL_CUDA(cudaEventCreate(&e));
   {
     const int P = p->nprob;
@@ -695,6 +697,30 @@ int bldtt_autotune(bldtt_plan* p, double* phi, void* cuda_stream, int* chosen) {
   if (chosen) *chosen = p->segments.empty() ? 0 : p->segments[0].layout;
   p->tuned = true;
   return BLDTT_OK;
+}
+
+int bldtt_set_pass_engine(bldtt_plan* p, int upward, int downward) {
+  auto valid = [](int e) { return e == BLDTT_PASS_SIMT || e == BLDTT_PASS_TENSOR; };
+  if (!p || !valid(upward) || !valid(downward)) {
+    set_error("set_pass_engine: plan must be non-NULL and each engine BLDTT_PASS_SIMT or "
+              "BLDTT_PASS_TENSOR");
+    return BLDTT_EINVAL;
+  }
+  p->up_engine = upward;
+  p->down_engine = downward;
+  if (p->graph_exec) {                    // a captured graph used the other kernels
+    cudaGraphExecDestroy(p->graph_exec);
+    p->graph_exec = nullptr;
+  }
+  return BLDTT_OK;
+}
+
+int bldtt_pass_engine_used(const bldtt_plan* p, int which) {
+  if (!p || (which != 0 && which != 1)) return -1;
+  const int e = which == 0 ? p->up_engine : p->down_engine;
+  return (p->precision == BLDTT_FP32_BULK && e == BLDTT_PASS_TENSOR && leaf_tc_supported(p->P))
+             ? BLDTT_PASS_TENSOR
+             : BLDTT_PASS_SIMT;
 }
 
 int bldtt_autotune_table(const bldtt_plan* p, int capacity, int* rows, int* launch, int* kernel,

@@ -313,6 +313,11 @@ struct bldtt_plan {
   float4* sh_item_box = nullptr;
   int32_t sh_nitems = 0;
   std::vector<Segment> sh_segments;
+  // Engines of the FP32_BULK leaf contractions, Eq. (9) (upward) and Eq. (21)
+  // (downward): BLDTT_PASS_SIMT or BLDTT_PASS_TENSOR (tcgen05).  Defaults:
+  // the faster of the two measured at 1E6 and 1E7 points, n = 8.
+  int up_engine = BLDTT_PASS_SIMT;
+  int down_engine = BLDTT_PASS_TENSOR;
   // Leaves (leaf order) the downward leaf pass writes: [down_lo, down_hi);
   // down_hi < 0 means all leaves.
   int32_t down_lo = 0, down_hi = -1;
@@ -387,6 +392,13 @@ int layouts_available(int kernel, int* out);
 int interaction_grids(bldtt_plan* p);                 // launch shape of every segment
 int run_segment(bldtt_plan* p, int seg, cudaStream_t s);
 int run_interactions(bldtt_plan* p, cudaStream_t s);
+
+// ---- tensor-core leaf passes (passes_tc.cu) ----
+bool leaf_tc_supported(int P);
+int configure_tc_kernels();
+int up_leaf_tc(bldtt_plan* p, cudaStream_t s);
+int down_leaf_tc(bldtt_plan* p, const int32_t* leaf_ids, int32_t nleaves, double* phi_user,
+                 cudaStream_t s);
 
 // ---- compute phase (capi.cu) ----
 // Upward pass, pool, interactions of the plan's current work items, downward
