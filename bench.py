@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparator timing")
+    ap.add_argument("--pass-engine", default="default", choices=["default", "simt", "tensor"],
+                    help="engine of the FP32 leaf contractions (default: the library's per-pass "
+                         "choice, SIMT upward and tensor cores downward)")
     return ap.parse_args()
 
 
@@ -413,6 +416,9 @@ def run_gpu(args):
         shards' potentials are gathered (the job's one exchange)."""
         plan = B.Plan(dt, ds, dq, precision=precision, stream=stream, **kw)
         if precision == B.FP32_BULK:
+            if args.pass_engine != "default":
+                e = B.PASS_TENSOR if args.pass_engine == "tensor" else B.PASS_SIMT
+                plan.set_pass_engine(e, e)
             st_engines[:] = [plan.pass_engine_used(0), plan.pass_engine_used(1)]
         if dist is None:
             plan.compute(phi, stream=stream)
