@@ -209,10 +209,12 @@ int scan_exclusive_dev(const int32_t* in, int32_t* out, int64_t n, int32_t* tota
 }
 
 // ---------------------------------------------------------------------------
-// Stable LSD radix sort, 4-bit digits
+// Stable LSD radix sort, 8-bit digits (a set-up sorts keys of 13 to 28 bits:
+// two to four passes of four launches each)
 // ---------------------------------------------------------------------------
-constexpr int kRadixBits = 4;
+constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
+static_assert(kRadix <= kScanThreads, "one thread per digit in the histogram and scatter kernels");
 
 __global__ void k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
                              int32_t* __restrict__ hist, int64_t tiles) {
