@@ -406,8 +406,10 @@ int bldtt_autotune(bldtt_plan* plan, double* phi, void* cuda_stream, int* chosen
  * error about 2^-22 per product, FP32 accumulation).  Grids of 2..11 points
  * (P^2 <= 121); other grids, and FP64 plans, keep the SIMT kernels.  A new
  * plan starts with the upward pass on SIMT and the downward pass on the tensor
- * cores, the faster engine of each measured on a GB300 (1E6 and 1E7 uniform
- * points, n = 8).  A captured graph of the plan is dropped.  Errors: EINVAL.
+ * cores when its target leaves hold 512 particles or more on average (else
+ * SIMT): the faster engine of each as measured on a GB300 (uniform points at
+ * 1E6 and 1E7 with leaves of 2000, and the batched workload's leaves of 500).
+ * A captured graph of the plan is dropped.  Errors: EINVAL.
  */
 int bldtt_set_pass_engine(bldtt_plan* plan, int upward, int downward);
 

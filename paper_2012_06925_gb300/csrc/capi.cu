@@ -219,6 +219,13 @@ int setup_impl(bldtt_plan* p, const double* targets, const double* sources, cons
   BL_TRY(dalloc_n(&p->q_tree, p->N, s));
   BL_TRY(permute_charges(p, charges, s));
   BL_CUDA(cudaEventRecord(p->ev[1], s));
+  // Default engine of the downward leaf contraction: the tensor cores when the
+  // target leaves hold 512 particles or more on average (four 128-particle MMA
+  // tiles per leaf), else SIMT.  Measured on a GB300: 0.15 against 0.18 ms at
+  // 1E6 (leaves of ~1950), 1.04 against 1.11 ms on the unequal-set workload,
+  // but 2.76 against 1.80 ms on the batched workload (leaves of ~250).
+  p->down_engine = (p->tt.nleaves > 0 && p->M >= 512 * (int64_t)p->tt.nleaves) ? BLDTT_PASS_TENSOR
+                                                                              : BLDTT_PASS_SIMT;
   BL_TRY(setup_degrees(p, s));
   BL_TRY(build_lists(p, s));
   BL_TRY(build_work_items(p, s));

@@ -314,8 +314,8 @@ struct bldtt_plan {
   int32_t sh_nitems = 0;
   std::vector<Segment> sh_segments;
   // Engines of the FP32_BULK leaf contractions, Eq. (9) (upward) and Eq. (21)
-  // (downward): BLDTT_PASS_SIMT or BLDTT_PASS_TENSOR (tcgen05).  Defaults:
-  // the faster of the two measured at 1E6 and 1E7 points, n = 8.
+  // (downward): BLDTT_PASS_SIMT or BLDTT_PASS_TENSOR (tcgen05).  The set-up
+  // picks the downward default by the target leaves' mean size.
   int up_engine = BLDTT_PASS_SIMT;
   int down_engine = BLDTT_PASS_TENSOR;
   // Leaves (leaf order) the downward leaf pass writes: [down_lo, down_hi);

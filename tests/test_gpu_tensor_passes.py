@@ -85,9 +85,12 @@ def test_tensor_engine_falls_back_beyond_eleven_points_and_shards_agree():
     with B.Plan(dt, dt, dq, n=11, theta=0.7, N0=2000, M0=2000, precision=B.FP32_BULK) as plan:
         plan.set_pass_engine(B.PASS_TENSOR, B.PASS_TENSOR)
         assert plan.pass_engine_used(0) == plan.pass_engine_used(1) == B.PASS_SIMT   # 12 points
-    with B.Plan(dt, dt, dq, n=6, theta=0.7, N0=300, M0=300, precision=B.FP32_BULK) as plan:
-        # the default: upward on SIMT, downward on the tensor cores
+    # the default: upward on SIMT; downward on the tensor cores for target
+    # leaves of 512 particles or more on average, else SIMT
+    with B.Plan(dt, dt, dq, n=6, theta=0.7, N0=2000, M0=2000, precision=B.FP32_BULK) as plan:
         assert (plan.pass_engine_used(0), plan.pass_engine_used(1)) == (B.PASS_SIMT, B.PASS_TENSOR)
+    with B.Plan(dt, dt, dq, n=6, theta=0.7, N0=300, M0=300, precision=B.FP32_BULK) as plan:
+        assert (plan.pass_engine_used(0), plan.pass_engine_used(1)) == (B.PASS_SIMT, B.PASS_SIMT)
         plan.set_pass_engine(B.PASS_TENSOR, B.PASS_TENSOR)
         full = plan.compute()
         again = plan.compute()
