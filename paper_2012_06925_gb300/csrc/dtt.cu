@@ -26,19 +26,16 @@ static TreeView view(const Tree& T) {
 // Action of a frontier pair: an entry of list class 0..kMaxClasses-1, or a split.
 constexpr int8_t kActSplitT = 100, kActSplitS = 101;
 
-// choice (may be NULL): the learned selector's decision per pair; NULL or
-// kChoiceFallback applies Alg. 2's MAC at the highest degree (index imax).
-__global__ void k_dtt_classify(const int2* __restrict__ pairs, int32_t F, TreeView tt, TreeView st,
-                               int64_t np, int imax, double theta, int variant,
-                               const int16_t* __restrict__ choice, int32_t* __restrict__ nkids,
-                               int32_t* __restrict__ isentry, int8_t* __restrict__ action) {
-  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= F) return;
-  int t = pairs[i].x, s = pairs[i].y;
-  int64_t cnt_t = tt.end[t] - tt.begin[t], cnt_s = st.end[s] - st.begin[s];
-  const int16_t ch = choice ? choice[i] : kChoiceFallback;
+// Alg. 2's decision for the pair (t, s): an entry of list class 0..kMaxClasses-1
+// or a split (kActSplitT / kActSplitS, with the number of child pairs in
+// *kids).  ch is the learned selector's decision for the pair, or
+// kChoiceFallback for the MAC at the highest degree (index imax).
+__device__ __forceinline__ int8_t classify_pair(int t, int s, const TreeView& tt, const TreeView& st,
+                                                int64_t np, int imax, double theta, int variant,
+                                                int16_t ch, int32_t* kids) {
+  const int64_t cnt_t = tt.end[t] - tt.begin[t], cnt_s = st.end[s] - st.begin[s];
   int8_t a = -1;
-  int32_t kids = 0;
+  *kids = 0;
   if (ch >= 0) {
     a = (int8_t)ch;
   } else if (ch == kChoiceFallback) {
@@ -60,9 +57,23 @@ __global__ void k_dtt_classify(const int2* __restrict__ pairs, int32_t F, TreeVi
     else if (leaf_s) a = kActSplitT;
     else if (leaf_t) a = kActSplitS;
     else a = cnt_s < cnt_t ? kActSplitT : kActSplitS;
-    if (a == kActSplitT) kids = tt.nchild[t];
-    if (a == kActSplitS) kids = st.nchild[s];
+    if (a == kActSplitT) *kids = tt.nchild[t];
+    if (a == kActSplitS) *kids = st.nchild[s];
   }
+  return a;
+}
+
+// choice (may be NULL): the learned selector's decision per pair; NULL or
+// kChoiceFallback applies Alg. 2's MAC at the highest degree (index imax).
+__global__ void k_dtt_classify(const int2* __restrict__ pairs, int32_t F, TreeView tt, TreeView st,
+                               int64_t np, int imax, double theta, int variant,
+                               const int16_t* __restrict__ choice, int32_t* __restrict__ nkids,
+                               int32_t* __restrict__ isentry, int8_t* __restrict__ action) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= F) return;
+  int32_t kids = 0;
+  const int8_t a = classify_pair(pairs[i].x, pairs[i].y, tt, st, np, imax, theta, variant,
+                                 choice ? choice[i] : kChoiceFallback, &kids);
   action[i] = a;
   nkids[i] = kids;
   isentry[i] = a < kActSplitT ? 1 : 0;
@@ -88,6 +99,204 @@ __global__ void k_dtt_emit(const int2* __restrict__ pairs, int32_t F, const int8
   } else {
     int32_t fc = st.first_child[s], k = st.nchild[s];
     for (int j = 0; j < k; ++j) next[koff[i] + j] = make_int2(t, fc + j);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The whole fixed-rule traversal in one cooperative launch
+// ---------------------------------------------------------------------------
+// Every level of the frontier loop above in one kernel, with no host round
+// trip between levels: each block takes a contiguous range of the frontier,
+// classifies its pairs and scans their child and entry counts; after a grid
+// barrier every block reads all blocks' totals (so every block knows its
+// offsets and the level's totals), checks the buffer capacities (the same
+// decision in every block), emits its entries and child pairs at those
+// offsets, and a second barrier ends the level.  Ranges and offsets follow the
+// frontier order, so entries and next frontiers are exactly those of the
+// level-by-level loop.  Data written by other blocks is read with L2 loads
+// (ld.global.cg).  Barriers wait at most kDttWaitNs, then report and return.
+constexpr int kDttThreads = 256;
+constexpr uint64_t kDttWaitNs = 5ull * 1000ull * 1000ull * 1000ull;
+
+struct DttGrid {
+  unsigned int count;   // blocks arrived at the current barrier
+  unsigned int gen;     // barrier generation
+  int32_t F0;           // size of the first frontier (set by the host)
+  int32_t status;       // 0 done, 1 a buffer would overflow, 2 a barrier gave up
+  long long E;          // entries written
+  int32_t levels;
+};
+
+__device__ __forceinline__ uint64_t dtt_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded grid barrier of the cooperative launch (all blocks co-resident).
+__device__ bool dtt_grid_sync(DttGrid* g, unsigned nblocks) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* vgen = &g->gen;
+    const unsigned gen0 = *vgen;
+    __threadfence();
+    if (atomicAdd(&g->count, 1u) == nblocks - 1u) {
+      atomicExch(&g->count, 0u);
+      __threadfence();
+      atomicAdd(&g->gen, 1u);
+    } else {
+      const uint64_t t0 = dtt_ns();
+      while (*vgen == gen0) {
+        if (dtt_ns() - t0 > kDttWaitNs) {
+          ok = 0;
+          atomicExch(&g->status, 2);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Block-wide exclusive scan of two counts; totals in *tk, *te.
+__device__ __forceinline__ void block_scan2(int32_t k, int32_t e, int32_t* xk, int32_t* xe, int32_t* tk,
+                                            int32_t* te) {
+  __shared__ int32_t wk[kDttThreads / 32], we[kDttThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t ik = k, ie = e;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t a = __shfl_up_sync(0xffffffffu, ik, o), c = __shfl_up_sync(0xffffffffu, ie, o);
+    if (lane >= o) {
+      ik += a;
+      ie += c;
+    }
+  }
+  if (lane == 31) {
+    wk[warp] = ik;
+    we[warp] = ie;
+  }
+  __syncthreads();
+  int32_t pk = 0, pe = 0, sk = 0, se = 0;
+  for (int w = 0; w < kDttThreads / 32; ++w) {
+    if (w < warp) {
+      pk += wk[w];
+      pe += we[w];
+    }
+    sk += wk[w];
+    se += we[w];
+  }
+  *xk = pk + ik - k;
+  *xe = pe + ie - e;
+  *tk = sk;
+  *te = se;
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kDttThreads) k_dtt_all(
+    TreeView tt, TreeView st, int64_t np, int imax, double theta, int variant, int32_t nct,
+    int2* __restrict__ buf0, int2* __restrict__ buf1, int32_t fcap, int32_t* __restrict__ ent_t,
+    int32_t* __restrict__ ent_s, uint32_t* __restrict__ ent_key, int64_t ecap,
+    int32_t* __restrict__ koff, int32_t* __restrict__ eoff, int8_t* __restrict__ action,
+    int2* __restrict__ part, DttGrid* __restrict__ g) {
+  __shared__ int32_t red[4][kDttThreads / 32];
+  const unsigned G = gridDim.x, b = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int2* front = buf0;
+  int2* next = buf1;
+  int32_t F = g->F0;
+  int64_t E = 0;
+  int level = 0;
+  for (; F > 0; ++level) {
+    const int32_t lo = (int32_t)((int64_t)F * b / G), hi = (int32_t)((int64_t)F * (b + 1) / G);
+    int32_t run_k = 0, run_e = 0;
+    for (int32_t base = lo; base < hi; base += kDttThreads) {   // block-uniform trip count
+      const int32_t i = base + threadIdx.x;
+      int32_t kids = 0, ent = 0;
+      if (i < hi) {
+        const int2 pr = __ldcg(front + i);
+        const int8_t a = classify_pair(pr.x, pr.y, tt, st, np, imax, theta, variant, kChoiceFallback, &kids);
+        action[i] = a;
+        ent = a < kActSplitT ? 1 : 0;
+      }
+      int32_t xk, xe, tk, te;
+      block_scan2(kids, ent, &xk, &xe, &tk, &te);
+      if (i < hi) {
+        koff[i] = run_k + xk;
+        eoff[i] = run_e + xe;
+      }
+      run_k += tk;
+      run_e += te;
+    }
+    if (threadIdx.x == 0) part[b] = make_int2(run_k, run_e);
+    if (!dtt_grid_sync(g, G)) return;
+    // this block's offsets and the level's totals, from every block's counts
+    int32_t pk = 0, pe = 0, sk = 0, se = 0;
+    for (unsigned j = threadIdx.x; j < G; j += kDttThreads) {
+      const int2 v = __ldcg(part + j);
+      if (j < b) {
+        pk += v.x;
+        pe += v.y;
+      }
+      sk += v.x;
+      se += v.y;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      pk += __shfl_xor_sync(0xffffffffu, pk, o);
+      pe += __shfl_xor_sync(0xffffffffu, pe, o);
+      sk += __shfl_xor_sync(0xffffffffu, sk, o);
+      se += __shfl_xor_sync(0xffffffffu, se, o);
+    }
+    if (lane == 0) {
+      red[0][warp] = pk;
+      red[1][warp] = pe;
+      red[2][warp] = sk;
+      red[3][warp] = se;
+    }
+    __syncthreads();
+    int32_t off_k = 0, off_e = 0, K = 0, En = 0;
+    for (int w = 0; w < kDttThreads / 32; ++w) {
+      off_k += red[0][w];
+      off_e += red[1][w];
+      K += red[2][w];
+      En += red[3][w];
+    }
+    __syncthreads();
+    if (K > fcap || E + En > ecap) {          // the same decision in every block
+      if (b == 0 && threadIdx.x == 0) atomicExch(&g->status, 1);
+      return;
+    }
+    for (int32_t i = lo + threadIdx.x; i < hi; i += kDttThreads) {
+      const int2 pr = __ldcg(front + i);
+      const int8_t a = action[i];
+      if (a < kActSplitT) {
+        const int64_t e = E + off_e + eoff[i];
+        ent_t[e] = pr.x;
+        ent_s[e] = pr.y;
+        ent_key[e] = (uint32_t)a * (uint32_t)nct + (uint32_t)pr.x;
+      } else if (a == kActSplitT) {
+        const int32_t fc = tt.first_child[pr.x], k = tt.nchild[pr.x], o = off_k + koff[i];
+        for (int j = 0; j < k; ++j) next[o + j] = make_int2(fc + j, pr.y);
+      } else {
+        const int32_t fc = st.first_child[pr.y], k = st.nchild[pr.y], o = off_k + koff[i];
+        for (int j = 0; j < k; ++j) next[o + j] = make_int2(pr.x, fc + j);
+      }
+    }
+    if (!dtt_grid_sync(g, G)) return;
+    int2* tmp = front;
+    front = next;
+    next = tmp;
+    E += En;
+    F = K;
+  }
+  if (b == 0 && threadIdx.x == 0) {
+    g->E = E;
+    g->levels = level;
   }
 }
 
@@ -140,6 +349,81 @@ __global__ void k_class_bounds(const int32_t* __restrict__ list_ptr, int32_t nct
   for (int k = threadIdx.x; k <= nclass; k += blockDim.x) o[k] = list_ptr[(int64_t)k * nct];
 }
 
+// The fixed-rule traversal from the P root pairs in `roots` by one cooperative
+// launch (k_dtt_all).  On success *E receives the entry count, the three entry
+// arrays are allocated here and *done is set; when a buffer would overflow the
+// capacity is doubled and the launch repeated (twice at most), after which
+// *done stays false and the caller runs the level-by-level loop.
+static int traverse_cooperative(bldtt_plan* p, const TreeView& tt, const TreeView& st, const int2* roots,
+                                int32_t P, int32_t** ent_t, int32_t** ent_s, uint32_t** ent_key,
+                                int64_t* E, bool* done, cudaStream_t s) {
+  *done = false;
+  int dev = 0, sms = 0, coop = 0, per_sm = 0;
+  BL_CUDA(cudaGetDevice(&dev));
+  BL_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) return BLDTT_OK;
+  BL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dtt_all, kDttThreads, 0));
+  if (per_sm < 1) return BLDTT_OK;
+  const unsigned G = (unsigned)(sms * (per_sm < 2 ? per_sm : 2));
+  const int32_t imax = p->deg.n - 1;
+  int64_t cap = 64 * ((int64_t)p->tt.nclusters + (int64_t)p->st.nclusters);
+  if (cap < 32768) cap = 32768;
+  for (int attempt = 0; attempt < 3 && !*done; ++attempt, cap *= 2) {
+    if (cap >= (int64_t)INT32_MAX) break;
+    int2 *b0 = nullptr, *b1 = nullptr, *part = nullptr;
+    int32_t *koff = nullptr, *eoff = nullptr, *et = nullptr, *es = nullptr;
+    uint32_t* ek = nullptr;
+    int8_t* act = nullptr;
+    DttGrid* g = nullptr;
+    BL_TRY(dalloc_n(&b0, cap, s));
+    BL_TRY(dalloc_n(&b1, cap, s));
+    BL_TRY(dalloc_n(&koff, cap, s));
+    BL_TRY(dalloc_n(&eoff, cap, s));
+    BL_TRY(dalloc_n(&act, cap, s));
+    BL_TRY(dalloc_n(&et, cap, s));
+    BL_TRY(dalloc_n(&es, cap, s));
+    BL_TRY(dalloc_n(&ek, cap, s));
+    BL_TRY(dalloc_n(&part, G, s));
+    BL_TRY(dalloc_n(&g, 1, s));
+    BL_CUDA(cudaMemsetAsync(g, 0, sizeof(DttGrid), s));
+    BL_CUDA(cudaMemcpyAsync(b0, roots, (size_t)P * sizeof(int2), cudaMemcpyDeviceToDevice, s));
+    BL_CUDA(cudaMemcpyAsync(&g->F0, &P, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    int64_t np = p->deg.np[imax];
+    double theta = p->theta;
+    int variant = p->variant;
+    int32_t nct = p->tt.nclusters;
+    int32_t fcap = (int32_t)cap;
+    int64_t ecap = cap;
+    TreeView a = tt, c = st;
+    int imx = imax;
+    void* args[] = {&a, &c, &np, &imx, &theta, &variant, &nct, &b0, &b1, &fcap, &et, &es, &ek, &ecap,
+                    &koff, &eoff, &act, &part, &g};
+    BL_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_dtt_all), dim3(G), dim3(kDttThreads),
+                                        args, 0, s));
+    BL_LAUNCHED(p->setup_counter.launches);
+    DttGrid h{};
+    BL_TRY(read_device(g, &h, sizeof(h), s));
+    dfree(b0, s); dfree(b1, s); dfree(koff, s); dfree(eoff, s); dfree(act, s); dfree(part, s); dfree(g, s);
+    if (h.status == 2) {
+      dfree(et, s); dfree(es, s); dfree(ek, s);
+      set_error("a grid barrier of the cooperative traversal gave up after %llu ns",
+                (unsigned long long)kDttWaitNs);
+      return BLDTT_ETIMEOUT;
+    }
+    if (h.status == 0) {
+      *ent_t = et;
+      *ent_s = es;
+      *ent_key = ek;
+      *E = h.E;
+      *done = true;
+    } else {
+      dfree(et, s); dfree(es, s); dfree(ek, s);
+    }
+  }
+  return BLDTT_OK;
+}
+
 int build_lists(bldtt_plan* p, cudaStream_t s) {
   bldtt::Counters& cnt = p->setup_counter;
   const TreeView tt = view(p->tt), st = view(p->st);
@@ -169,6 +453,22 @@ int build_lists(bldtt_plan* p, cudaStream_t s) {
   int32_t F = P;
   int64_t E = 0;
   const int imax = p->deg.n - 1;
+  // The fixed rule runs as one cooperative launch; the learned selector (a
+  // network inference per frontier level) and an overflowing estimate of the
+  // buffers take the level-by-level loop below.
+  if (!p->learned) {
+    bool done = false;
+    int32_t *ct = nullptr, *cs = nullptr;
+    uint32_t* ck = nullptr;
+    BL_TRY(traverse_cooperative(p, tt, st, front, P, &ct, &cs, &ck, &E, &done, s));
+    if (done) {
+      dfree(ent_t, s); dfree(ent_s, s); dfree(ent_key, s);
+      ent_t = ct;
+      ent_s = cs;
+      ent_key = ck;
+      F = 0;                                   // the loop below has nothing left to do
+    }
+  }
   // per-level scratch, grown as the front grows; the two totals of a level
   // come back to the host in one read
   size_t cap_k = 0, cap_i = 0, cap_o = 0, cap_e = 0, cap_a = 0, cap_c = 0;
