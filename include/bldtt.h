@@ -402,8 +402,8 @@ int bldtt_autotune(bldtt_plan* plan, double* phi, void* cuda_stream, int* chosen
  * L_k1 per leaf of m particles, in chunks of 32 particles folded by TwoSum;
  * downward, the 128 x P matrix of L_k1 of 128 particles times the P x P^2
  * proxy potentials, then the k2, k3 sums per particle in FP32 (the k2 sum
- * compensated).  Operands are TF32 pairs (three products per term, relative
- * error about 2^-22 per product, FP32 accumulation).  Grids of 2..11 points
+ * compensated).  Operands are TF32 pairs a_h + a_l (four products per term,
+ * the pair holding each operand to about 2^-22, FP32 accumulation).  Grids of 2..11 points
  * (P^2 <= 121); other grids, and FP64 plans, keep the SIMT kernels.  A new
  * plan starts with the upward pass on SIMT and the downward pass on the tensor
  * cores when its target leaves hold 512 particles or more on average (else

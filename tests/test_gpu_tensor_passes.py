@@ -3,9 +3,9 @@
 particles, Sec. 2.7), against the oracle and against the SIMT kernels.
 
 Tolerances: the proxy charges of the FP32 plan against the FP64 plan's,
-relative l2 over all clusters <= 2e-6: each product carries a relative error
-of about 2^-22 (the dropped low x low term of the TF32 pairs, and the TF32
-rounding of the low parts), each 32-particle chunk is summed in FP32 (about
+relative l2 over all clusters <= 2e-6: each operand is held by its TF32 pair
+to about 2^-22 (the TF32 rounding of the low part; all four products of the
+pairs are taken), each 32-particle chunk is summed in FP32 (about
 u sqrt(32) = 3.4e-7 of the chunk's root-sum-square), and the charges' mixed
 signs make |qhat| smaller than the sum of |terms| by a further factor of a
 few.  Potentials: the metric's 1e-6 relative l2 and 1e-5 max-norm against
