@@ -737,7 +737,8 @@ __device__ __forceinline__ void eval_chunk_f64(const void* buf, int count, const
 // __grid_constant__ parameter instead removes those writes but ran slower,
 // 32.30 against 32.09 ms at 1E6 and 154-179 against 90 ms on the unequal-set
 // Yukawa workload (1E7 targets, 5E6 Plummer sources), also when only the
-// producer kept a private copy.
+// producer kept a private copy.  A pointer to per-segment blocks in device
+// memory ran slower too: 32.3 against 32.1 ms and 143 against 90 ms.
 template <bool F32, int KERN, int NCW, int K, int MINB, int STAGES, bool SKIP>
 __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_interact(InteractView v) {
   static_assert(NCW * 32 * K == kTile, "a CTA covers exactly one work-item tile");
