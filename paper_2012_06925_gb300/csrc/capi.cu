@@ -121,12 +121,22 @@ float fp32_parameter(int kernel, double kappa) {
   return (float)kappa;
 }
 
-// Target and source trees of unequal sets are independent: the source tree is
-// built on a second stream by a helper thread while this thread builds the
-// target tree (each build synchronises with the host once per level, so one
-// thread would serialise the two).  The stream of the call then waits for both.
+// Target and source trees of unequal sets are independent.  With the
+// cooperative build each tree is one launch and the two run one after the
+// other on the call's stream.  Level by level, the source tree is built on a
+// second stream by a helper thread while this thread builds the target tree
+// (each such build synchronises with the host once per level, so one thread
+// would serialise the two); the stream of the call then waits for both.
 static int build_two_trees(bldtt_plan* p, const double* targets, const double* sources,
-                           cudaStream_t s) {
+                           const double* charges, cudaStream_t s) {
+  if (tree_build_cooperative()) {
+    BL_TRY(build_tree_checked(p->tt, targets, (int32_t)p->M, p->t_off, p->M0, p->n, nullptr, 0, s,
+                              p->setup_counter));
+    BL_TRY(morton_order_leaves(p->tt, p->M0, s, p->setup_counter));
+    BL_TRY(build_tree_checked(p->st, sources, (int32_t)p->N, p->s_off, p->N0, p->n, charges, p->N, s,
+                              p->setup_counter));
+    return morton_order_leaves(p->st, p->N0, s, p->setup_counter);
+  }
   cudaStream_t s2 = nullptr;
   cudaEvent_t go = nullptr, done = nullptr;
   BL_CUDA(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
@@ -144,11 +154,12 @@ static int build_two_trees(bldtt_plan* p, const double* targets, const double* s
       err2 = "cudaSetDevice failed in the source-tree thread";
       return;
     }
-    rc2 = build_tree(p->st, sources, (int32_t)p->N, p->s_off, p->N0, p->n, s2, c2);
+    rc2 = build_tree_checked(p->st, sources, (int32_t)p->N, p->s_off, p->N0, p->n, charges, p->N, s2, c2);
     if (rc2 == BLDTT_OK) rc2 = morton_order_leaves(p->st, p->N0, s2, c2);
     if (rc2 != BLDTT_OK) err2 = last_error();
   });
-  int rc1 = build_tree(p->tt, targets, (int32_t)p->M, p->t_off, p->M0, p->n, s, p->setup_counter);
+  int rc1 = build_tree_checked(p->tt, targets, (int32_t)p->M, p->t_off, p->M0, p->n, nullptr, 0, s,
+                               p->setup_counter);
   if (rc1 == BLDTT_OK) rc1 = morton_order_leaves(p->tt, p->M0, s, p->setup_counter);
   worker.join();
   p->setup_counter.launches += c2.launches;
@@ -189,32 +200,20 @@ int setup_impl(bldtt_plan* p, const double* targets, const double* sources, cons
   }
   BL_TRY(dalloc_n(&p->dev_err, 1, s));
   BL_CUDA(cudaMemsetAsync(p->dev_err, 0, sizeof(int), s));
-  int* bad = nullptr;
-  BL_TRY(dalloc_n(&bad, 1, s));
-  BL_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
   BL_CUDA(cudaEventRecord(p->ev[0], s));
-  // Reject non-finite input before any tree is built: a box of infinite
-  // extent would be split without end.
-  BL_TRY(check_finite(targets, 3 * p->M, bad, s, p->setup_counter));
-  if (sources != targets) BL_TRY(check_finite(sources, 3 * p->N, bad, s, p->setup_counter));
-  BL_TRY(check_finite(charges, p->N, bad, s, p->setup_counter));
-  int h_bad = 0;
-  BL_TRY(read_device(bad, &h_bad, sizeof(int), s));
-  dfree(bad, s);
-  if (h_bad) {
-    set_error("a target, source or charge value is not finite");
-    return BLDTT_EINVAL;
-  }
+  // Non-finite input is rejected by the tree build before any cluster splits
+  // (a box of infinite extent would be split without end).
   // Targets that are the sources, with the same leaf size and problem
   // offsets, give two identical trees (the build is deterministic): build one
   // and let the source tree alias it.
   p->shared_tree = targets == sources && p->M == p->N && p->M0 == p->N0 && p->t_off == p->s_off;
   if (p->shared_tree) {
-    BL_TRY(build_tree(p->tt, targets, (int32_t)p->M, p->t_off, p->M0, p->n, s, p->setup_counter));
+    BL_TRY(build_tree_checked(p->tt, targets, (int32_t)p->M, p->t_off, p->M0, p->n, charges, p->N, s,
+                              p->setup_counter));
     BL_TRY(morton_order_leaves(p->tt, p->M0, s, p->setup_counter));
     p->st = p->tt;
   } else {
-    BL_TRY(build_two_trees(p, targets, sources, s));
+    BL_TRY(build_two_trees(p, targets, sources, charges, s));
   }
   BL_TRY(dalloc_n(&p->q_tree, p->N, s));
   BL_TRY(permute_charges(p, charges, s));

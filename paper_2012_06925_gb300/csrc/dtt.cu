@@ -8,6 +8,7 @@
 // rest are replaced by the pairs of the split side's children (Alg. 2,
 // lines 11-17).  Compaction uses prefix sums, so the entry order, and hence
 // every later summation order, is deterministic.
+#include <cstring>
 #include <vector>
 
 #include "internal.cuh"
@@ -300,6 +301,12 @@ __global__ void __launch_bounds__(kDttThreads) k_dtt_all(
   }
 }
 
+// Root pair (r, r) of every problem r.
+__global__ void k_root_pairs(int2* __restrict__ front, int32_t P) {
+  const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < P) front[r] = make_int2(r, r);
+}
+
 __global__ void k_iota(int32_t* v, int64_t n) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) v[i] = (int32_t)i;
@@ -439,17 +446,13 @@ int build_lists(bldtt_plan* p, cudaStream_t s) {
   BL_TRY(dalloc_n(&ent_key, ecap, s));
   // One root pair per problem (Alg. 2 starts from the two roots of each problem).
   const int32_t P = p->tt.nroots;
-  {
-    std::vector<int2> roots(P);
-    for (int32_t r = 0; r < P; ++r) roots[r] = make_int2(r, r);
-    if ((size_t)P > fcap) {
-      size_t c = fcap;
-      BL_TRY(dgrow(&front, &c, (size_t)P, 0, s));
-      fcap = c;
-    }
-    BL_CUDA(cudaMemcpyAsync(front, roots.data(), P * sizeof(int2), cudaMemcpyHostToDevice, s));
-    BL_CUDA(cudaStreamSynchronize(s));   // the host vector goes out of scope
+  if ((size_t)P > fcap) {
+    size_t c = fcap;
+    BL_TRY(dgrow(&front, &c, (size_t)P, 0, s));
+    fcap = c;
   }
+  k_root_pairs<<<nblk(P, 256), 256, 0, s>>>(front, P);
+  BL_LAUNCHED(cnt.launches);
   int32_t F = P;
   int64_t E = 0;
   const int imax = p->deg.n - 1;
@@ -845,9 +848,10 @@ int build_work_items(bldtt_plan* p, cudaStream_t s) {
   BL_TRY(dalloc_n(&off, nct, s));
   BL_TRY(dalloc_n(&cost_part, nct, s));
   BL_TRY(dalloc_n(&cost_prox, (size_t)nct * kMaxDegrees, s));
-  unsigned long long* executed = nullptr;
-  BL_TRY(dalloc_n(&executed, 2, s));
-  BL_CUDA(cudaMemsetAsync(executed, 0, 2 * sizeof(unsigned long long), s));
+  unsigned long long* summary = nullptr;   // [0, 2): executed counters; [2, 6): segment starts
+  BL_TRY(dalloc_n(&summary, 6, s));
+  BL_CUDA(cudaMemsetAsync(summary, 0, 2 * sizeof(unsigned long long), s));
+  unsigned long long* executed = summary;
   dfree_ptr(p->eval_part, s);
   dfree_ptr(p->eval_prox, s);
   BL_TRY(dalloc_n(&p->eval_part, nct, s));
@@ -878,8 +882,9 @@ int build_work_items(bldtt_plan* p, cudaStream_t s) {
   int seg_bits = 0;
   while ((1 << seg_bits) < segmap.n) ++seg_bits;
   BL_TRY(radix_sort_pairs(keys, vals, ni, 25 + seg_bits, s, cnt));
-  int32_t* seg_first = nullptr;
-  BL_TRY(dalloc_n(&seg_first, 8, s));
+  // segment starts (8 int32) and the two executed-evaluation counters come
+  // back to the host in one read
+  int32_t* seg_first = reinterpret_cast<int32_t*>(summary + 2);
   BL_CUDA(cudaMemsetAsync(seg_first, 0xff, 8 * sizeof(int32_t), s));
   if (ni > 0) {
     k_segment_starts<<<nblk(ni, 256), 256, 0, s>>>(keys, ni, seg_first);
@@ -898,14 +903,15 @@ int build_work_items(bldtt_plan* p, cudaStream_t s) {
                                                                     p->deg, p->item_box);
     BL_LAUNCHED(cnt.launches);
   }
-  unsigned long long h_exec[2] = {0, 0};
-  BL_TRY(read_device(seg_first, h_first, sizeof(h_first), s));
-  BL_TRY(read_device(executed, h_exec, sizeof(h_exec), s));
+  unsigned long long h_sum[6];
+  BL_TRY(read_device(summary, h_sum, sizeof(h_sum), s));
+  const unsigned long long h_exec[2] = {h_sum[0], h_sum[1]};
+  std::memcpy(h_first, h_sum + 2, sizeof(h_first));
   p->executed_skip = (double)h_exec[0];
   p->executed_noskip = (double)h_exec[1];
   p->skip_saved_evaluations = p->executed_noskip - p->executed_skip;
   p->executed_evaluations = p->executed_noskip;
-  dfree(seg_first, s);
+  dfree(summary, s);
   p->segments.clear();
   for (int i = 0; i < segmap.n; ++i) {
     if (h_first[i] < 0) continue;                    // no items for this kernel
@@ -917,7 +923,7 @@ int build_work_items(bldtt_plan* p, cudaStream_t s) {
       }
     p->segments.push_back({segmap.kernel[i], h_first[i], end - h_first[i], 0, 0, 0});
   }
-  dfree(items, s); dfree(keys, s); dfree(vals, s); dfree(executed, s);
+  dfree(items, s); dfree(keys, s); dfree(vals, s);
   dfree(nitems, s); dfree(off, s); dfree(cost_part, s); dfree(cost_prox, s);
   return BLDTT_OK;
 }

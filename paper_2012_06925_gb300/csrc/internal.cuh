@@ -370,6 +370,13 @@ int check_finite(const double* v, int64_t n, int* bad_dev, cudaStream_t s, Count
 int build_tree(Tree& T, const double* coords_user, int32_t n, const std::vector<int32_t>& roots,
                int32_t max_leaf, int degree, cudaStream_t s, Counters& c);
 // Reorder the particles inside every leaf along a Morton curve of the leaf's box.
+// build_tree by one cooperative launch where the device has them, else level
+// by level; non-finite coordinates or charges (charges may be null) give
+// BLDTT_EINVAL before any cluster splits.
+int build_tree_checked(Tree& T, const double* coords, int32_t n, const std::vector<int32_t>& roots,
+                       int32_t max_leaf, int degree, const double* charges, int64_t ncharges,
+                       cudaStream_t s, Counters& cnt);
+bool tree_build_cooperative();
 int morton_order_leaves(Tree& T, int32_t max_leaf, cudaStream_t s, Counters& c);
 void free_tree(Tree& T, cudaStream_t s);
 

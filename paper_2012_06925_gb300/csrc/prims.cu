@@ -82,6 +82,8 @@ template int dgrow<uint8_t>(uint8_t**, size_t*, size_t, size_t, cudaStream_t);
 template int dgrow<int8_t>(int8_t**, size_t*, size_t, size_t, cudaStream_t);
 template int dgrow<int16_t>(int16_t**, size_t*, size_t, size_t, cudaStream_t);
 template int dgrow<int4>(int4**, size_t*, size_t, size_t, cudaStream_t);
+template int dgrow<long long>(long long**, size_t*, size_t, size_t, cudaStream_t);
+template int dgrow<unsigned long long>(unsigned long long**, size_t*, size_t, size_t, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Exclusive scan (reduce, scan the tile sums, apply)

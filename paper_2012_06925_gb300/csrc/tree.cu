@@ -52,22 +52,13 @@ __global__ void k_tree_roots(int32_t nroots, const int32_t* __restrict__ offsets
   problem[p] = p;
 }
 
-// Split decision of each cluster of the level (reading: leaf iff |C| <= M0 or
-// all extents zero; up to 1/2/3 dims by the count rule; eligible iff
-// L_d*L_d*2 >= L_max*L_max; longest eligible first, ties to the lower axis).
-__global__ void k_tree_decide(int32_t ls, int32_t nl, const int32_t* __restrict__ begin,
-                              const int32_t* __restrict__ end, const double* __restrict__ box,
-                              int32_t max_leaf, uint8_t* __restrict__ splitmask,
-                              double* __restrict__ mid, int32_t* __restrict__ nchunks,
-                              int32_t* __restrict__ first_child, int32_t* __restrict__ nchild,
-                              int32_t* __restrict__ nsplit) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= nl) return;
-  int c = ls + j;
-  int64_t cnt = (int64_t)end[c] - begin[c];
-  first_child[c] = -1;
-  nchild[c] = 0;
-  const double* b = box + (int64_t)c * 6;
+// Split decision of one cluster of cnt particles in box b (reading: leaf iff
+// |C| <= M0 or all extents zero; up to 1/2/3 dims by the count rule; eligible
+// iff L_d*L_d*2 >= L_max*L_max; longest eligible first, ties to the lower
+// axis).  Returns the split mask (bit 4 >> d for dimension d) and the box
+// midpoint.
+__device__ __forceinline__ uint8_t decide_split(int64_t cnt, const double* b, int32_t max_leaf,
+                                                double mid[3]) {
   double ext[3];
   for (int d = 0; d < 3; ++d) ext[d] = __dsub_rn(b[3 + d], b[d]);
   uint8_t mask = 0;
@@ -93,8 +84,27 @@ __global__ void k_tree_decide(int32_t ls, int32_t nl, const int32_t* __restrict_
       }
     }
   }
+  for (int d = 0; d < 3; ++d) mid[d] = __dmul_rn(__dadd_rn(b[d], b[3 + d]), 0.5);
+  return mask;
+}
+
+// Split decision of each cluster of the level.
+__global__ void k_tree_decide(int32_t ls, int32_t nl, const int32_t* __restrict__ begin,
+                              const int32_t* __restrict__ end, const double* __restrict__ box,
+                              int32_t max_leaf, uint8_t* __restrict__ splitmask,
+                              double* __restrict__ mid, int32_t* __restrict__ nchunks,
+                              int32_t* __restrict__ first_child, int32_t* __restrict__ nchild,
+                              int32_t* __restrict__ nsplit) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nl) return;
+  int c = ls + j;
+  int64_t cnt = (int64_t)end[c] - begin[c];
+  first_child[c] = -1;
+  nchild[c] = 0;
+  double m[3];
+  const uint8_t mask = decide_split(cnt, box + (int64_t)c * 6, max_leaf, m);
   splitmask[j] = mask;
-  for (int d = 0; d < 3; ++d) mid[(int64_t)j * 3 + d] = __dmul_rn(__dadd_rn(b[d], b[3 + d]), 0.5);
+  for (int d = 0; d < 3; ++d) mid[(int64_t)j * 3 + d] = m[d];
   // every cluster of the level is streamed: split ones are scattered to their
   // children, the others (leaves) copied to the same place of the other buffer
   nchunks[j] = (int32_t)((cnt + kTreeChunk - 1) / kTreeChunk);
@@ -260,6 +270,87 @@ __global__ void k_tree_children(int32_t nl, int32_t ls, int32_t le, int32_t lvl,
   nchild[c] = k;
 }
 
+// Stable scatter of the splitting chunk [s0, s1) by child code: particle i
+// goes to base[code] + (its rank among the chunk's particles of that code).
+// warp_cnt, running and base are shared arrays of the block; base[0..8) holds
+// the chunk's destinations on entry.  Every thread of the block calls this.
+template <typename Ld>
+__device__ __forceinline__ void scatter_chunk(int32_t s0, int32_t s1, const uint8_t* __restrict__ code,
+                                              const double* __restrict__ x, const double* __restrict__ y,
+                                              const double* __restrict__ z, const int32_t* __restrict__ perm,
+                                              double* __restrict__ x2, double* __restrict__ y2,
+                                              double* __restrict__ z2, int32_t* __restrict__ perm2,
+                                              int32_t (*warp_cnt)[9], int32_t* running, const int32_t* base,
+                                              Ld ld) {
+  constexpr int W = kTreeThreads / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // each step's particle is loaded one step ahead, so that its loads overlap
+  // the block barriers of the step before
+  int32_t i = s0 + threadIdx.x;
+  bool valid = i < s1;
+  double px = 0.0, py = 0.0, pz = 0.0;
+  int32_t pp = 0;
+  int d = 8;
+  if (valid) {
+    px = ld(x + i);
+    py = ld(y + i);
+    pz = ld(z + i);
+    pp = ld(perm + i);
+    d = code[i];
+  }
+  for (int r = 0; r < kTreeChunk / kTreeThreads; ++r) {
+    const int32_t in = i + kTreeThreads;
+    const bool vn = in < s1;
+    double nx = 0.0, ny = 0.0, nz = 0.0;
+    int32_t np = 0;
+    int dn = 8;
+    if (vn) {
+      nx = ld(x + in);
+      ny = ld(y + in);
+      nz = ld(z + in);
+      np = ld(perm + in);
+      dn = code[in];
+    }
+    for (int k = threadIdx.x; k < W * 9; k += kTreeThreads) (&warp_cnt[0][0])[k] = 0;
+    __syncthreads();
+    unsigned peers = __match_any_sync(0xffffffffu, d);
+    int rank = __popc(peers & ((1u << lane) - 1u));
+    if (rank == 0) warp_cnt[warp][d] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      int32_t dst = base[d] + running[d] + rank;
+      for (int w = 0; w < warp; ++w) dst += warp_cnt[w][d];
+      x2[dst] = px;
+      y2[dst] = py;
+      z2[dst] = pz;
+      perm2[dst] = pp;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+      int32_t t = 0;
+      for (int w = 0; w < W; ++w) t += warp_cnt[w][threadIdx.x];
+      running[threadIdx.x] += t;
+    }
+    __syncthreads();
+    i = in;
+    valid = vn;
+    px = nx;
+    py = ny;
+    pz = nz;
+    pp = np;
+    d = dn;
+  }
+}
+
+struct LdPlain {
+  template <typename T>
+  __device__ T operator()(const T* p) const { return *p; }
+};
+struct LdCg {   // bypasses L1: data written by other blocks of the same launch
+  template <typename T>
+  __device__ T operator()(const T* p) const { return __ldcg(p); }
+};
+
 __global__ void k_tree_scatter(int32_t ls, const int32_t* __restrict__ chunk_cluster,
                                const int32_t* __restrict__ chunk_start,
                                const int32_t* __restrict__ end, const uint8_t* __restrict__ splitmask,
@@ -273,7 +364,6 @@ __global__ void k_tree_scatter(int32_t ls, const int32_t* __restrict__ chunk_clu
   __shared__ int32_t warp_cnt[W][9];
   __shared__ int32_t running[8];
   __shared__ int32_t base[8];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int q = blockIdx.x;
   int32_t s0 = chunk_start[q];
   int32_t s1 = min(s0 + kTreeChunk, end[ls + chunk_cluster[q]]);
@@ -290,32 +380,7 @@ __global__ void k_tree_scatter(int32_t ls, const int32_t* __restrict__ chunk_clu
     running[threadIdx.x] = 0;
     base[threadIdx.x] = chunk_base[(int64_t)q * 8 + threadIdx.x];
   }
-  for (int r = 0; r < kTreeChunk / kTreeThreads; ++r) {
-    for (int i = threadIdx.x; i < W * 9; i += kTreeThreads) (&warp_cnt[0][0])[i] = 0;
-    __syncthreads();
-    int32_t i = s0 + r * kTreeThreads + threadIdx.x;
-    bool valid = i < s1;
-    int d = valid ? code[i] : 8;
-    unsigned peers = __match_any_sync(0xffffffffu, d);
-    int rank = __popc(peers & ((1u << lane) - 1u));
-    if (rank == 0) warp_cnt[warp][d] = __popc(peers);
-    __syncthreads();
-    if (valid) {
-      int32_t dst = base[d] + running[d] + rank;
-      for (int w = 0; w < warp; ++w) dst += warp_cnt[w][d];
-      x2[dst] = x[i];
-      y2[dst] = y[i];
-      z2[dst] = z[i];
-      perm2[dst] = perm[i];
-    }
-    __syncthreads();
-    if (threadIdx.x < 8) {
-      int32_t t = 0;
-      for (int w = 0; w < W; ++w) t += warp_cnt[w][threadIdx.x];
-      running[threadIdx.x] += t;
-    }
-    __syncthreads();
-  }
+  scatter_chunk(s0, s1, code, x, y, z, perm, x2, y2, z2, perm2, warp_cnt, running, base, LdPlain());
 }
 
 // Shrink every new cluster to the bounding box of its particles (Sec. 2.3):
@@ -623,6 +688,766 @@ int build_tree(Tree& T, const double* coords, int32_t n, const std::vector<int32
   dfree(flag, s);
   dfree(excl, s);
   return BLDTT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// The whole build in one cooperative launch
+// ---------------------------------------------------------------------------
+// k_tree_all runs the build above without returning to the host: the roots'
+// boxes, then every level (split decisions, child counts, stable scatter),
+// then the leaf order, separated by grid barriers (all blocks are co-resident
+// in a cooperative launch; every barrier wait is bounded).  The decisions,
+// the scatter and hence the tree are those of the level-by-level kernels:
+// the same device functions make them.  Two things differ in how, not what:
+// the children's boxes are reduced per chunk of the scattered order (each
+// chunk holds whole runs of children; exact minima and maxima of the
+// order-preserving keys, folded together by atomics), and the leaf order
+// comes from subtree leaf counts instead of a scan over particles.
+//
+// Key boxes: entry e holds 6 unsigned words, the complements of the flipped
+// keys of the minima (x, y, z) and the flipped keys of the maxima, so that
+// every update is an atomicMax and zero is the empty box.
+constexpr int kTreeCoopThreads = kTreeThreads;
+constexpr int kTreeMaxBlocks = 1024;
+constexpr uint64_t kTreeWaitNs = 5000000000ull;   // bound on one grid barrier wait (5 s)
+constexpr int kTreeHeadLevels = 232;              // level starts carried in the result header
+constexpr int kWideCombine = 64;                  // clusters of more chunks are combined block-wide
+
+struct TreeGrid {
+  unsigned count, gen;   // barrier
+  int32_t status;        // -1 running, 0 done, 1 clusters would exceed the capacity, 2 a barrier
+                         // gave up, 3 deeper than kMaxTreeLevels, 4 a non-finite input value
+  int32_t level;         // resume: the level to (re)process; done: the last level
+  int32_t parity;        // coordinate buffer holding that level's order
+  int32_t need;          // status 1: clusters needed
+  int32_t nleaves;
+  int32_t bad;           // set by any block that met a non-finite value
+  int32_t level_start[kTreeHeadLevels];   // first kTreeHeadLevels level starts
+};
+static_assert(sizeof(TreeGrid) <= kPinnedSlot, "the result header is read through one pinned slot");
+
+struct TreeCoop {
+  int32_t *begin, *end, *parent, *first_child, *nchild, *level, *problem;
+  double* box;
+  int32_t cap;                                   // cluster capacity of every per-cluster array
+  const double* coords;                          // input, SoA [3][n]
+  int32_t n;
+  double *x0, *y0, *z0, *x1, *y1, *z1;
+  int32_t *perm0, *perm1;
+  uint8_t* code;
+  const int32_t* roots;                          // [nroots + 1] particle offsets
+  int32_t nroots;
+  const double* charges;                         // checked for finite values (may be null)
+  int64_t ncharges;
+  int32_t max_leaf;
+  uint8_t* mask;                                 // per cluster of the level, [cap]
+  long long* midk;                               // [cap][3] midpoint keys
+  int32_t *coff, *nchk, *child_cnt, *nch, *chof;   // chunk offsets (block-local), chunks, [cap][8], children
+  int32_t *chunk_cluster, *chunk_start, *counts, *chunk_base;   // per chunk, [qcap], [qcap][8]
+  int32_t qcap;
+  unsigned long long *kbox0, *kbox1;             // [8 cap][6] key boxes (by level parity)
+  int32_t* bsrc;                                 // [cap] cluster -> its key box entry
+  int32_t *nsub, *leaf_ids, *leaf_first, *leaf_last;
+  int2* part;                                    // [grid] per-block chunk and split counts
+  int32_t* part2;                                // [grid] per-block child counts
+  int32_t* level_start;                          // [kMaxTreeLevels + 2]
+  TreeGrid* g;
+};
+
+__device__ __forceinline__ uint64_t tree_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ bool tree_grid_sync(TreeGrid* g, unsigned nblocks) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* vgen = &g->gen;
+    const unsigned gen0 = *vgen;
+    __threadfence();
+    if (atomicAdd(&g->count, 1u) == nblocks - 1u) {
+      atomicExch(&g->count, 0u);
+      __threadfence();
+      atomicAdd(&g->gen, 1u);
+    } else {
+      const uint64_t t0 = tree_ns();
+      while (*vgen == gen0) {
+        if (tree_ns() - t0 > kTreeWaitNs) {
+          ok = 0;
+          atomicExch(&g->status, 2);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long flip_key(double v) {
+  return (unsigned long long)okey(v) ^ 0x8000000000000000ull;
+}
+__device__ __forceinline__ double unflip_key(unsigned long long u) {
+  return okey_inv((long long)(u ^ 0x8000000000000000ull));
+}
+
+// Block-wide exclusive scan of two counts; totals in *ta, *tb.
+__device__ __forceinline__ void tree_block_scan2(int32_t a, int32_t b, int32_t* xa, int32_t* xb,
+                                                 int32_t* ta, int32_t* tb) {
+  __shared__ int32_t wa[kTreeCoopThreads / 32], wb[kTreeCoopThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t ia = a, ib = b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t u = __shfl_up_sync(0xffffffffu, ia, o), v = __shfl_up_sync(0xffffffffu, ib, o);
+    if (lane >= o) {
+      ia += u;
+      ib += v;
+    }
+  }
+  if (lane == 31) {
+    wa[warp] = ia;
+    wb[warp] = ib;
+  }
+  __syncthreads();
+  int32_t pa = 0, pb = 0, sa = 0, sb = 0;
+  for (int w = 0; w < kTreeCoopThreads / 32; ++w) {
+    if (w < warp) {
+      pa += wa[w];
+      pb += wb[w];
+    }
+    sa += wa[w];
+    sb += wb[w];
+  }
+  *xa = pa + ia - a;
+  *xb = pb + ib - b;
+  *ta = sa;
+  *tb = sb;
+  __syncthreads();
+}
+
+// pre[0..G] = exclusive prefix of v(0..G-1) (per-block counts), in shared memory.
+template <typename F>
+__device__ __forceinline__ void block_prefix(unsigned G, int32_t* pre, F v) {
+  int32_t run = 0;
+  for (unsigned base = 0; base < G; base += kTreeCoopThreads) {
+    const unsigned i = base + threadIdx.x;
+    const int32_t x = i < G ? v(i) : 0;
+    int32_t xa, xb, ta, tb;
+    tree_block_scan2(x, 0, &xa, &xb, &ta, &tb);
+    if (i < G) pre[i] = run + xa;
+    run += ta;
+  }
+  if (threadIdx.x == 0) pre[G] = run;
+  __syncthreads();
+}
+
+// Last index k in [lo, hi) with key(k) <= q (key non-decreasing, key(lo) <= q).
+template <typename F>
+__device__ __forceinline__ int32_t last_le(int32_t lo, int32_t hi, int64_t q, F key) {
+  while (hi - lo > 1) {
+    const int32_t m = (lo + hi) >> 1;
+    if (key(m) <= q) lo = m; else hi = m;
+  }
+  return lo;
+}
+
+// Exact box of particles [a, b) folded into key box kb (flipped keys; the
+// block's threads all call this and thread 0 issues the atomics).
+__device__ void box_keys_of_range(int32_t a, int32_t b, const double* __restrict__ x,
+                                  const double* __restrict__ y, const double* __restrict__ z,
+                                  unsigned long long* __restrict__ kb) {
+  __shared__ unsigned long long sm[kTreeCoopThreads / 32][6];
+  unsigned long long m[6] = {0, 0, 0, 0, 0, 0};
+  for (int32_t i = a + threadIdx.x; i < b; i += kTreeCoopThreads) {
+    const unsigned long long u[3] = {flip_key(__ldcg(x + i)), flip_key(__ldcg(y + i)), flip_key(__ldcg(z + i))};
+    for (int d = 0; d < 3; ++d) {
+      m[d] = max(m[d], ~u[d]);
+      m[3 + d] = max(m[3 + d], u[d]);
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = 0; k < 6; ++k)
+    for (int o = 16; o; o >>= 1) m[k] = max(m[k], __shfl_down_sync(0xffffffffu, m[k], o));
+  if (lane == 0)
+    for (int k = 0; k < 6; ++k) sm[warp][k] = m[k];
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    unsigned long long r = 0;
+    for (int w = 0; w < kTreeCoopThreads / 32; ++w) r = max(r, sm[w][threadIdx.x]);
+    if (b > a) atomicMax(kb + threadIdx.x, r);
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kTreeCoopThreads, 4) k_tree_all(TreeCoop p) {
+  __shared__ int32_t pq[kTreeMaxBlocks + 1];   // per-block chunk prefix of the level
+  __shared__ int32_t pc[kTreeMaxBlocks + 1];   // per-block child prefix of the level
+  __shared__ int32_t s_cnt[8];
+  __shared__ int32_t s_ws[kTreeCoopThreads / 32][8];   // block_scan8 workspace
+  __shared__ int32_t warp_cnt[kTreeThreads / 32][9];
+  __shared__ int32_t running[8], s_base[8];
+  const unsigned G = gridDim.x, b = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  TreeGrid* g = p.g;
+  int L = __ldcg(&g->level);
+  int par = __ldcg(&g->parity);
+  const int64_t gthreads = (int64_t)G * kTreeCoopThreads;
+  const int64_t gtid = (int64_t)b * kTreeCoopThreads + threadIdx.x;
+
+  if (L == 0 && par == 0) {
+    // ---- prologue: particles into buffer 0, the roots and their boxes ----
+    bool bad = false;
+    for (int64_t i = gtid; i < p.n; i += gthreads) {
+      const double vx = p.coords[i], vy = p.coords[(int64_t)p.n + i], vz = p.coords[2 * (int64_t)p.n + i];
+      bad |= !isfinite(vx) || !isfinite(vy) || !isfinite(vz);
+      p.x0[i] = vx;
+      p.y0[i] = vy;
+      p.z0[i] = vz;
+      p.perm0[i] = (int32_t)i;
+    }
+    for (int64_t i = gtid; i < p.ncharges; i += gthreads) bad |= !isfinite(p.charges[i]);
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicExch(&g->bad, 1);
+    for (int64_t r = gtid; r < p.nroots; r += gthreads) {
+      p.begin[r] = p.roots[r];
+      p.end[r] = p.roots[r + 1];
+      p.parent[r] = -1;
+      p.level[r] = 0;
+      p.problem[r] = (int32_t)r;
+      p.bsrc[r] = (int32_t)r * 8;
+    }
+    if (b == 0 && threadIdx.x == 0) {
+      p.level_start[0] = g->level_start[0] = 0;
+      p.level_start[1] = g->level_start[1] = p.nroots;
+    }
+    // root boxes: chunks of the particle array, each folded into the roots it overlaps
+    const int64_t nq = ((int64_t)p.n + kTreeChunk - 1) / kTreeChunk;
+    for (int64_t q = b; q < nq; q += G) {
+      const int32_t s0 = (int32_t)(q * kTreeChunk), s1 = (int32_t)min((int64_t)p.n, (q + 1) * kTreeChunk);
+      int32_t r = last_le(0, p.nroots, s0, [&](int32_t k) { return (int64_t)p.roots[k]; });
+      for (; r < p.nroots && p.roots[r] < s1; ++r) {
+        const int32_t a = max(s0, p.roots[r]), e = min(s1, p.roots[r + 1]);
+        box_keys_of_range(a, e, p.coords, p.coords + p.n, p.coords + 2 * (int64_t)p.n,
+                          p.kbox0 + (int64_t)r * 8 * 6);
+      }
+    }
+    if (!tree_grid_sync(g, G)) return;
+    if (__ldcg(&g->bad)) {
+      if (b == 0 && threadIdx.x == 0) atomicExch(&g->status, 4);
+      return;
+    }
+  }
+
+  for (;; ++L, par ^= 1) {
+    const int32_t ls = __ldcg(p.level_start + L), le = __ldcg(p.level_start + L + 1), nl = le - ls;
+    const double* x = par ? p.x1 : p.x0;
+    const double* y = par ? p.y1 : p.y0;
+    const double* z = par ? p.z1 : p.z0;
+    const int32_t* perm = par ? p.perm1 : p.perm0;
+    double* x2 = par ? p.x0 : p.x1;
+    double* y2 = par ? p.y0 : p.y1;
+    double* z2 = par ? p.z0 : p.z1;
+    int32_t* perm2 = par ? p.perm0 : p.perm1;
+    const unsigned long long* kcur = (L & 1) ? p.kbox1 : p.kbox0;
+    unsigned long long* knext = (L & 1) ? p.kbox0 : p.kbox1;
+    const int32_t jlo = (int32_t)((int64_t)nl * b / G), jhi = (int32_t)((int64_t)nl * (b + 1) / G);
+
+    // ---- 1. boxes of the level's clusters, split decisions, chunk counts ----
+    int32_t run_q = 0, run_s = 0;
+    for (int32_t base = jlo; base < jhi; base += kTreeCoopThreads) {   // block-uniform trip count
+      const int32_t j = base + threadIdx.x;
+      int32_t nq = 0, sp = 0;
+      if (j < jhi) {
+        const int32_t c = ls + j;
+        const unsigned long long* kb = kcur + (int64_t)__ldcg(p.bsrc + c) * 6;
+        double bx[6];
+        for (int d = 0; d < 3; ++d) {
+          bx[d] = unflip_key(~__ldcg(kb + d));
+          bx[3 + d] = unflip_key(__ldcg(kb + 3 + d));
+        }
+        for (int k = 0; k < 6; ++k) p.box[(int64_t)c * 6 + k] = bx[k];
+        const int64_t cnt = (int64_t)__ldcg(p.end + c) - __ldcg(p.begin + c);
+        double mid[3];
+        const uint8_t mask = decide_split(cnt, bx, p.max_leaf, mid);
+        p.mask[j] = mask;
+        for (int d = 0; d < 3; ++d) p.midk[(int64_t)j * 3 + d] = okey(mid[d]);
+        p.first_child[c] = -1;
+        p.nchild[c] = 0;
+        nq = (int32_t)((cnt + kTreeChunk - 1) / kTreeChunk);
+        p.nchk[j] = nq;
+        sp = mask ? 1 : 0;
+        if (mask)
+          for (int k = 0; k < 48; ++k) knext[(int64_t)j * 48 + k] = 0ull;
+      }
+      int32_t xq, xs, tq, ts;
+      tree_block_scan2(nq, sp, &xq, &xs, &tq, &ts);
+      if (j < jhi) p.coff[j] = run_q + xq;
+      run_q += tq;
+      run_s += ts;
+    }
+    if (threadIdx.x == 0) p.part[b] = make_int2(run_q, run_s);
+    if (!tree_grid_sync(g, G)) return;
+    block_prefix(G, pq, [&](unsigned i) { return __ldcg(&p.part[i].x); });
+    {
+      int32_t splits = 0;
+      for (unsigned i = threadIdx.x; i < G; i += kTreeCoopThreads) splits += __ldcg(&p.part[i].y);
+      splits = __syncthreads_or(splits != 0);
+      if (!splits) break;                     // no cluster of this level splits
+    }
+    const int32_t TC = pq[G];
+    if (TC > p.qcap) {                        // cannot happen: qcap >= n / kTreeChunk + cap
+      if (b == 0 && threadIdx.x == 0) atomicExch(&g->status, 1);
+      return;
+    }
+    // cluster j of chunk q: the block whose chunk range holds q, then its cluster
+    auto cluster_of = [&](int32_t q, int32_t* qstart) {
+      const int32_t bb = last_le(0, (int32_t)G, q, [&](int32_t k) { return (int64_t)pq[k]; });
+      // blocks with no chunks share pq with their successor: take the last block at or below q
+      const int32_t blo = (int32_t)((int64_t)nl * bb / G), bhi = (int32_t)((int64_t)nl * (bb + 1) / G);
+      const int32_t j = last_le(blo, bhi, q, [&](int32_t k) { return (int64_t)pq[bb] + __ldcg(p.coff + k); });
+      *qstart = pq[bb] + __ldcg(p.coff + j);
+      return j;
+    };
+
+    // ---- 2. child codes and counts per chunk (two particles per thread and step) ----
+    for (int32_t q = b; q < TC; q += G) {
+      int32_t q0;
+      const int32_t j = cluster_of(q, &q0);
+      const int32_t c = ls + j;
+      const int32_t s0 = __ldcg(p.begin + c) + (q - q0) * kTreeChunk;
+      const int32_t s1 = min(s0 + kTreeChunk, __ldcg(p.end + c));
+      if (threadIdx.x == 0) {
+        p.chunk_cluster[q] = j;
+        p.chunk_start[q] = s0;
+      }
+      const uint8_t mask = __ldcg(p.mask + j);
+      if (!mask) continue;                    // a leaf's chunk: copied, not counted
+      if (threadIdx.x < 8) s_cnt[threadIdx.x] = 0;
+      __syncthreads();
+      const long long mk[3] = {__ldcg(p.midk + (int64_t)j * 3), __ldcg(p.midk + (int64_t)j * 3 + 1),
+                               __ldcg(p.midk + (int64_t)j * 3 + 2)};
+      for (int32_t i0 = s0; i0 < s1; i0 += 2 * kTreeCoopThreads) {   // warp-uniform trip count
+        const int32_t ia = i0 + threadIdx.x, ib = ia + kTreeCoopThreads;
+        const bool va = ia < s1, vb = ib < s1;
+        double ax = 0.0, ay = 0.0, az = 0.0, bx = 0.0, by = 0.0, bz = 0.0;
+        if (va) {
+          ax = __ldcg(x + ia);
+          ay = __ldcg(y + ia);
+          az = __ldcg(z + ia);
+        }
+        if (vb) {
+          bx = __ldcg(x + ib);
+          by = __ldcg(y + ib);
+          bz = __ldcg(z + ib);
+        }
+        const int ca = va ? child_code(ax, ay, az, mask, mk) : 8;
+        const int cb = vb ? child_code(bx, by, bz, mask, mk) : 8;
+        if (va) p.code[ia] = (uint8_t)ca;
+        if (vb) p.code[ib] = (uint8_t)cb;
+        const unsigned pa = __match_any_sync(0xffffffffu, ca), pb = __match_any_sync(0xffffffffu, cb);
+        if (va && (pa & ((1u << lane) - 1u)) == 0) atomicAdd(&s_cnt[ca], __popc(pa));
+        if (vb && (pb & ((1u << lane) - 1u)) == 0) atomicAdd(&s_cnt[cb], __popc(pb));
+      }
+      __syncthreads();
+      if (threadIdx.x < 8) p.counts[(int64_t)q * 8 + threadIdx.x] = s_cnt[threadIdx.x];
+      __syncthreads();
+    }
+    if (!tree_grid_sync(g, G)) return;
+
+    // ---- 3. per splitting cluster: child counts and the chunks' destinations ----
+    // Clusters of many chunks take the whole block, one after the other; the
+    // rest take one warp each.
+    for (int32_t j = jlo; j < jhi; ++j) {     // block-uniform
+      const int32_t nq = __ldcg(p.nchk + j);
+      if (nq <= kWideCombine || !__ldcg(p.mask + j)) continue;
+      const int32_t q0 = pq[b] + __ldcg(p.coff + j);
+      int32_t v[8], ex[8], tot[8], cb[8], run[8];
+      for (int d = 0; d < 8; ++d) v[d] = 0;
+      for (int32_t t = threadIdx.x; t < nq; t += kTreeCoopThreads)
+        for (int d = 0; d < 8; ++d) v[d] += __ldcg(p.counts + (int64_t)(q0 + t) * 8 + d);
+      block_scan8(v, ex, tot, s_ws);
+      int32_t pos = __ldcg(p.begin + ls + j), k = 0;
+      for (int d = 0; d < 8; ++d) {
+        cb[d] = pos;
+        pos += tot[d];
+        run[d] = 0;
+        k += tot[d] > 0;
+      }
+      if (threadIdx.x < 8) p.child_cnt[(int64_t)j * 8 + threadIdx.x] = tot[threadIdx.x];
+      if (threadIdx.x == 0) p.nch[j] = k;
+      for (int32_t base = 0; base < nq; base += kTreeCoopThreads) {
+        const int32_t t = base + threadIdx.x;
+        for (int d = 0; d < 8; ++d) v[d] = t < nq ? __ldcg(p.counts + (int64_t)(q0 + t) * 8 + d) : 0;
+        int32_t tile[8];
+        block_scan8(v, ex, tile, s_ws);
+        if (t < nq)
+          for (int d = 0; d < 8; ++d) p.chunk_base[(int64_t)(q0 + t) * 8 + d] = cb[d] + run[d] + ex[d];
+        for (int d = 0; d < 8; ++d) run[d] += tile[d];
+      }
+    }
+    for (int32_t j = jlo + warp; j < jhi; j += kTreeCoopThreads / 32) {
+      const uint8_t mask = __ldcg(p.mask + j);
+      const int32_t nq = __ldcg(p.nchk + j);
+      if (!mask) {
+        if (lane == 0) p.nch[j] = 0;
+        continue;
+      }
+      if (nq > kWideCombine) continue;        // done above
+      const int32_t q0 = pq[b] + __ldcg(p.coff + j);
+      int32_t tot[8];
+      for (int d = 0; d < 8; ++d) tot[d] = 0;
+      for (int32_t t = lane; t < nq; t += 32)
+        for (int d = 0; d < 8; ++d) tot[d] += __ldcg(p.counts + (int64_t)(q0 + t) * 8 + d);
+      for (int d = 0; d < 8; ++d)
+        for (int o = 16; o; o >>= 1) tot[d] += __shfl_xor_sync(0xffffffffu, tot[d], o);
+      int32_t cb[8], k = 0;
+      int32_t pos = __ldcg(p.begin + ls + j);
+      for (int d = 0; d < 8; ++d) {
+        cb[d] = pos;
+        pos += tot[d];
+        k += tot[d] > 0;
+      }
+      if (lane < 8) p.child_cnt[(int64_t)j * 8 + lane] = tot[lane];
+      if (lane == 0) p.nch[j] = k;
+      for (int32_t t0 = 0; t0 < nq; t0 += 32) {   // chunk-order exclusive scan per code
+        const int32_t t = t0 + lane;
+        for (int d = 0; d < 8; ++d) {
+          const int32_t v = t < nq ? __ldcg(p.counts + (int64_t)(q0 + t) * 8 + d) : 0;
+          int32_t inc = v;
+          for (int o = 1; o < 32; o <<= 1) {
+            const int32_t w = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += w;
+          }
+          if (t < nq) p.chunk_base[(int64_t)(q0 + t) * 8 + d] = cb[d] + inc - v;
+          cb[d] += __shfl_sync(0xffffffffu, inc, 31);
+        }
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    {
+      int32_t run_c = 0;
+      for (int32_t base = jlo; base < jhi; base += kTreeCoopThreads) {
+        const int32_t j = base + threadIdx.x;
+        const int32_t v = j < jhi ? __ldcg(p.nch + j) : 0;
+        int32_t xa, xb, ta, tb;
+        tree_block_scan2(v, 0, &xa, &xb, &ta, &tb);
+        if (j < jhi) p.chof[j] = run_c + xa;
+        run_c += ta;
+      }
+      if (threadIdx.x == 0) p.part2[b] = run_c;
+    }
+    if (!tree_grid_sync(g, G)) return;
+    block_prefix(G, pc, [&](unsigned i) { return __ldcg(p.part2 + i); });
+    const int32_t NC = pc[G];
+    if ((int64_t)le + NC > (int64_t)p.cap || L + 1 >= kMaxTreeLevels) {   // the same decision in every block
+      if (b == 0 && threadIdx.x == 0) {
+        g->level = L;
+        g->parity = par;
+        g->need = le + NC;
+        atomicExch(&g->status, L + 1 >= kMaxTreeLevels ? 3 : 1);
+      }
+      return;
+    }
+
+    // ---- 4. the children, and the stable scatter into the other buffer ----
+    for (int32_t j = jlo + threadIdx.x; j < jhi; j += kTreeCoopThreads) {
+      if (!__ldcg(p.mask + j)) continue;
+      const int32_t c = ls + j;
+      const int32_t fc = le + pc[b] + __ldcg(p.chof + j);
+      int32_t pos = __ldcg(p.begin + c), k = 0;
+      const int32_t prob = __ldcg(p.problem + c);
+      for (int d = 0; d < 8; ++d) {
+        const int32_t cnt = __ldcg(p.child_cnt + (int64_t)j * 8 + d);
+        if (cnt == 0) continue;
+        const int32_t id = fc + k++;
+        p.begin[id] = pos;
+        p.end[id] = pos + cnt;
+        p.parent[id] = c;
+        p.level[id] = L + 1;
+        p.problem[id] = prob;
+        p.bsrc[id] = j * 8 + d;
+        pos += cnt;
+      }
+      p.first_child[c] = fc;
+      p.nchild[c] = k;
+    }
+    for (int32_t q = b; q < TC; q += G) {
+      const int32_t j = __ldcg(p.chunk_cluster + q);
+      const int32_t s0 = __ldcg(p.chunk_start + q);
+      const int32_t s1 = min(s0 + kTreeChunk, __ldcg(p.end + ls + j));
+      if (!__ldcg(p.mask + j)) {              // a leaf: same positions in the other buffer
+        for (int32_t i = s0 + threadIdx.x; i < s1; i += kTreeCoopThreads) {
+          x2[i] = __ldcg(x + i);
+          y2[i] = __ldcg(y + i);
+          z2[i] = __ldcg(z + i);
+          perm2[i] = __ldcg(perm + i);
+        }
+        continue;
+      }
+      if (threadIdx.x < 8) {
+        running[threadIdx.x] = 0;
+        s_base[threadIdx.x] = __ldcg(p.chunk_base + (int64_t)q * 8 + threadIdx.x);
+      }
+      scatter_chunk(s0, s1, p.code, x, y, z, perm, x2, y2, z2, perm2, warp_cnt, running, s_base, LdCg());
+    }
+    if (b == 0 && threadIdx.x == 0) {
+      p.level_start[L + 2] = le + NC;
+      if (L + 2 < kTreeHeadLevels) g->level_start[L + 2] = le + NC;   // the host reads these
+    }
+    if (!tree_grid_sync(g, G)) return;
+
+    // ---- 5. the children's boxes: each chunk's positions now hold whole runs of children ----
+    for (int32_t q = b; q < TC; q += G) {
+      const int32_t j = __ldcg(p.chunk_cluster + q);
+      if (!__ldcg(p.mask + j)) continue;
+      const int32_t s0 = __ldcg(p.chunk_start + q);
+      const int32_t s1 = min(s0 + kTreeChunk, __ldcg(p.end + ls + j));
+      int32_t pos = __ldcg(p.begin + ls + j);
+      for (int d = 0; d < 8 && pos < s1; ++d) {   // block-uniform
+        const int32_t e = pos + __ldcg(p.child_cnt + (int64_t)j * 8 + d);
+        if (e > s0 && e > pos)
+          box_keys_of_range(max(pos, s0), min(e, s1), x2, y2, z2, knext + ((int64_t)j * 8 + d) * 6);
+        pos = e;
+      }
+    }
+    if (!tree_grid_sync(g, G)) return;
+  }
+
+  // ---- leaf order: leaves under every cluster, then each cluster's first leaf ----
+  const int32_t C = __ldcg(p.level_start + L + 1);
+  for (int64_t c = gtid; c < C; c += gthreads) p.nsub[c] = 0;
+  if (!tree_grid_sync(g, G)) return;
+  for (int64_t c = gtid; c < C; c += gthreads)   // every leaf counts itself in each ancestor
+    if (__ldcg(p.nchild + c) == 0)
+      for (int32_t a = (int32_t)c; a >= 0; a = __ldcg(p.parent + a)) atomicAdd(p.nsub + a, 1);
+  if (!tree_grid_sync(g, G)) return;
+  if (b == 0) {   // roots in particle order
+    int32_t run = 0;
+    for (int32_t base = 0; base < p.nroots; base += kTreeCoopThreads) {
+      const int32_t r = base + threadIdx.x;
+      const int32_t v = r < p.nroots ? __ldcg(p.nsub + r) : 0;
+      int32_t xa, xb, ta, tb;
+      tree_block_scan2(v, 0, &xa, &xb, &ta, &tb);
+      if (r < p.nroots) p.leaf_first[r] = run + xa;
+      run += ta;
+    }
+    if (threadIdx.x == 0) g->nleaves = run;
+  }
+  if (!tree_grid_sync(g, G)) return;
+  // first leaf of c: its root's first leaf plus the leaves under the earlier
+  // siblings of c and of each of its ancestors (children are in particle order)
+  for (int64_t c = gtid; c < C; c += gthreads) {
+    int32_t f = 0, a = (int32_t)c;
+    for (int32_t up = __ldcg(p.parent + a); up >= 0; a = up, up = __ldcg(p.parent + a))
+      for (int32_t sib = __ldcg(p.first_child + up); sib < a; ++sib) f += __ldcg(p.nsub + sib);
+    f += __ldcg(p.leaf_first + a);   // a is the root
+    const int32_t n_c = __ldcg(p.nsub + c);
+    if (c >= p.nroots) p.leaf_first[c] = f;
+    p.leaf_last[c] = f + n_c;
+    if (__ldcg(p.nchild + c) == 0) p.leaf_ids[f] = (int32_t)c;
+  }
+  if (b == 0 && threadIdx.x == 0) {
+    g->level = L;
+    g->parity = par;
+    atomicCAS(&g->status, -1, 0);            // unless a block met an error
+  }
+}
+
+static bool coop_tree_available(int* blocks) {
+  int dev = 0, sms = 0, coop = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree_all, kTreeCoopThreads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (!coop || per_sm < 1) return false;
+  *blocks = std::min(kTreeMaxBlocks, sms * std::min(per_sm, 4));
+  return true;
+}
+
+// The build by one cooperative launch (k_tree_all), relaunched from the level
+// it stopped at when the cluster arrays must grow.  *done stays false when the
+// device has no cooperative launch; the caller then runs build_tree.
+static int build_tree_coop(Tree& T, const double* coords, int32_t n, const std::vector<int32_t>& roots,
+                           int32_t max_leaf, int degree, const double* charges, int64_t ncharges,
+                           cudaStream_t s, Counters& cnt, bool* done) {
+  *done = false;
+  int G = 0;
+  if (!coop_tree_available(&G)) return BLDTT_OK;
+  T.n = n;
+  const int32_t nroots = (int32_t)roots.size() - 1;
+  TreeCoop p{};
+  p.n = n;
+  p.coords = coords;
+  p.nroots = nroots;
+  p.charges = charges;
+  p.ncharges = charges ? ncharges : 0;
+  p.max_leaf = max_leaf;
+  BL_TRY(dalloc_n(&T.x, n, s));
+  BL_TRY(dalloc_n(&T.y, n, s));
+  BL_TRY(dalloc_n(&T.z, n, s));
+  BL_TRY(dalloc_n(&T.perm, n, s));
+  BL_TRY(dalloc_n(&p.x1, n, s));
+  BL_TRY(dalloc_n(&p.y1, n, s));
+  BL_TRY(dalloc_n(&p.z1, n, s));
+  BL_TRY(dalloc_n(&p.perm1, n, s));
+  BL_TRY(dalloc_n(&p.code, n, s));
+  p.x0 = T.x;
+  p.y0 = T.y;
+  p.z0 = T.z;
+  p.perm0 = T.perm;
+  int32_t* d_roots = nullptr;
+  BL_TRY(dalloc_n(&d_roots, roots.size(), s));
+  BL_CUDA(cudaMemcpyAsync(d_roots, roots.data(), roots.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  p.roots = d_roots;
+  BL_TRY(dalloc_n(&p.part, G, s));
+  BL_TRY(dalloc_n(&p.part2, G, s));
+  BL_TRY(dalloc_n(&p.level_start, kMaxTreeLevels + 2, s));
+  BL_TRY(dalloc_n(&p.g, 1, s));
+  BL_CUDA(cudaMemsetAsync(p.g, 0, sizeof(TreeGrid), s));
+  // cluster capacity: grown (and the launch resumed) when a level needs more
+  size_t cap = std::max<size_t>(1024, 2 * (size_t)nroots + 4 * ((size_t)n / std::max(1, max_leaf) + 1));
+  size_t c_k0 = 0, c_k1 = 0, c_bs = 0, c_mask = 0, c_midk = 0, c_coff = 0, c_nchk = 0, c_cc = 0,
+         c_nch = 0, c_chof = 0, c_nsub = 0, c_lid = 0, c_lf = 0, c_ll = 0, c_qc = 0, c_qs = 0, c_cnt = 0,
+         c_cb = 0;
+  int status = BLDTT_OK;
+  TreeGrid h{};
+  bool first = true;
+  for (;;) {
+    const size_t keep = first ? 0 : (size_t)T.level_start.back();   // clusters made so far
+    BL_TRY(grow_clusters(T, cap, keep, s));
+    cap = T.cap;
+    const size_t kkeep = first ? 0 : c_k0;
+    BL_TRY(dgrow(&p.kbox0, &c_k0, cap * 48, kkeep, s));
+    BL_TRY(dgrow(&p.kbox1, &c_k1, cap * 48, first ? 0 : c_k1, s));
+    BL_TRY(dgrow(&p.bsrc, &c_bs, cap, keep, s));
+    BL_TRY(dgrow(&p.mask, &c_mask, cap, 0, s));
+    BL_TRY(dgrow(&p.midk, &c_midk, cap * 3, 0, s));
+    BL_TRY(dgrow(&p.coff, &c_coff, cap, 0, s));
+    BL_TRY(dgrow(&p.nchk, &c_nchk, cap, 0, s));
+    BL_TRY(dgrow(&p.child_cnt, &c_cc, cap * 8, 0, s));
+    BL_TRY(dgrow(&p.nch, &c_nch, cap, 0, s));
+    BL_TRY(dgrow(&p.chof, &c_chof, cap, 0, s));
+    BL_TRY(dgrow(&p.nsub, &c_nsub, cap, 0, s));
+    BL_TRY(dgrow(&T.leaf_ids, &c_lid, cap, 0, s));
+    BL_TRY(dgrow(&T.leaf_first, &c_lf, cap, 0, s));
+    BL_TRY(dgrow(&T.leaf_last, &c_ll, cap, 0, s));
+    const size_t qcap = (size_t)n / kTreeChunk + cap + 1;
+    BL_TRY(dgrow(&p.chunk_cluster, &c_qc, qcap, 0, s));
+    BL_TRY(dgrow(&p.chunk_start, &c_qs, qcap, 0, s));
+    BL_TRY(dgrow(&p.counts, &c_cnt, qcap * 8, 0, s));
+    BL_TRY(dgrow(&p.chunk_base, &c_cb, qcap * 8, 0, s));
+    if (first)   // the roots' key boxes start empty (zero)
+      BL_CUDA(cudaMemsetAsync(p.kbox0, 0, (size_t)nroots * 48 * sizeof(unsigned long long), s));
+    BL_CUDA(cudaMemsetAsync(p.g, 0, 2 * sizeof(unsigned), s));           // barrier
+    BL_CUDA(cudaMemsetAsync(&p.g->status, 0xff, sizeof(int32_t), s));    // -1: running
+    p.begin = T.begin;
+    p.end = T.end;
+    p.parent = T.parent;
+    p.first_child = T.first_child;
+    p.nchild = T.nchild;
+    p.level = T.level;
+    p.problem = T.problem;
+    p.box = T.box;
+    p.cap = (int32_t)std::min<size_t>(cap, INT32_MAX);
+    p.qcap = (int32_t)std::min<size_t>(qcap, INT32_MAX);
+    p.leaf_ids = T.leaf_ids;
+    p.leaf_first = T.leaf_first;
+    p.leaf_last = T.leaf_last;
+    void* args[] = {&p};
+    BL_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_tree_all), dim3(G),
+                                        dim3(kTreeCoopThreads), args, 0, s));
+    BL_LAUNCHED(cnt.launches);
+    BL_TRY(read_device(p.g, &h, sizeof(h), s));
+    first = false;
+    if (h.status != 1) break;
+    // clusters so far: the levels up to the one that stopped
+    T.level_start.assign(h.level_start, h.level_start + std::min(h.level + 2, kTreeHeadLevels));
+    if (h.level + 2 > kTreeHeadLevels) {
+      T.level_start.resize(h.level + 2);
+      BL_TRY(read_device(p.level_start, T.level_start.data(), T.level_start.size() * sizeof(int32_t), s));
+    }
+    cap = std::max<size_t>(2 * cap, (size_t)h.need);
+  }
+  if (h.status == 0) {
+    const int L = h.level;
+    T.level_start.assign(h.level_start, h.level_start + std::min(L + 2, kTreeHeadLevels));
+    if (L + 2 > kTreeHeadLevels) {
+      T.level_start.resize(L + 2);
+      BL_TRY(read_device(p.level_start, T.level_start.data(), T.level_start.size() * sizeof(int32_t), s));
+    }
+    T.nlevels = L + 1;
+    T.nclusters = T.level_start.back();
+    T.nroots = nroots;
+    T.nleaves = h.nleaves;
+    if (h.parity) {   // the final order is in buffer 1
+      std::swap(T.x, p.x1);
+      std::swap(T.y, p.y1);
+      std::swap(T.z, p.z1);
+      std::swap(T.perm, p.perm1);
+    }
+  } else if (h.status == 2) {
+    set_error("a grid barrier of the tree build gave up after %llu ns", (unsigned long long)kTreeWaitNs);
+    status = BLDTT_ETIMEOUT;
+  } else if (h.status == 3) {
+    set_error("tree deeper than %d levels: some cluster is not separated by its midpoints", kMaxTreeLevels);
+    status = BLDTT_EINTERNAL;
+  } else if (h.status == 4) {
+    set_error("a target, source or charge value is not finite");
+    status = BLDTT_EINVAL;
+  } else {
+    set_error("the tree build ended with status %d", h.status);
+    status = BLDTT_EINTERNAL;
+  }
+  dfree(p.x1, s); dfree(p.y1, s); dfree(p.z1, s); dfree(p.perm1, s); dfree(p.code, s);
+  dfree(d_roots, s); dfree(p.part, s); dfree(p.part2, s); dfree(p.level_start, s); dfree(p.g, s);
+  dfree(p.kbox0, s); dfree(p.kbox1, s); dfree(p.bsrc, s); dfree(p.mask, s); dfree(p.midk, s);
+  dfree(p.coff, s); dfree(p.nchk, s); dfree(p.child_cnt, s); dfree(p.nch, s); dfree(p.chof, s);
+  dfree(p.nsub, s); dfree(p.chunk_cluster, s); dfree(p.chunk_start, s); dfree(p.counts, s);
+  dfree(p.chunk_base, s);
+  if (status != BLDTT_OK) return status;
+  const int C = T.nclusters;
+  BL_TRY(dalloc_n(&T.center, (size_t)C * 3, s));
+  BL_TRY(dalloc_n(&T.radius, (size_t)C, s));
+  BL_TRY(dalloc_n(&T.nodes, (size_t)C * 3 * (degree + 1), s));
+  k_tree_geometry<<<nblk(C, 128), 128, 0, s>>>(C, degree, T.box, T.center, T.radius, T.nodes);
+  BL_LAUNCHED(cnt.launches);
+  *done = true;
+  return BLDTT_OK;
+}
+
+bool tree_build_cooperative() {
+  int G = 0;
+  return coop_tree_available(&G);
+}
+
+int build_tree_checked(Tree& T, const double* coords, int32_t n, const std::vector<int32_t>& roots,
+                       int32_t max_leaf, int degree, const double* charges, int64_t ncharges,
+                       cudaStream_t s, Counters& cnt) {
+  bool done = false;
+  BL_TRY(build_tree_coop(T, coords, n, roots, max_leaf, degree, charges, ncharges, s, cnt, &done));
+  if (done) return BLDTT_OK;
+  // level by level: reject non-finite input first (an infinite box is split without end)
+  int* bad = nullptr;
+  BL_TRY(dalloc_n(&bad, 1, s));
+  BL_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  BL_TRY(check_finite(coords, 3 * (int64_t)n, bad, s, cnt));
+  if (charges) BL_TRY(check_finite(charges, ncharges, bad, s, cnt));
+  int h_bad = 0;
+  BL_TRY(read_device(bad, &h_bad, sizeof(int), s));
+  dfree(bad, s);
+  if (h_bad) {
+    set_error("a target, source or charge value is not finite");
+    return BLDTT_EINVAL;
+  }
+  return build_tree(T, coords, n, roots, max_leaf, degree, s, cnt);
 }
 
 // ---------------------------------------------------------------------------
