@@ -4,6 +4,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -66,6 +67,23 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
   return ms;
 }
 
+constexpr size_t kPoolKeep = size_t(1) << 30;
+constexpr int kMaxDevices = 64;
+std::mutex g_res_mu;
+cudaMemPool_t g_pools[kMaxDevices] = {};
+std::vector<void*> g_pinned_free;
+
+
+static void release_pool(bldtt_plan* p) {
+  if (p->mempool) cudaMemPoolTrimTo(p->mempool, kPoolKeep);
+  if (p->h_pinned) {
+    std::lock_guard<std::mutex> lock(g_res_mu);
+    g_pinned_free.push_back(p->h_pinned);
+  }
+  p->mempool = nullptr;
+  p->h_pinned = nullptr;
+}
+
 void release(bldtt_plan* p) {
   if (!p) return;
   cudaStream_t s = p->stream;
@@ -106,8 +124,7 @@ void release(bldtt_plan* p) {
   dfree_ptr(p->sel_b, s);
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
   cudaStreamSynchronize(s);
-  if (p->mempool) cudaMemPoolDestroy(p->mempool);   // every allocation from it is freed
-  if (p->h_pinned) cudaFreeHost(p->h_pinned);
+  release_pool(p);
   for (auto& e : p->ev)
     if (e) cudaEventDestroy(e);
   cudaGetLastError();
@@ -256,8 +273,8 @@ int setup_impl(bldtt_plan* p, const double* targets, const double* sources, cons
   BL_TRY(interaction_grids(p));
   BL_CUDA(cudaEventRecord(p->ev[2], s));
   BL_CUDA(cudaStreamSynchronize(s));
-  // hand back what the set-up's temporaries held; the plan's arrays stay
-  BL_CUDA(cudaMemPoolTrimTo(p->mempool, 0));
+  // hand back what the set-up's temporaries held beyond kPoolKeep; the plan's arrays stay
+  BL_CUDA(cudaMemPoolTrimTo(p->mempool, kPoolKeep));
   p->ms_tree = elapsed(p->ev[0], p->ev[1]);
   p->ms_lists = elapsed(p->ev[1], p->ev[2]);
   return BLDTT_OK;
@@ -338,24 +355,43 @@ static int upload_selector(bldtt_plan* p, const float* weights) {
   return BLDTT_OK;
 }
 
-// The plan's memory pool: device memory, kept when freed (release threshold
-// at the maximum) until the plan is destroyed or the set-up trims it; and its
-// pinned host slots for the set-up's small device-to-host reads.
+// Device memory comes from one memory pool per device, shared by every plan
+// of the process: memory freed by a plan stays reserved (release threshold at
+// the maximum) for the next set-up, whose allocations then need no new
+// mapping; set-ups and destroys trim the pool back to kPoolKeep bytes beyond
+// what live plans hold.  The set-up's small device-to-host reads go through
+// two pinned host slots per plan, recycled from a process-wide free list.
 static int create_pool(bldtt_plan* p) {
   int dev = 0;
   BL_CUDA(cudaGetDevice(&dev));
-  cudaMemPoolProps props;
-  std::memset(&props, 0, sizeof(props));
-  props.allocType = cudaMemAllocationTypePinned;
-  props.handleTypes = cudaMemHandleTypeNone;
-  props.location.type = cudaMemLocationTypeDevice;
-  props.location.id = dev;
-  BL_CUDA(cudaMemPoolCreate(&p->mempool, &props));
-  uint64_t keep = UINT64_MAX;
-  BL_CUDA(cudaMemPoolSetAttribute(p->mempool, cudaMemPoolAttrReleaseThreshold, &keep));
-  BL_CUDA(cudaMallocHost(&p->h_pinned, 2 * kPinnedSlot));
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("device ordinal %d beyond the supported %d", dev, kMaxDevices);
+    return BLDTT_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(g_res_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    BL_CUDA(cudaMemPoolCreate(&pool, &props));
+    uint64_t keep = UINT64_MAX;
+    BL_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    g_pools[dev] = pool;
+  }
+  p->mempool = g_pools[dev];
+  if (!g_pinned_free.empty()) {
+    p->h_pinned = g_pinned_free.back();
+    g_pinned_free.pop_back();
+  } else {
+    BL_CUDA(cudaMallocHost(&p->h_pinned, 2 * kPinnedSlot));
+  }
   return BLDTT_OK;
 }
+
 
 // Common set-up of a batch of nprob problems (nprob = 1 for bldtt_setup).
 // t_off / s_off: host offsets (nprob + 1) of each problem's targets / sources.

@@ -8,6 +8,7 @@
 // rest are replaced by the pairs of the split side's children (Alg. 2,
 // lines 11-17).  Compaction uses prefix sums, so the entry order, and hence
 // every later summation order, is deterministic.
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -383,16 +384,18 @@ static int traverse_cooperative(bldtt_plan* p, const TreeView& tt, const TreeVie
     uint32_t* ek = nullptr;
     int8_t* act = nullptr;
     DttGrid* g = nullptr;
-    BL_TRY(dalloc_n(&b0, cap, s));
-    BL_TRY(dalloc_n(&b1, cap, s));
-    BL_TRY(dalloc_n(&koff, cap, s));
-    BL_TRY(dalloc_n(&eoff, cap, s));
-    BL_TRY(dalloc_n(&act, cap, s));
+    Arena scratch;
+    scratch.add(&b0, cap);
+    scratch.add(&b1, cap);
+    scratch.add(&koff, cap);
+    scratch.add(&eoff, cap);
+    scratch.add(&act, cap);
+    scratch.add(&part, G);
+    scratch.add(&g, 1);
+    BL_TRY(scratch.alloc(s));
     BL_TRY(dalloc_n(&et, cap, s));
     BL_TRY(dalloc_n(&es, cap, s));
     BL_TRY(dalloc_n(&ek, cap, s));
-    BL_TRY(dalloc_n(&part, G, s));
-    BL_TRY(dalloc_n(&g, 1, s));
     BL_CUDA(cudaMemsetAsync(g, 0, sizeof(DttGrid), s));
     BL_CUDA(cudaMemcpyAsync(b0, roots, (size_t)P * sizeof(int2), cudaMemcpyDeviceToDevice, s));
     BL_CUDA(cudaMemcpyAsync(&g->F0, &P, sizeof(int32_t), cudaMemcpyHostToDevice, s));
@@ -411,7 +414,7 @@ static int traverse_cooperative(bldtt_plan* p, const TreeView& tt, const TreeVie
     BL_LAUNCHED(p->setup_counter.launches);
     DttGrid h{};
     BL_TRY(read_device(g, &h, sizeof(h), s));
-    dfree(b0, s); dfree(b1, s); dfree(koff, s); dfree(eoff, s); dfree(act, s); dfree(part, s); dfree(g, s);
+    scratch.release(s);
     if (h.status == 2) {
       dfree(et, s); dfree(es, s); dfree(ek, s);
       set_error("a grid barrier of the cooperative traversal gave up after %llu ns",
@@ -439,18 +442,10 @@ int build_lists(bldtt_plan* p, cudaStream_t s) {
   int2 *front = nullptr, *next = nullptr;
   int32_t *ent_t = nullptr, *ent_s = nullptr;
   uint32_t* ent_key = nullptr;
-  BL_TRY(dalloc_n(&front, fcap, s));
-  BL_TRY(dalloc_n(&next, ncap, s));
-  BL_TRY(dalloc_n(&ent_t, ecap, s));
-  BL_TRY(dalloc_n(&ent_s, ecap, s));
-  BL_TRY(dalloc_n(&ent_key, ecap, s));
   // One root pair per problem (Alg. 2 starts from the two roots of each problem).
   const int32_t P = p->tt.nroots;
-  if ((size_t)P > fcap) {
-    size_t c = fcap;
-    BL_TRY(dgrow(&front, &c, (size_t)P, 0, s));
-    fcap = c;
-  }
+  fcap = std::max(fcap, (size_t)P);
+  BL_TRY(dalloc_n(&front, fcap, s));
   k_root_pairs<<<nblk(P, 256), 256, 0, s>>>(front, P);
   BL_LAUNCHED(cnt.launches);
   int32_t F = P;
@@ -465,12 +460,17 @@ int build_lists(bldtt_plan* p, cudaStream_t s) {
     uint32_t* ck = nullptr;
     BL_TRY(traverse_cooperative(p, tt, st, front, P, &ct, &cs, &ck, &E, &done, s));
     if (done) {
-      dfree(ent_t, s); dfree(ent_s, s); dfree(ent_key, s);
       ent_t = ct;
       ent_s = cs;
       ent_key = ck;
       F = 0;                                   // the loop below has nothing left to do
     }
+  }
+  if (F > 0) {   // the level-by-level loop's buffers
+    BL_TRY(dalloc_n(&next, ncap, s));
+    BL_TRY(dalloc_n(&ent_t, ecap, s));
+    BL_TRY(dalloc_n(&ent_s, ecap, s));
+    BL_TRY(dalloc_n(&ent_key, ecap, s));
   }
   // per-level scratch, grown as the front grows; the two totals of a level
   // come back to the host in one read
@@ -478,7 +478,7 @@ int build_lists(bldtt_plan* p, cudaStream_t s) {
   int32_t *nkids = nullptr, *isentry = nullptr, *koff = nullptr, *eoff = nullptr, *tot2 = nullptr;
   int8_t* action = nullptr;
   int16_t* choice = nullptr;
-  BL_TRY(dalloc_n(&tot2, 2, s));
+  if (F > 0) BL_TRY(dalloc_n(&tot2, 2, s));
   while (F > 0) {
     BL_TRY(dgrow(&nkids, &cap_k, (size_t)F, 0, s));
     BL_TRY(dgrow(&isentry, &cap_i, (size_t)F, 0, s));
@@ -554,9 +554,7 @@ int build_lists(bldtt_plan* p, cudaStream_t s) {
     k_key_hist<<<nblk(E, 256), 256, 0, s>>>(ent_key, E, hist);
     BL_LAUNCHED(cnt.launches);
   }
-  int32_t total = 0;
-  BL_TRY(scan_exclusive(hist, p->list_ptr, nkeys, &total, s, cnt));
-  BL_CUDA(cudaMemcpyAsync(p->list_ptr + nkeys, &total, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  BL_TRY(scan_exclusive_dev(hist, p->list_ptr, nkeys, p->list_ptr + nkeys, s, cnt));   // total last
 
   // evals: kMaxClasses counters, then room for the nclass + 1 class offsets
   constexpr int kRead = kMaxClasses + (kMaxClasses + 2) / 2;
@@ -589,8 +587,8 @@ int build_lists(bldtt_plan* p, cudaStream_t s) {
     p->list_count[class_type(c)] += p->class_count[c];
     p->interactions[class_type(c)] += p->class_evals[c];
   }
-  if (total != E) {
-    set_error("interaction list CSR holds %d entries, traversal produced %lld", total, (long long)E);
+  if (h_ptr[nclass] != E) {
+    set_error("interaction list CSR holds %d entries, traversal produced %lld", h_ptr[nclass], (long long)E);
     return BLDTT_EINTERNAL;
   }
   dfree(evals, s); dfree(hist, s); dfree(order, s);

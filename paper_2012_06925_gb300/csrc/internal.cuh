@@ -20,6 +20,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/bldtt.h"
@@ -177,6 +178,36 @@ inline void dfree_ptr(T*& p, cudaStream_t s) {
 // Grow a device array to hold at least `need` elements, keeping `keep` of them.
 template <class T>
 int dgrow(T** p, size_t* cap, size_t need, size_t keep, cudaStream_t s);
+// Several scratch arrays carved from one device allocation (256-byte aligned
+// each): one pool call instead of one per array.  add() records where each
+// array's pointer goes; alloc() allocates and sets them all; release() frees.
+class Arena {
+ public:
+  template <class T>
+  void add(T** p, size_t n) {
+    parts_.push_back({reinterpret_cast<void**>(p), n * sizeof(T)});
+  }
+  int alloc(cudaStream_t s) {
+    size_t total = 0;
+    for (const auto& pr : parts_) total += round(pr.second);
+    BL_TRY(dalloc(&block_, total > 0 ? total : 256, s));
+    char* c = static_cast<char*>(block_);
+    for (const auto& pr : parts_) {
+      *pr.first = c;
+      c += round(pr.second);
+    }
+    return BLDTT_OK;
+  }
+  void release(cudaStream_t s) {
+    dfree(block_, s);
+    block_ = nullptr;
+  }
+
+ private:
+  static size_t round(size_t b) { return (b + 255) & ~size_t(255); }
+  std::vector<std::pair<void**, size_t>> parts_;
+  void* block_ = nullptr;
+};
 
 struct Tree {
   int32_t n = 0;                      // particles
@@ -184,6 +215,8 @@ struct Tree {
   size_t cap = 0;                     // allocated cluster capacity
   double *x = nullptr, *y = nullptr, *z = nullptr;   // tree order
   int32_t* perm = nullptr;            // tree position -> input index
+  double *sx = nullptr, *sy = nullptr, *sz = nullptr;   // spare buffers of the build (or null),
+  int32_t* sperm = nullptr;                             // taken by the Morton pass
   int32_t *begin = nullptr, *end = nullptr, *parent = nullptr;
   int32_t *first_child = nullptr, *nchild = nullptr, *level = nullptr;
   int32_t* problem = nullptr;         // [C] problem (root) the cluster belongs to

@@ -172,15 +172,16 @@ static int scan_impl(const int32_t* in, int32_t* out, int64_t n, int32_t* total_
     return BLDTT_OK;
   }
   int32_t *sums = nullptr, *offs = nullptr;
-  BL_TRY(dalloc_n(&sums, tiles, s));
-  BL_TRY(dalloc_n(&offs, tiles, s));
+  Arena scratch;
+  scratch.add(&sums, tiles);
+  scratch.add(&offs, tiles);
+  BL_TRY(scratch.alloc(s));
   k_scan_reduce<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums);
   BL_LAUNCHED(c.launches);
   BL_TRY(scan_impl(sums, offs, tiles, nullptr, s, c));
   k_scan_apply<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, offs, total_dev);
   BL_LAUNCHED(c.launches);
-  dfree(sums, s);
-  dfree(offs, s);
+  scratch.release(s);
   return BLDTT_OK;
 }
 
@@ -280,10 +281,12 @@ int radix_sort_pairs(uint32_t* keys, int32_t* vals, int64_t n, int bits, cudaStr
   int64_t tiles = (n + kScanTile - 1) / kScanTile;
   uint32_t* k2 = nullptr;
   int32_t *v2 = nullptr, *hist = nullptr, *offs = nullptr;
-  BL_TRY(dalloc_n(&k2, n, s));
-  BL_TRY(dalloc_n(&v2, n, s));
-  BL_TRY(dalloc_n(&hist, tiles * kRadix, s));
-  BL_TRY(dalloc_n(&offs, tiles * kRadix, s));
+  Arena scratch;
+  scratch.add(&k2, n);
+  scratch.add(&v2, n);
+  scratch.add(&hist, tiles * kRadix);
+  scratch.add(&offs, tiles * kRadix);
+  BL_TRY(scratch.alloc(s));
   uint32_t *ka = keys, *kb = k2;
   int32_t *va = vals, *vb = v2;
   for (int p = 0; p < passes; ++p) {
@@ -300,10 +303,7 @@ int radix_sort_pairs(uint32_t* keys, int32_t* vals, int64_t n, int bits, cudaStr
     BL_CUDA(cudaMemcpyAsync(keys, ka, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
     BL_CUDA(cudaMemcpyAsync(vals, va, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   }
-  dfree(k2, s);
-  dfree(v2, s);
-  dfree(hist, s);
-  dfree(offs, s);
+  scratch.release(s);
   return BLDTT_OK;
 }
 

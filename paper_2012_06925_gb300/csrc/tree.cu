@@ -1298,25 +1298,26 @@ static int build_tree_coop(Tree& T, const double* coords, int32_t n, const std::
   BL_TRY(dalloc_n(&p.y1, n, s));
   BL_TRY(dalloc_n(&p.z1, n, s));
   BL_TRY(dalloc_n(&p.perm1, n, s));
-  BL_TRY(dalloc_n(&p.code, n, s));
   p.x0 = T.x;
   p.y0 = T.y;
   p.z0 = T.z;
   p.perm0 = T.perm;
   int32_t* d_roots = nullptr;
-  BL_TRY(dalloc_n(&d_roots, roots.size(), s));
+  Arena fixed;   // scratch of the whole build
+  fixed.add(&p.code, n);
+  fixed.add(&d_roots, roots.size());
+  fixed.add(&p.part, G);
+  fixed.add(&p.part2, G);
+  fixed.add(&p.level_start, kMaxTreeLevels + 2);
+  fixed.add(&p.g, 1);
+  BL_TRY(fixed.alloc(s));
   BL_CUDA(cudaMemcpyAsync(d_roots, roots.data(), roots.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   p.roots = d_roots;
-  BL_TRY(dalloc_n(&p.part, G, s));
-  BL_TRY(dalloc_n(&p.part2, G, s));
-  BL_TRY(dalloc_n(&p.level_start, kMaxTreeLevels + 2, s));
-  BL_TRY(dalloc_n(&p.g, 1, s));
   BL_CUDA(cudaMemsetAsync(p.g, 0, sizeof(TreeGrid), s));
   // cluster capacity: grown (and the launch resumed) when a level needs more
   size_t cap = std::max<size_t>(1024, 2 * (size_t)nroots + 4 * ((size_t)n / std::max(1, max_leaf) + 1));
-  size_t c_k0 = 0, c_k1 = 0, c_bs = 0, c_mask = 0, c_midk = 0, c_coff = 0, c_nchk = 0, c_cc = 0,
-         c_nch = 0, c_chof = 0, c_nsub = 0, c_lid = 0, c_lf = 0, c_ll = 0, c_qc = 0, c_qs = 0, c_cnt = 0,
-         c_cb = 0;
+  size_t c_lid = 0, c_lf = 0, c_ll = 0, old_cap = 0;
+  Arena per_cap;   // scratch sized by the cluster capacity
   int status = BLDTT_OK;
   TreeGrid h{};
   bool first = true;
@@ -1324,28 +1325,41 @@ static int build_tree_coop(Tree& T, const double* coords, int32_t n, const std::
     const size_t keep = first ? 0 : (size_t)T.level_start.back();   // clusters made so far
     BL_TRY(grow_clusters(T, cap, keep, s));
     cap = T.cap;
-    const size_t kkeep = first ? 0 : c_k0;
-    BL_TRY(dgrow(&p.kbox0, &c_k0, cap * 48, kkeep, s));
-    BL_TRY(dgrow(&p.kbox1, &c_k1, cap * 48, first ? 0 : c_k1, s));
-    BL_TRY(dgrow(&p.bsrc, &c_bs, cap, keep, s));
-    BL_TRY(dgrow(&p.mask, &c_mask, cap, 0, s));
-    BL_TRY(dgrow(&p.midk, &c_midk, cap * 3, 0, s));
-    BL_TRY(dgrow(&p.coff, &c_coff, cap, 0, s));
-    BL_TRY(dgrow(&p.nchk, &c_nchk, cap, 0, s));
-    BL_TRY(dgrow(&p.child_cnt, &c_cc, cap * 8, 0, s));
-    BL_TRY(dgrow(&p.nch, &c_nch, cap, 0, s));
-    BL_TRY(dgrow(&p.chof, &c_chof, cap, 0, s));
-    BL_TRY(dgrow(&p.nsub, &c_nsub, cap, 0, s));
+    const size_t qcap = (size_t)n / kTreeChunk + cap + 1;
+    Arena grown;
+    TreeCoop q = p;   // the new capacity's arrays, then what must carry over
+    grown.add(&q.kbox0, cap * 48);
+    grown.add(&q.kbox1, cap * 48);
+    grown.add(&q.bsrc, cap);
+    grown.add(&q.mask, cap);
+    grown.add(&q.midk, cap * 3);
+    grown.add(&q.coff, cap);
+    grown.add(&q.nchk, cap);
+    grown.add(&q.child_cnt, cap * 8);
+    grown.add(&q.nch, cap);
+    grown.add(&q.chof, cap);
+    grown.add(&q.nsub, cap);
+    grown.add(&q.chunk_cluster, qcap);
+    grown.add(&q.chunk_start, qcap);
+    grown.add(&q.counts, qcap * 8);
+    grown.add(&q.chunk_base, qcap * 8);
+    BL_TRY(grown.alloc(s));
+    if (first) {   // the roots' key boxes start empty (zero)
+      BL_CUDA(cudaMemsetAsync(q.kbox0, 0, (size_t)nroots * 48 * sizeof(unsigned long long), s));
+    } else {       // the key boxes of the level to resume, and the clusters' box entries
+      BL_CUDA(cudaMemcpyAsync(q.kbox0, p.kbox0, old_cap * 48 * sizeof(unsigned long long),
+                              cudaMemcpyDeviceToDevice, s));
+      BL_CUDA(cudaMemcpyAsync(q.kbox1, p.kbox1, old_cap * 48 * sizeof(unsigned long long),
+                              cudaMemcpyDeviceToDevice, s));
+      BL_CUDA(cudaMemcpyAsync(q.bsrc, p.bsrc, keep * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    }
+    per_cap.release(s);
+    per_cap = std::move(grown);
+    p = q;
+    old_cap = cap;
     BL_TRY(dgrow(&T.leaf_ids, &c_lid, cap, 0, s));
     BL_TRY(dgrow(&T.leaf_first, &c_lf, cap, 0, s));
     BL_TRY(dgrow(&T.leaf_last, &c_ll, cap, 0, s));
-    const size_t qcap = (size_t)n / kTreeChunk + cap + 1;
-    BL_TRY(dgrow(&p.chunk_cluster, &c_qc, qcap, 0, s));
-    BL_TRY(dgrow(&p.chunk_start, &c_qs, qcap, 0, s));
-    BL_TRY(dgrow(&p.counts, &c_cnt, qcap * 8, 0, s));
-    BL_TRY(dgrow(&p.chunk_base, &c_cb, qcap * 8, 0, s));
-    if (first)   // the roots' key boxes start empty (zero)
-      BL_CUDA(cudaMemsetAsync(p.kbox0, 0, (size_t)nroots * 48 * sizeof(unsigned long long), s));
     BL_CUDA(cudaMemsetAsync(p.g, 0, 2 * sizeof(unsigned), s));           // barrier
     BL_CUDA(cudaMemsetAsync(&p.g->status, 0xff, sizeof(int32_t), s));    // -1: running
     p.begin = T.begin;
@@ -1406,13 +1420,16 @@ static int build_tree_coop(Tree& T, const double* coords, int32_t n, const std::
     set_error("the tree build ended with status %d", h.status);
     status = BLDTT_EINTERNAL;
   }
-  dfree(p.x1, s); dfree(p.y1, s); dfree(p.z1, s); dfree(p.perm1, s); dfree(p.code, s);
-  dfree(d_roots, s); dfree(p.part, s); dfree(p.part2, s); dfree(p.level_start, s); dfree(p.g, s);
-  dfree(p.kbox0, s); dfree(p.kbox1, s); dfree(p.bsrc, s); dfree(p.mask, s); dfree(p.midk, s);
-  dfree(p.coff, s); dfree(p.nchk, s); dfree(p.child_cnt, s); dfree(p.nch, s); dfree(p.chof, s);
-  dfree(p.nsub, s); dfree(p.chunk_cluster, s); dfree(p.chunk_start, s); dfree(p.counts, s);
-  dfree(p.chunk_base, s);
-  if (status != BLDTT_OK) return status;
+  fixed.release(s);
+  per_cap.release(s);
+  if (status != BLDTT_OK) {
+    dfree(p.x1, s); dfree(p.y1, s); dfree(p.z1, s); dfree(p.perm1, s);
+    return status;
+  }
+  T.sx = p.x1;   // the other coordinate buffer: the Morton pass writes into it
+  T.sy = p.y1;
+  T.sz = p.z1;
+  T.sperm = p.perm1;
   const int C = T.nclusters;
   BL_TRY(dalloc_n(&T.center, (size_t)C * 3, s));
   BL_TRY(dalloc_n(&T.radius, (size_t)C, s));
@@ -1570,13 +1587,18 @@ __global__ void __launch_bounds__(kMortonThreads) k_leaf_morton(
 }
 
 int morton_order_leaves(Tree& T, int32_t max_leaf, cudaStream_t s, Counters& cnt) {
-  if (T.nleaves == 0) return BLDTT_OK;
-  double *x2 = nullptr, *y2 = nullptr, *z2 = nullptr;
-  int32_t* perm2 = nullptr;
-  BL_TRY(dalloc_n(&x2, T.n, s));
-  BL_TRY(dalloc_n(&y2, T.n, s));
-  BL_TRY(dalloc_n(&z2, T.n, s));
-  BL_TRY(dalloc_n(&perm2, T.n, s));
+  double *x2 = T.sx, *y2 = T.sy, *z2 = T.sz;   // the build's spare buffers, else new ones
+  int32_t* perm2 = T.sperm;
+  T.sx = T.sy = T.sz = nullptr;
+  T.sperm = nullptr;
+  if (T.nleaves == 0) {
+    dfree(x2, s); dfree(y2, s); dfree(z2, s); dfree(perm2, s);
+    return BLDTT_OK;
+  }
+  if (!x2) BL_TRY(dalloc_n(&x2, T.n, s));
+  if (!y2) BL_TRY(dalloc_n(&y2, T.n, s));
+  if (!z2) BL_TRY(dalloc_n(&z2, T.n, s));
+  if (!perm2) BL_TRY(dalloc_n(&perm2, T.n, s));
   // keys of the largest sorted leaf (leaves hold at most max_leaf particles)
   int n2max = 2;
   while (n2max < max_leaf && n2max < kMortonMax) n2max <<= 1;
@@ -1607,6 +1629,7 @@ int morton_order_leaves(Tree& T, int32_t max_leaf, cudaStream_t s, Counters& cnt
 
 void free_tree(Tree& T, cudaStream_t s) {
   dfree_ptr(T.x, s); dfree_ptr(T.y, s); dfree_ptr(T.z, s); dfree_ptr(T.perm, s);
+  dfree_ptr(T.sx, s); dfree_ptr(T.sy, s); dfree_ptr(T.sz, s); dfree_ptr(T.sperm, s);
   dfree_ptr(T.begin, s); dfree_ptr(T.end, s); dfree_ptr(T.parent, s);
   dfree_ptr(T.first_child, s); dfree_ptr(T.nchild, s); dfree_ptr(T.level, s);
   dfree_ptr(T.problem, s);
