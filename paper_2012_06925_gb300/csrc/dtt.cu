@@ -825,18 +825,10 @@ int build_work_items(bldtt_plan* p, cudaStream_t s) {
     set_error("source pool of %lld entries exceeds the int32 index range", (long long)bound);
     return BLDTT_EINVAL;
   }
-  int32_t total = 0;
-  BL_TRY(scan_exclusive(padded, p->pad_prefix, st.nleaves, &total, s, cnt));
-  BL_CUDA(cudaMemcpyAsync(p->pad_prefix + st.nleaves, &total, sizeof(int32_t),
-                          cudaMemcpyHostToDevice, s));
+  // the padded total lands at pad_prefix[nleaves]; it comes back to the host
+  // with the item count, in one read
+  BL_TRY(scan_exclusive_dev(padded, p->pad_prefix, st.nleaves, p->pad_prefix + st.nleaves, s, cnt));
   dfree(padded, s);
-  p->pool_particles = total;
-  p->pool_len = total;
-  for (int i = 0; i < p->deg.n; ++i) {   // proxy blocks of every source cluster, per degree
-    p->deg.proxy_base[i] = p->pool_len;
-    p->pool_len += (int64_t)st.nclusters * p->deg.np_pad[i];
-  }
-  p->np_pad = p->deg.np_pad[p->deg.n - 1];
 
   const int32_t nct = tt.nclusters;
   ListView L{p->list_ptr, p->list_src, nct, st.leaf_first, st.leaf_last, p->pad_prefix, p->deg};
@@ -858,9 +850,22 @@ int build_work_items(bldtt_plan* p, cudaStream_t s) {
                                               st.begin, st.end, nitems, cost_part, cost_prox,
                                               executed, p->eval_part, p->eval_prox);
   BL_LAUNCHED(cnt.launches);
-  int32_t ni = 0;
-  BL_TRY(scan_exclusive(nitems, off, nct, &ni, s, cnt));
+  int32_t* totals = nullptr;   // [0] items, [1] padded pool particles
+  BL_TRY(dalloc_n(&totals, 2, s));
+  BL_TRY(scan_exclusive_dev(nitems, off, nct, totals, s, cnt));
+  BL_CUDA(cudaMemcpyAsync(totals + 1, p->pad_prefix + st.nleaves, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  int32_t h_tot[2];
+  BL_TRY(read_device(totals, h_tot, sizeof(h_tot), s));
+  dfree(totals, s);
+  const int32_t ni = h_tot[0];
   p->nitems = ni;
+  p->pool_particles = h_tot[1];
+  p->pool_len = h_tot[1];
+  for (int i = 0; i < p->deg.n; ++i) {   // proxy blocks of every source cluster, per degree
+    p->deg.proxy_base[i] = p->pool_len;
+    p->pool_len += (int64_t)st.nclusters * p->deg.np_pad[i];
+  }
+  p->np_pad = p->deg.np_pad[p->deg.n - 1];
   int4* items = nullptr;
   uint32_t* keys = nullptr;
   int32_t* vals = nullptr;
@@ -879,7 +884,10 @@ int build_work_items(bldtt_plan* p, cudaStream_t s) {
   // each persistent launch's tail is short.
   int seg_bits = 0;
   while ((1 << seg_bits) < segmap.n) ++seg_bits;
-  BL_TRY(radix_sort_pairs(keys, vals, ni, 25 + seg_bits, s, cnt));
+  bool fused = false;   // a shared Coulomb/Yukawa segment sets the kernel bit (bit 24)
+  for (int i = 0; i < segmap.n; ++i) fused |= segmap.kernel[i] == kKernCoulombYukawa;
+  const int key_bits = seg_bits > 0 ? 25 + seg_bits : (fused ? 25 : 24);
+  BL_TRY(radix_sort_pairs(keys, vals, ni, key_bits, s, cnt));
   // segment starts (8 int32) and the two executed-evaluation counters come
   // back to the host in one read
   int32_t* seg_first = reinterpret_cast<int32_t*>(summary + 2);
