@@ -67,15 +67,22 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
   return ms;
 }
 
-constexpr size_t kPoolKeep = size_t(1) << 30;
 constexpr int kMaxDevices = 64;
 std::mutex g_res_mu;
 cudaMemPool_t g_pools[kMaxDevices] = {};
+size_t g_pool_keep[kMaxDevices] = {};   // an eighth of the device's memory
 std::vector<void*> g_pinned_free;
+
+static size_t pool_keep(cudaMemPool_t pool) {
+  std::lock_guard<std::mutex> lock(g_res_mu);
+  for (int d = 0; d < kMaxDevices; ++d)
+    if (g_pools[d] == pool) return g_pool_keep[d];
+  return 0;
+}
 
 
 static void release_pool(bldtt_plan* p) {
-  if (p->mempool) cudaMemPoolTrimTo(p->mempool, kPoolKeep);
+  if (p->mempool) cudaMemPoolTrimTo(p->mempool, pool_keep(p->mempool));
   if (p->h_pinned) {
     std::lock_guard<std::mutex> lock(g_res_mu);
     g_pinned_free.push_back(p->h_pinned);
@@ -273,8 +280,8 @@ int setup_impl(bldtt_plan* p, const double* targets, const double* sources, cons
   BL_TRY(interaction_grids(p));
   BL_CUDA(cudaEventRecord(p->ev[2], s));
   BL_CUDA(cudaStreamSynchronize(s));
-  // hand back what the set-up's temporaries held beyond kPoolKeep; the plan's arrays stay
-  BL_CUDA(cudaMemPoolTrimTo(p->mempool, kPoolKeep));
+  // hand back what the set-up's temporaries held beyond the pool's keep; the plan's arrays stay
+  BL_CUDA(cudaMemPoolTrimTo(p->mempool, pool_keep(p->mempool)));
   p->ms_tree = elapsed(p->ev[0], p->ev[1]);
   p->ms_lists = elapsed(p->ev[1], p->ev[2]);
   return BLDTT_OK;
@@ -358,9 +365,11 @@ static int upload_selector(bldtt_plan* p, const float* weights) {
 // Device memory comes from one memory pool per device, shared by every plan
 // of the process: memory freed by a plan stays reserved (release threshold at
 // the maximum) for the next set-up, whose allocations then need no new
-// mapping; set-ups and destroys trim the pool back to kPoolKeep bytes beyond
-// what live plans hold.  The set-up's small device-to-host reads go through
-// two pinned host slots per plan, recycled from a process-wide free list.
+// mapping (at 1E8 particles, mapping the set-up's memory afresh took ~10 ms);
+// set-ups and destroys trim the pool back to an eighth of the device's memory
+// (or what live plans hold, if more).  The set-up's small device-to-host reads
+// go through two pinned host slots per plan, recycled from a process-wide free
+// list.
 static int create_pool(bldtt_plan* p) {
   int dev = 0;
   BL_CUDA(cudaGetDevice(&dev));
@@ -380,6 +389,9 @@ static int create_pool(bldtt_plan* p) {
     BL_CUDA(cudaMemPoolCreate(&pool, &props));
     uint64_t keep = UINT64_MAX;
     BL_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    size_t free_b = 0, total_b = 0;
+    BL_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    g_pool_keep[dev] = total_b / 8;
     g_pools[dev] = pool;
   }
   p->mempool = g_pools[dev];
