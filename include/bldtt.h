@@ -133,9 +133,16 @@ typedef struct bldtt_stats {
  * The caller keeps ownership of targets/sources/charges; they are copied into
  * tree order before the call returns (the call synchronises the stream), so
  * they may be freed afterwards.  The plan owns all device memory it
- * allocates (stream-ordered allocations on cuda_stream).
+ * allocates (stream-ordered allocations on cuda_stream, from one memory pool
+ * per device that the library shares between its plans and trims to an
+ * eighth of the device's memory when a set-up ends or a plan is destroyed).
+ * Each tree is built, and the fixed-rule traversal run, by one cooperative
+ * launch; with the environment variable BLDTT_LEVEL_BY_LEVEL=1 (or on a
+ * device without cooperative launches) both run level by level from the
+ * host instead, with identical results.
  * Errors: EINVAL for out-of-range sizes or parameters, a non-finite
- * coordinate or charge, an unknown kernel or precision; ENOMEM; ECUDA.
+ * coordinate or charge, an unknown kernel or precision; ENOMEM; ECUDA;
+ * ETIMEOUT if a grid barrier of a cooperative launch waited 5 s in vain.
  */
 int bldtt_setup(bldtt_plan** plan,
                 const double* targets, int64_t M,

@@ -366,6 +366,7 @@ static int traverse_cooperative(bldtt_plan* p, const TreeView& tt, const TreeVie
                                 int32_t P, int32_t** ent_t, int32_t** ent_s, uint32_t** ent_key,
                                 int64_t* E, bool* done, cudaStream_t s) {
   *done = false;
+  if (cooperative_set_up_disabled()) return BLDTT_OK;
   int dev = 0, sms = 0, coop = 0, per_sm = 0;
   BL_CUDA(cudaGetDevice(&dev));
   BL_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));

@@ -410,6 +410,9 @@ int build_tree_checked(Tree& T, const double* coords, int32_t n, const std::vect
                        int32_t max_leaf, int degree, const double* charges, int64_t ncharges,
                        cudaStream_t s, Counters& cnt);
 bool tree_build_cooperative();
+// The environment variable BLDTT_LEVEL_BY_LEVEL=1 turns the cooperative tree
+// build and traversal off (the level-by-level loops run instead; same results).
+bool cooperative_set_up_disabled();
 int morton_order_leaves(Tree& T, int32_t max_leaf, cudaStream_t s, Counters& c);
 void free_tree(Tree& T, cudaStream_t s);
 

@@ -4,6 +4,7 @@
 // depends on the order in which atomics land.
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "internal.cuh"
@@ -33,6 +34,11 @@ void set_thread_context(cudaMemPool_t pool, void* pinned) {
 }
 cudaMemPool_t thread_pool() { return t_pool; }
 void* thread_pinned() { return t_pinned; }
+
+bool cooperative_set_up_disabled() {
+  const char* e = std::getenv("BLDTT_LEVEL_BY_LEVEL");
+  return e && e[0] == '1' && e[1] == '\0';
+}
 
 int read_device(const void* dev, void* host, size_t bytes, cudaStream_t s) {
   if (t_pinned && bytes <= kPinnedSlot) {

@@ -1259,6 +1259,7 @@ __global__ void __launch_bounds__(kTreeCoopThreads, 4) k_tree_all(TreeCoop p) {
 }
 
 static bool coop_tree_available(int* blocks) {
+  if (cooperative_set_up_disabled()) return false;
   int dev = 0, sms = 0, coop = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||

@@ -199,7 +199,10 @@ def test_set_charges_and_solve_host():
     assert stats["launches_compute"] > 0
 
 
-def test_invalid_inputs_on_device():
+@pytest.mark.parametrize("level_by_level", [False, True])
+def test_invalid_inputs_on_device(level_by_level, monkeypatch):
+    if level_by_level:
+        monkeypatch.setenv("BLDTT_LEVEL_BY_LEVEL", "1")
     tgt, src, q = W.make_problem("uniform", 500, seed=13)
     bad = tgt.copy()
     bad[1, 17] = np.nan
@@ -211,7 +214,7 @@ def test_invalid_inputs_on_device():
     with pytest.raises(B.BLDTTError) as e:
         B.Plan(to_dev(tgt), to_dev(src), to_dev(qb), n=3, N0=20, M0=20)
     assert e.value.status == 1
-    # a bad source coordinate, found by the source-tree build (second stream)
+    # a bad source coordinate, found by the source-tree build
     bad_src = src.copy()
     bad_src[2, 400] = -np.inf
     with pytest.raises(B.BLDTTError) as e:
@@ -221,6 +224,37 @@ def test_invalid_inputs_on_device():
     phi, plan = run_gpu(tgt, src.copy(), q, n=3, theta=0.7, N0=20, M0=20, precision=B.FP64)
     plan.close()
     assert np.all(np.isfinite(phi))
+
+
+SET_UP_CASES = [CASES[0], CASES[1], CASES[2], CASES[6]]
+
+
+@pytest.mark.parametrize("name,pkw,mkw", SET_UP_CASES, ids=[c[0] for c in SET_UP_CASES])
+def test_cooperative_set_up_equals_level_by_level(name, pkw, mkw, monkeypatch):
+    """The tree build and the traversal in one cooperative launch each give the
+    trees, lists and potentials of the level-by-level host loops bit for bit
+    (BLDTT_LEVEL_BY_LEVEL=1 selects the loops)."""
+    tgt, src, q = problem(pkw)
+
+    def run():
+        phi, plan = run_gpu(tgt, src, q, precision=B.FP64, **mkw)
+        with plan:
+            trees = [plan.export_tree(k) for k in (0, 1)]
+            lists = plan.export_lists()
+            st = plan.stats()
+        return phi, trees, lists, st
+
+    phi_c, trees_c, lists_c, st_c = run()
+    monkeypatch.setenv("BLDTT_LEVEL_BY_LEVEL", "1")
+    phi_l, trees_l, lists_l, st_l = run()
+    assert st_l["launches_setup"] > st_c["launches_setup"]     # the loops did run
+    for a, b in zip(trees_c, trees_l):
+        assert a.keys() == b.keys()
+        for k in a:
+            assert np.asarray(a[k]).tobytes() == np.asarray(b[k]).tobytes(), k
+    for (tc, sc), (tl, sl) in zip(lists_c, lists_l):
+        assert np.array_equal(tc, tl) and np.array_equal(sc, sl)
+    assert np.array_equal(phi_c, phi_l)
 
 
 def test_plain_fp64_workload_full_size():
