@@ -139,7 +139,10 @@ typedef struct bldtt_stats {
  * Each tree is built, and the fixed-rule traversal run, by one cooperative
  * launch; with the environment variable BLDTT_LEVEL_BY_LEVEL=1 (or on a
  * device without cooperative launches) both run level by level from the
- * host instead, with identical results.
+ * host instead, with identical results.  BLDTT_TREE_CAPACITY and
+ * BLDTT_TRAVERSAL_CAPACITY override the initial cluster and traversal buffer
+ * capacities (testing: a small start makes the launches regrow and resume;
+ * the results do not change).
  * Errors: EINVAL for out-of-range sizes or parameters, a non-finite
  * coordinate or charge, an unknown kernel or precision; ENOMEM; ECUDA;
  * ETIMEOUT if a grid barrier of a cooperative launch waited 5 s in vain.

@@ -9,6 +9,7 @@
 // lines 11-17).  Compaction uses prefix sums, so the entry order, and hence
 // every later summation order, is deterministic.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -378,6 +379,8 @@ static int traverse_cooperative(bldtt_plan* p, const TreeView& tt, const TreeVie
   const int32_t imax = p->deg.n - 1;
   int64_t cap = 64 * ((int64_t)p->tt.nclusters + (int64_t)p->st.nclusters);
   if (cap < 32768) cap = 32768;
+  if (const char* e = std::getenv("BLDTT_TRAVERSAL_CAPACITY"))   // a smaller start exercises the relaunches
+    cap = std::max<int64_t>(std::strtoll(e, nullptr, 10), (int64_t)P);
   for (int attempt = 0; attempt < 3 && !*done; ++attempt, cap *= 2) {
     if (cap >= (int64_t)INT32_MAX) break;
     int2 *b0 = nullptr, *b1 = nullptr, *part = nullptr;

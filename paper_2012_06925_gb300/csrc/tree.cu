@@ -15,6 +15,7 @@
 // all problems at once, so a batch of independent problems costs one set of
 // launches per level.
 #include <algorithm>
+#include <cstdlib>
 #include <utility>
 
 #include "internal.cuh"
@@ -1317,6 +1318,8 @@ static int build_tree_coop(Tree& T, const double* coords, int32_t n, const std::
   BL_CUDA(cudaMemsetAsync(p.g, 0, sizeof(TreeGrid), s));
   // cluster capacity: grown (and the launch resumed) when a level needs more
   size_t cap = std::max<size_t>(1024, 2 * (size_t)nroots + 4 * ((size_t)n / std::max(1, max_leaf) + 1));
+  if (const char* e = std::getenv("BLDTT_TREE_CAPACITY"))   // a smaller start exercises the regrowth
+    cap = std::max<size_t>((size_t)std::strtoull(e, nullptr, 10), (size_t)nroots);
   size_t c_lid = 0, c_lf = 0, c_ll = 0, old_cap = 0;
   Arena per_cap;   // scratch sized by the cluster capacity
   int status = BLDTT_OK;

@@ -257,6 +257,51 @@ def test_cooperative_set_up_equals_level_by_level(name, pkw, mkw, monkeypatch):
     assert np.array_equal(phi_c, phi_l)
 
 
+def test_set_up_regrowth_gives_the_same_plan(monkeypatch):
+    """The cooperative launches' capacity paths: a tree build that starts with
+    room for 64 clusters (grown and resumed level by level), a traversal whose
+    buffers overflow at least once (relaunched with doubled buffers), and one
+    that never fits (three launches, then the level loop) all give the default
+    plan's trees, lists and potentials bit for bit."""
+    name, pkw, mkw = CASES[2]                     # sphere, leaves of 7: ~1000 clusters
+    tgt, src, q = problem(pkw)
+
+    def run():
+        phi, plan = run_gpu(tgt, src, q, precision=B.FP64, **mkw)
+        with plan:
+            trees = [plan.export_tree(k) for k in (0, 1)]
+            lists = plan.export_lists()
+            st = plan.stats()
+        return phi, trees, lists, st
+
+    def same(a, b):
+        assert np.array_equal(a[0], b[0])
+        for ta, tb in zip(a[1], b[1]):
+            for k in ta:
+                assert np.asarray(ta[k]).tobytes() == np.asarray(tb[k]).tobytes(), k
+        for (tc, sc), (tl, sl) in zip(a[2], b[2]):
+            assert np.array_equal(tc, tl) and np.array_equal(sc, sl)
+
+    base = run()
+    assert base[3]["num_target_clusters"] > 256
+    entries = int(sum(base[3]["list_entries"]))
+    with monkeypatch.context() as m:
+        m.setenv("BLDTT_TREE_CAPACITY", "8")
+        grown = run()
+    same(base, grown)
+    assert grown[3]["launches_setup"] > base[3]["launches_setup"]      # resumed launches
+    with monkeypatch.context() as m:                # 3 E/8 entries overflow at least once
+        m.setenv("BLDTT_TRAVERSAL_CAPACITY", str(3 * entries // 8))
+        relaunched = run()
+    same(base, relaunched)
+    assert relaunched[3]["launches_setup"] >= base[3]["launches_setup"] + 1
+    with monkeypatch.context() as m:
+        m.setenv("BLDTT_TRAVERSAL_CAPACITY", "1")
+        looped = run()
+    same(base, looped)
+    assert looped[3]["launches_setup"] > base[3]["launches_setup"] + 2
+
+
 def test_plain_fp64_workload_full_size():
     """The 2E4-particle plain FP64 workload (n=4, theta=0.7, leaves of 500):
     GPU FP64 equals the oracle BLDTT, and both are within the expected
