@@ -413,11 +413,14 @@ static int traverse_cooperative(bldtt_plan* p, const TreeView& tt, const TreeVie
     int imx = imax;
     void* args[] = {&a, &c, &np, &imx, &theta, &variant, &nct, &b0, &b1, &fcap, &et, &es, &ek, &ecap,
                     &koff, &eoff, &act, &part, &g};
-    BL_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_dtt_all), dim3(G), dim3(kDttThreads),
-                                        args, 0, s));
-    BL_LAUNCHED(p->setup_counter.launches);
     DttGrid h{};
-    BL_TRY(read_device(g, &h, sizeof(h), s));
+    {
+      std::lock_guard<std::mutex> lock(cooperative_launch_mutex());
+      BL_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_dtt_all), dim3(G),
+                                          dim3(kDttThreads), args, 0, s));
+      BL_LAUNCHED(p->setup_counter.launches);
+      BL_TRY(read_device(g, &h, sizeof(h), s));
+    }
     scratch.release(s);
     if (h.status == 2) {
       dfree(et, s); dfree(es, s); dfree(ek, s);

@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -413,6 +414,9 @@ bool tree_build_cooperative();
 // The environment variable BLDTT_LEVEL_BY_LEVEL=1 turns the cooperative tree
 // build and traversal off (the level-by-level loops run instead; same results).
 bool cooperative_set_up_disabled();
+// Held from a cooperative launch until its result is read, so that set-ups on
+// several host threads run their grid-synchronised launches one at a time.
+std::mutex& cooperative_launch_mutex();
 int morton_order_leaves(Tree& T, int32_t max_leaf, cudaStream_t s, Counters& c);
 void free_tree(Tree& T, cudaStream_t s);
 

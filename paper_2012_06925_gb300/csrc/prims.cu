@@ -35,6 +35,11 @@ void set_thread_context(cudaMemPool_t pool, void* pinned) {
 cudaMemPool_t thread_pool() { return t_pool; }
 void* thread_pinned() { return t_pinned; }
 
+std::mutex& cooperative_launch_mutex() {
+  static std::mutex mu;
+  return mu;
+}
+
 bool cooperative_set_up_disabled() {
   const char* e = std::getenv("BLDTT_LEVEL_BY_LEVEL");
   return e && e[0] == '1' && e[1] == '\0';

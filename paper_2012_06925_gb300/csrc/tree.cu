@@ -1380,10 +1380,13 @@ static int build_tree_coop(Tree& T, const double* coords, int32_t n, const std::
     p.leaf_first = T.leaf_first;
     p.leaf_last = T.leaf_last;
     void* args[] = {&p};
-    BL_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_tree_all), dim3(G),
-                                        dim3(kTreeCoopThreads), args, 0, s));
-    BL_LAUNCHED(cnt.launches);
-    BL_TRY(read_device(p.g, &h, sizeof(h), s));
+    {
+      std::lock_guard<std::mutex> lock(cooperative_launch_mutex());
+      BL_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_tree_all), dim3(G),
+                                          dim3(kTreeCoopThreads), args, 0, s));
+      BL_LAUNCHED(cnt.launches);
+      BL_TRY(read_device(p.g, &h, sizeof(h), s));
+    }
     first = false;
     if (h.status != 1) break;
     // clusters so far: the levels up to the one that stopped

@@ -302,6 +302,47 @@ def test_set_up_regrowth_gives_the_same_plan(monkeypatch):
     assert looped[3]["launches_setup"] > base[3]["launches_setup"] + 2
 
 
+def test_plans_on_two_host_threads():
+    """Plans set up and computed at the same time from two host threads, each
+    on its own stream, share the library's device memory pool and pinned read
+    slots; each gives the result it gives alone, bit for bit."""
+    import threading
+    cases = [CASES[0], CASES[1]]
+    inputs = [problem(pkw) for _, pkw, _ in cases]
+    alone = []
+    for (_, _, mkw), (tgt, src, q) in zip(cases, inputs):
+        phi, plan = run_gpu(tgt, src, q, precision=B.FP32_BULK, **mkw)
+        plan.close()
+        alone.append(phi)
+    dev = [(to_dev(t), to_dev(s_), to_dev(q)) for t, s_, q in inputs]
+    torch.cuda.synchronize()
+    out = [[None] * 3 for _ in cases]
+    errors = []
+
+    def work(i):
+        try:
+            stream = torch.cuda.Stream()
+            with torch.cuda.stream(stream):
+                for r in range(3):
+                    with B.Plan(*dev[i], precision=B.FP32_BULK, stream=stream, **cases[i][2]) as plan:
+                        phi = torch.empty(plan.M, dtype=torch.float64, device="cuda")
+                        plan.compute(phi, stream=stream)
+                        stream.synchronize()
+                        out[i][r] = phi.cpu().numpy()
+        except Exception as e:   # reported on the main thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(len(cases))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for i in range(len(cases)):
+        for r in range(3):
+            assert np.array_equal(out[i][r], alone[i]), (i, r)
+
+
 def test_plain_fp64_workload_full_size():
     """The 2E4-particle plain FP64 workload (n=4, theta=0.7, leaves of 500):
     GPU FP64 equals the oracle BLDTT, and both are within the expected
