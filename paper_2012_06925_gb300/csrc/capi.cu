@@ -370,7 +370,8 @@ static int upload_selector(bldtt_plan* p, const float* weights) {
 // (or what live plans hold, if more).  The set-up's small device-to-host reads
 // go through two pinned host slots per plan, recycled from a process-wide free
 // list.
-static int create_pool(bldtt_plan* p) {
+// The current device's shared pool (created on first use).
+static int shared_pool(cudaMemPool_t* out) {
   int dev = 0;
   BL_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) {
@@ -394,7 +395,13 @@ static int create_pool(bldtt_plan* p) {
     g_pool_keep[dev] = total_b / 8;
     g_pools[dev] = pool;
   }
-  p->mempool = g_pools[dev];
+  *out = g_pools[dev];
+  return BLDTT_OK;
+}
+
+static int create_pool(bldtt_plan* p) {
+  BL_TRY(shared_pool(&p->mempool));
+  std::lock_guard<std::mutex> lock(g_res_mu);
   if (!g_pinned_free.empty()) {
     p->h_pinned = g_pinned_free.back();
     g_pinned_free.pop_back();
@@ -403,7 +410,6 @@ static int create_pool(bldtt_plan* p) {
   }
   return BLDTT_OK;
 }
-
 
 // Common set-up of a batch of nprob problems (nprob = 1 for bldtt_setup).
 // t_off / s_off: host offsets (nprob + 1) of each problem's targets / sources.
@@ -963,6 +969,9 @@ int bldtt_solve_host(const double* targets, int64_t M, const double* sources, in
     return BLDTT_EINVAL;
   }
   BL_TRY(validate(M, N, kernel, kappa, n, theta, N0, M0, precision));
+  cudaMemPool_t pool = nullptr;   // the input and output buffers come from the shared pool too
+  BL_TRY(shared_pool(&pool));
+  PlanScope scope(pool, nullptr);
   cudaStream_t s = nullptr;
   BL_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
   const bool same = targets == sources && M == N;
