@@ -181,9 +181,23 @@ template <class T>
 int dgrow(T** p, size_t* cap, size_t need, size_t keep, cudaStream_t s);
 // Several scratch arrays carved from one device allocation (256-byte aligned
 // each): one pool call instead of one per array.  add() records where each
-// array's pointer goes; alloc() allocates and sets them all; release() frees.
+// array's pointer goes; alloc() allocates and sets them all; the block is
+// freed (stream-ordered) by release() or when the arena goes out of scope,
+// so an early error return does not leak it.
 class Arena {
  public:
+  Arena() = default;
+  Arena(const Arena&) = delete;
+  Arena& operator=(const Arena&) = delete;
+  Arena(Arena&& o) noexcept { take(o); }
+  Arena& operator=(Arena&& o) noexcept {
+    if (this != &o) {
+      release(stream_);
+      take(o);
+    }
+    return *this;
+  }
+  ~Arena() { release(stream_); }
   template <class T>
   void add(T** p, size_t n) {
     parts_.push_back({reinterpret_cast<void**>(p), n * sizeof(T)});
@@ -191,6 +205,7 @@ class Arena {
   int alloc(cudaStream_t s) {
     size_t total = 0;
     for (const auto& pr : parts_) total += round(pr.second);
+    stream_ = s;
     BL_TRY(dalloc(&block_, total > 0 ? total : 256, s));
     char* c = static_cast<char*>(block_);
     for (const auto& pr : parts_) {
@@ -200,14 +215,21 @@ class Arena {
     return BLDTT_OK;
   }
   void release(cudaStream_t s) {
-    dfree(block_, s);
+    if (block_) dfree(block_, s);
     block_ = nullptr;
   }
 
  private:
   static size_t round(size_t b) { return (b + 255) & ~size_t(255); }
+  void take(Arena& o) {
+    parts_ = std::move(o.parts_);
+    block_ = o.block_;
+    stream_ = o.stream_;
+    o.block_ = nullptr;
+  }
   std::vector<std::pair<void**, size_t>> parts_;
   void* block_ = nullptr;
+  cudaStream_t stream_ = nullptr;
 };
 
 struct Tree {

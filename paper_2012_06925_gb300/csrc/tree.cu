@@ -1296,10 +1296,14 @@ static int build_tree_coop(Tree& T, const double* coords, int32_t n, const std::
   BL_TRY(dalloc_n(&T.y, n, s));
   BL_TRY(dalloc_n(&T.z, n, s));
   BL_TRY(dalloc_n(&T.perm, n, s));
-  BL_TRY(dalloc_n(&p.x1, n, s));
-  BL_TRY(dalloc_n(&p.y1, n, s));
-  BL_TRY(dalloc_n(&p.z1, n, s));
-  BL_TRY(dalloc_n(&p.perm1, n, s));
+  BL_TRY(dalloc_n(&T.sx, n, s));   // the other coordinate buffer, held by the tree from here on
+  BL_TRY(dalloc_n(&T.sy, n, s));   // (the Morton pass writes into it; free_tree frees it)
+  BL_TRY(dalloc_n(&T.sz, n, s));
+  BL_TRY(dalloc_n(&T.sperm, n, s));
+  p.x1 = T.sx;
+  p.y1 = T.sy;
+  p.z1 = T.sz;
+  p.perm1 = T.sperm;
   p.x0 = T.x;
   p.y0 = T.y;
   p.z0 = T.z;
@@ -1409,10 +1413,10 @@ static int build_tree_coop(Tree& T, const double* coords, int32_t n, const std::
     T.nroots = nroots;
     T.nleaves = h.nleaves;
     if (h.parity) {   // the final order is in buffer 1
-      std::swap(T.x, p.x1);
-      std::swap(T.y, p.y1);
-      std::swap(T.z, p.z1);
-      std::swap(T.perm, p.perm1);
+      std::swap(T.x, T.sx);
+      std::swap(T.y, T.sy);
+      std::swap(T.z, T.sz);
+      std::swap(T.perm, T.sperm);
     }
   } else if (h.status == 2) {
     set_error("a grid barrier of the tree build gave up after %llu ns", (unsigned long long)kTreeWaitNs);
@@ -1429,14 +1433,7 @@ static int build_tree_coop(Tree& T, const double* coords, int32_t n, const std::
   }
   fixed.release(s);
   per_cap.release(s);
-  if (status != BLDTT_OK) {
-    dfree(p.x1, s); dfree(p.y1, s); dfree(p.z1, s); dfree(p.perm1, s);
-    return status;
-  }
-  T.sx = p.x1;   // the other coordinate buffer: the Morton pass writes into it
-  T.sy = p.y1;
-  T.sz = p.z1;
-  T.sperm = p.perm1;
+  if (status != BLDTT_OK) return status;
   const int C = T.nclusters;
   BL_TRY(dalloc_n(&T.center, (size_t)C * 3, s));
   BL_TRY(dalloc_n(&T.radius, (size_t)C, s));

@@ -364,11 +364,15 @@ def test_plain_fp64_workload_full_size():
 
 def test_plans_release_their_memory():
     """Set-ups and destroys in a loop (shared and separate trees, a batch, a
-    learned plan's degree set) leave the device's free memory where it was:
-    every plan's pool, pinned slots and arrays go with it."""
+    set-up that fails on a non-finite source) leave the device's free memory
+    where it was: every plan's arrays go back to the library's pool, whose
+    reserve stays the same from one cycle to the next."""
     tgt, src, q = W.make_problem("uniform", 60_000, 40_000, seed=17, sources_kind="plummer")
     dt, ds, dq = to_dev(tgt), to_dev(src), to_dev(q)
     dq_t = to_dev(W.make_problem("uniform", 60_000, seed=17)[2])
+    src_bad = src.copy()
+    src_bad[1, 39_000] = np.nan
+    ds_bad = to_dev(src_bad)
     torch.cuda.synchronize()
 
     def cycle():
@@ -381,6 +385,8 @@ def test_plans_release_their_memory():
         with B.Plan.batch(dt, off, dt, off, dq_t, [B.COULOMB, B.YUKAWA], [0.0, 0.5], n=4, N0=200,
                           M0=200) as p:
             p.compute()
+        with pytest.raises(B.BLDTTError):    # a set-up that fails in the tree build frees all it took
+            B.Plan(dt, ds_bad, dq, n=5, theta=0.7, N0=200, M0=200)
         torch.cuda.synchronize()
 
     cycle()                                   # first use: library state, module loading
