@@ -145,10 +145,11 @@ void set_error(const char* fmt, ...);
   } while (0)
 
 // Stream-ordered device allocation helpers.  Allocations come from the memory
-// pool set for the calling thread (a plan's own pool during its set-up), else
-// from the device's default pool.  A plan's pool keeps the memory that its
-// set-up frees between tree and traversal levels for reuse, where the default
-// pool hands it back to the driver at every host synchronisation.
+// pool set for the calling thread (the library's shared pool of the device
+// while a plan is set up or a host solve runs), else from the device's
+// default pool.  The shared pool keeps freed memory for reuse (up to an
+// eighth of the device's memory between set-ups), where the default pool
+// hands it back to the driver at every host synchronisation.
 int dalloc(void** p, size_t bytes, cudaStream_t s);
 // Per-thread context of the plan being set up: its memory pool and a pinned
 // host slot of kPinnedSlot bytes for small device-to-host reads.
@@ -395,8 +396,9 @@ struct bldtt_plan {
 
   // Captured compute phase (bldtt_compute_graph).
   cudaGraphExec_t graph_exec = nullptr;
-  cudaMemPool_t mempool = nullptr;    // the plan's device memory pool (see dalloc)
-  void* h_pinned = nullptr;           // two pinned slots (set-up thread, source-tree thread)
+  cudaMemPool_t mempool = nullptr;    // the device's pool, shared by the process's plans (see dalloc)
+  void* h_pinned = nullptr;           // two pinned read slots (set-up thread, source-tree thread),
+                                      // recycled between plans
   double* graph_phi = nullptr;
 };
 
